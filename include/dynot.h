@@ -1,0 +1,185 @@
+/*
+ * dynot.h -- C ABI of the GB300 dynamic optimal-transport solver.
+ *
+ * The library solves the discrete dynamic optimal-transport problem of
+ * Fitschen, Laus & Steidl, "Dynamic Optimal Transport with Mixed Boundary
+ * Conditions for Color Image Processing" (arXiv 1501.04840):
+ *
+ *   minimise ||J(u, v)||_1  s.t.  S_M m = u,  S_F f + f_b^+ = v,
+ *                                (D_M | D_F)(m, f) = f_b^-          (section 2)
+ *
+ * with the primal-dual iteration of Algorithm 1 (section 3), on a staggered grid
+ * of one to three spatial axes (x, y, colour) with Neumann or periodic boundary
+ * conditions per axis and P time intervals:
+ *   - RGB images: n = {n1, n2, 3}, bc = {NEUMANN, NEUMANN, PERIODIC} (section 1,
+ *     Remark 2: the 4D Poisson problem with periodic colour);
+ *   - hue histograms: ndim = 1, n = {bins}, bc = {PERIODIC} (section 5);
+ *   - grey images / 1D signals: ndim = 2 or 1 with Neumann axes (section 1).
+ *
+ * Array conventions (all float32, C order, slowest index first):
+ *   densities f0, f1 : [c][y][x]               (S = n1*n2*C values per problem)
+ *   path f           : [t][c][y][x], t = 1..P-1 (f at time t/P; section 2)
+ *   path m_k         : [t][c][y][x] with axis k holding n_k - kappa_k faces,
+ *                      t = 1..P (half-times (t-1/2)/P).  Face index i along
+ *                      axis k is the paper's face j = i + kappa_k at position
+ *                      j/n_k: for Neumann axes (kappa = 1) the face right of
+ *                      cell i, for periodic axes (kappa = 0) the face left of
+ *                      cell i (section 2, "Discretization").
+ *   packed path      : m_0 | m_1 | ... | m_{d-1} | f   (the vector (m, f)).
+ *   packed dual      : b_m0 | ... | b_m{d-1} | b_f, each P*S cells [t][c][y][x].
+ * A batch of B problems of one size is stored problem after problem.
+ *
+ * Pointers: every array argument may be host or device memory (unified virtual
+ * addressing; copies use cudaMemcpyDefault).  The caller owns its buffers; the
+ * plan owns its device workspace.  All work is ordered on the plan's stream;
+ * every call returns after its results are in the caller's buffers.
+ *
+ * Errors: every entry point returns an ot_status; ot_last_error() gives a
+ * thread-local message for the last failure on the calling thread.
+ */
+#ifndef DYNOT_H
+#define DYNOT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OT_ABI_VERSION 1
+
+typedef struct ot_plan_s* ot_plan_t;
+
+typedef enum {
+  OT_OK = 0,
+  OT_EINVAL = 1,       /* bad argument or unsupported grid */
+  OT_EMASS = 2,        /* negative / non-finite density or ||f0||_1 != ||f1||_1 */
+  OT_ENOMEM = 3,       /* device allocation failed */
+  OT_ECUDA = 4,        /* a CUDA call failed (message in ot_last_error) */
+  OT_ETIMEOUT = 5,     /* reserved: a device wait exceeded its limit */
+  OT_ENUMERIC = 6,     /* NaN or Inf in a residual */
+  OT_ENOTCONV = 7,     /* iteration budget spent before the tolerance; results valid */
+  OT_EUNSUPPORTED = 8  /* grid shape outside what the kernels implement */
+} ot_status;
+
+typedef enum { OT_BC_PERIODIC = 0, OT_BC_NEUMANN = 1 } ot_bc; /* kappa of section 2 */
+
+typedef enum {
+  OT_PREC_MIXED = 0, /* FP32 stencils/transforms/prox; FP64 low-mode divide and reductions */
+  OT_PREC_FP32 = 1,  /* as MIXED but every eigenvalue divide in FP32 */
+  OT_PREC_FP64 = 2   /* every kernel in FP64 */
+} ot_precision;
+
+typedef struct {
+  int ndim;              /* spatial axes: 1 (hue / 1D), 2 (grey), 3 (x, y, colour) */
+  int n[3];              /* cells per axis; unused axes are ignored */
+  int bc[3];             /* ot_bc per axis */
+  int P;                 /* time intervals p (2..64) */
+  double sigma;          /* step 2 parameter; 0 selects the default 0.3 */
+  double tau;            /* step 1 parameter, tau*sigma < 1 (Algorithm 1); 0 => 0.99/sigma */
+  double axis_scale[3];  /* factor of D_n per axis; 0 => n[k] (the unit cube, eq. (cont_model)) */
+  int precision;         /* ot_precision */
+  int check_every;       /* iterations between residual checks in ot_solve (0 => 10) */
+  double lam_fp64;       /* MIXED: eigenvalues below this are divided in FP64 (0 => 64) */
+} ot_grid;
+
+typedef struct {
+  int iterations;        /* iterations performed */
+  double residual;       /* ||b^{r+1} - b^r|| / ||K x^{r+1} + (0, f_b^+)|| at the last check */
+  double energy;         /* (1/#cells) sum J(u, v) in the caller's density units */
+  double mass_drift;     /* max_t |sum_x f(t) - M| / M over the interior times */
+  double elapsed_ms;     /* device time of the call (CUDA events) */
+} ot_solve_stats;
+
+/* Fill *g with the defaults for an RGB grid n1 x n2 x 3 with P time intervals. */
+void ot_grid_rgb(ot_grid* g, int n1, int n2, int P);
+/* Fill *g with the defaults for a periodic hue histogram of `bins` bins. */
+void ot_grid_hue(ot_grid* g, int bins, int P);
+
+/*
+ * Create a plan for `batch` problems of the shape *g, ordered on `cuda_stream`
+ * (a cudaStream_t; NULL => the plan creates its own stream).  Allocates the
+ * device workspace on the current device.  Returns OT_EINVAL / OT_EUNSUPPORTED
+ * for grids the kernels do not cover, OT_ENOMEM when allocation fails.
+ */
+ot_status ot_plan(const ot_grid* g, int batch, void* cuda_stream, ot_plan_t* out);
+
+/* Release the plan and its device memory.  NULL is ignored. */
+void ot_destroy(ot_plan_t p);
+
+/*
+ * Solve Algorithm 1 for the pairs (f0, f1) (batch x S values each).
+ * Validates f >= 0, finite, and | ||f0||_1 - ||f1||_1 | <= 1e-6 max(...) per pair
+ * (section 2 requires equal masses; section 4 rescales images to reach it),
+ * otherwise returns OT_EMASS.  Internally every pair is rescaled to mean
+ * density 1 and the path is scaled back by the mean of the two masses over S.
+ * Starts from x = 0, b = bbar = 0 (Algorithm 1) or, if init_path != NULL, from
+ * x = init_path (packed path in the caller's units) with b = bbar = 0.
+ * Runs until the residual of the last check is <= tol or `iters` iterations
+ * are done (OT_ENOTCONV with valid results in the latter case when tol > 0).
+ * `g` may be NULL (use the plan's grid) or must match the plan's sizes; its
+ * sigma, tau and check_every then apply to this call.  stats may be NULL.
+ */
+ot_status ot_solve(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
+                   const float* init_path, ot_solve_stats* stats);
+
+/*
+ * Copy the primal path x of the last iteration into caller buffers (any of
+ * them may be NULL): f, and m along axes 0, 1, 2 (in the layout above, caller
+ * units).  For ndim < 3 the unused m pointers are ignored.
+ */
+ot_status ot_path(ot_plan_t p, float* f, float* m0, float* m1, float* m2);
+
+/* Number of floats of the packed path and packed dual per batch (all problems). */
+size_t ot_path_size(ot_plan_t p);
+size_t ot_dual_size(ot_plan_t p);
+
+/*
+ * Checkpoint / resume of the iteration state (x, b, bbar) of Algorithm 1 in
+ * solver units, with the boundary densities f0, f1 used as given (no mass
+ * rescaling).  bbar may be NULL on set (=> bbar = b).
+ */
+ot_status ot_state_set(ot_plan_t p, const float* f0, const float* f1, const float* x_packed,
+                       const float* b_packed, const float* bbar_packed);
+ot_status ot_state_get(ot_plan_t p, float* x_packed, float* b_packed, float* bbar_packed);
+
+/* Run `iters` iterations of Algorithm 1 from the current state; stats may be NULL. */
+ot_status ot_iterate(ot_plan_t p, int iters, ot_solve_stats* stats);
+
+/*
+ * Step 1 of Algorithm 1 alone: x = Pi_{C_d}(a) = a - A^T (A A^T)^+ (A a - f_b^-)
+ * (section 3), for a packed path a and boundary densities f0, f1 used as given.
+ * phi (P*S per problem, NULL allowed) receives (A A^T)^+ (A a - f_b^-).
+ */
+ot_status ot_project(ot_plan_t p, const float* f0, const float* f1, const float* a_packed, float* x_packed,
+                     float* phi);
+
+/*
+ * Step 2 of Algorithm 1 alone: for each of `count` cells,
+ *   (u, v) = argmin |u|^2/(2v) + sigma/2 |u - a_m|^2 + sigma/2 (v - a_f)^2
+ * (section 3).  a_m holds ncomp (1..3) components of `count` values each
+ * (component-major), u likewise; FP32 on the device.
+ */
+ot_status ot_prox(int count, int ncomp, double sigma, const float* a_m, const float* a_f, float* u, float* v);
+
+/*
+ * Measurement: run `iters` iterations with CUDA events around every kernel and
+ * return the mean device time per launch in ms: ms[0..3] = the four kernels of
+ * an iteration (rhs + forward x/t transform, y/colour solve, inverse x/t
+ * transform, update), ms[4] = one whole iteration replayed from a CUDA graph.
+ * The state advances.  `names` (may be NULL) receives a static string naming
+ * the kernels.
+ */
+ot_status ot_profile(ot_plan_t p, int iters, double ms[5], const char** names);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* ot_last_error(void);
+
+/* Version of this ABI (OT_ABI_VERSION). */
+int ot_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DYNOT_H */

@@ -1,0 +1,255 @@
+// Host side of the C ABI declared in include/dynot.h: plans, workspace,
+// transform tables, kernel selection, the iteration driver with CUDA graphs,
+// residual checks and the checkpoint / single-step entry points.
+#include "../../include/dynot.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "plan_base.h"
+
+using namespace dynot;
+
+namespace dynot {
+
+namespace {
+thread_local std::string t_err;
+}
+
+ot_status seterr(ot_status s, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return s;
+}
+
+}  // namespace dynot
+
+namespace {
+
+ot_status make_compact(PlanBase& P) {
+  Compact& c = P.cp;
+  c.n[0] = P.n1; c.n[1] = P.n2; c.n[2] = P.C;
+  c.per[0] = P.grid.bc[0] == OT_BC_PERIODIC;
+  c.per[1] = P.d >= 2 && P.grid.bc[1] == OT_BC_PERIODIC;
+  c.per[2] = P.d >= 3 && P.grid.bc[2] == OT_BC_PERIODIC;
+  c.P = P.P;
+  c.d = P.d;
+  long long off = 0;
+  for (int k = 0; k < 3; ++k) {
+    c.off[k] = off;
+    if (k < P.d) {
+      long long dims = 1;
+      for (int j = 0; j < 3; ++j) dims *= (j == k) ? (c.per[k] ? c.n[j] : c.n[j] - 1) : c.n[j];
+      c.len[k] = dims * P.P;
+    } else {
+      c.len[k] = 0;
+    }
+    off += c.len[k];
+  }
+  c.off[3] = off;
+  c.len[3] = (long long)(P.P - 1) * P.S;
+  c.total = off + c.len[3];
+  return OT_OK;
+}
+
+ot_status validate(const ot_grid* gi, int batch, ot_grid& g) {
+  if (!gi) return seterr(OT_EINVAL, "grid is NULL");
+  g = *gi;
+  if (g.ndim < 1 || g.ndim > 3) return seterr(OT_EINVAL, "ndim must be 1, 2 or 3");
+  if (batch < 1) return seterr(OT_EINVAL, "batch must be >= 1");
+  for (int k = 0; k < g.ndim; ++k) {
+    if (g.n[k] < 1) return seterr(OT_EINVAL, "n[%d] must be >= 1", k);
+    if (g.bc[k] != OT_BC_PERIODIC && g.bc[k] != OT_BC_NEUMANN) return seterr(OT_EINVAL, "bc[%d] invalid", k);
+    if (g.axis_scale[k] == 0) g.axis_scale[k] = g.n[k];
+    if (!(g.axis_scale[k] > 0)) return seterr(OT_EINVAL, "axis_scale[%d] must be > 0", k);
+  }
+  for (int k = g.ndim; k < 3; ++k) {
+    g.n[k] = 1;
+    g.bc[k] = OT_BC_NEUMANN;
+    g.axis_scale[k] = 1;
+  }
+  if (g.P < 2 || g.P > 64) return seterr(OT_EUNSUPPORTED, "P must be in [2, 64]");
+  if (g.sigma == 0) g.sigma = 0.3;
+  if (g.tau == 0) g.tau = 0.99 / g.sigma;
+  if (!(g.sigma > 0) || !(g.tau > 0) || !(g.tau * g.sigma < 1))
+    return seterr(OT_EINVAL, "need sigma > 0, tau > 0, tau*sigma < 1 (Algorithm 1)");
+  if (g.check_every <= 0) g.check_every = 10;
+  if (g.lam_fp64 <= 0) g.lam_fp64 = 64.0;
+  if (g.precision < 0 || g.precision > 2) return seterr(OT_EINVAL, "precision invalid");
+  const bool hue = g.ndim == 1 && g.bc[0] == OT_BC_PERIODIC;
+  if (!hue) {
+    if (g.ndim >= 1 && g.bc[0] == OT_BC_PERIODIC) return seterr(OT_EUNSUPPORTED, "periodic x axis needs ndim == 1");
+    if (g.ndim >= 2 && g.bc[1] == OT_BC_PERIODIC) return seterr(OT_EUNSUPPORTED, "periodic y axis is not implemented");
+    if (g.n[2] > dynot::kMaxC) return seterr(OT_EUNSUPPORTED, "colour axis longer than %d", kMaxC);
+    if (g.n[0] < 2) return seterr(OT_EUNSUPPORTED, "n[0] must be >= 2");
+    if (g.n[0] > 4096 || g.n[1] > 4096) return seterr(OT_EUNSUPPORTED, "axes longer than 4096");
+  } else {
+    if (g.n[0] < 2 || g.n[0] > 8192) return seterr(OT_EUNSUPPORTED, "hue bins must be in [2, 8192]");
+  }
+  return OT_OK;
+}
+
+}  // namespace
+
+struct ot_plan_s {
+  std::unique_ptr<PlanBase> impl;
+};
+
+extern "C" {
+
+void ot_grid_rgb(ot_grid* g, int n1, int n2, int P) {
+  if (!g) return;
+  std::memset(g, 0, sizeof *g);
+  g->ndim = 3;
+  g->n[0] = n1; g->n[1] = n2; g->n[2] = 3;
+  g->bc[0] = OT_BC_NEUMANN; g->bc[1] = OT_BC_NEUMANN; g->bc[2] = OT_BC_PERIODIC;
+  g->P = P;
+  g->sigma = 0.3;
+  g->tau = 0.99 / 0.3;
+  g->precision = OT_PREC_MIXED;
+  g->check_every = 10;
+  g->lam_fp64 = 64.0;
+}
+
+void ot_grid_hue(ot_grid* g, int bins, int P) {
+  if (!g) return;
+  ot_grid_rgb(g, bins, 1, P);
+  g->ndim = 1;
+  g->n[1] = g->n[2] = 1;
+  g->bc[0] = OT_BC_PERIODIC;
+}
+
+ot_status ot_plan(const ot_grid* gi, int batch, void* cuda_stream, ot_plan_t* out) {
+  if (!out) return seterr(OT_EINVAL, "out is NULL");
+  *out = nullptr;
+  ot_grid g;
+  OT_TRY(validate(gi, batch, g));
+  std::unique_ptr<PlanBase> impl;
+  if (g.precision == OT_PREC_FP64) impl.reset(new_plan_f64());
+  else impl.reset(new_plan_f32());
+  PlanBase& P = *impl;
+  P.grid = g;
+  P.B = batch;
+  P.d = g.ndim;
+  P.n1 = g.n[0]; P.n2 = g.n[1]; P.C = g.n[2];
+  P.P = g.P;
+  P.S = P.n1 * P.n2 * P.C;
+  P.N = (long long)P.P * P.S;
+  P.hue = g.ndim == 1 && g.bc[0] == OT_BC_PERIODIC;
+  if (cuda_stream) {
+    P.st = (cudaStream_t)cuda_stream;
+  } else {
+    CUDA_OK(cudaStreamCreateWithFlags(&P.st, cudaStreamNonBlocking));
+    P.own_stream = true;
+  }
+  OT_TRY(make_compact(P));
+  OT_TRY(P.init());
+  CUDA_OK(cudaStreamSynchronize(P.st));
+  ot_plan_s* h = new ot_plan_s;
+  h->impl = std::move(impl);
+  *out = h;
+  return OT_OK;
+}
+
+void ot_destroy(ot_plan_t p) {
+  if (!p) return;
+  if (p->impl && p->impl->st) cudaStreamSynchronize(p->impl->st);
+  delete p;
+}
+
+ot_status ot_solve(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
+                   const float* init_path, ot_solve_stats* stats) {
+  if (!p) return seterr(OT_EINVAL, "plan is NULL");
+  PlanBase& P = *p->impl;
+  if (g) {
+    if (g->ndim != P.grid.ndim || g->P != P.grid.P)
+      return seterr(OT_EINVAL, "grid does not match the plan");
+    for (int k = 0; k < g->ndim; ++k)
+      if (g->n[k] != P.grid.n[k] || g->bc[k] != P.grid.bc[k]) return seterr(OT_EINVAL, "grid does not match the plan");
+    const double sg = g->sigma > 0 ? g->sigma : P.grid.sigma;
+    const double ta = g->tau > 0 ? g->tau : 0.99 / sg;
+    if (!(sg * ta < 1)) return seterr(OT_EINVAL, "need tau*sigma < 1");
+    if (sg != P.grid.sigma || ta != P.grid.tau)
+      return seterr(OT_EINVAL, "sigma/tau differ from the plan's; create a plan with them");
+    if (g->check_every > 0) P.grid.check_every = g->check_every;
+  }
+  return P.solve(f0, f1, iters, tol, init_path, stats);
+}
+
+ot_status ot_path(ot_plan_t p, float* f, float* m0, float* m1, float* m2) {
+  if (!p) return seterr(OT_EINVAL, "plan is NULL");
+  return p->impl->path(f, m0, m1, m2);
+}
+
+size_t ot_path_size(ot_plan_t p) { return p ? (size_t)p->impl->B * p->impl->cp.total : 0; }
+size_t ot_dual_size(ot_plan_t p) {
+  return p ? (size_t)p->impl->B * (p->impl->d + 1) * (size_t)p->impl->N : 0;
+}
+
+ot_status ot_state_set(ot_plan_t p, const float* f0, const float* f1, const float* x, const float* b,
+                       const float* bb) {
+  if (!p) return seterr(OT_EINVAL, "plan is NULL");
+  return p->impl->state_set(f0, f1, x, b, bb);
+}
+
+ot_status ot_state_get(ot_plan_t p, float* x, float* b, float* bb) {
+  if (!p) return seterr(OT_EINVAL, "plan is NULL");
+  return p->impl->state_get(x, b, bb);
+}
+
+ot_status ot_iterate(ot_plan_t p, int iters, ot_solve_stats* stats) {
+  if (!p) return seterr(OT_EINVAL, "plan is NULL");
+  return p->impl->iterate(iters, stats);
+}
+
+ot_status ot_project(ot_plan_t p, const float* f0, const float* f1, const float* a, float* x, float* phi) {
+  if (!p) return seterr(OT_EINVAL, "plan is NULL");
+  return p->impl->project(f0, f1, a, x, phi);
+}
+
+ot_status ot_prox(int count, int ncomp, double sigma, const float* am, const float* af, float* u, float* v) {
+  if (count < 0 || ncomp < 1 || ncomp > 3 || !(sigma > 0)) return seterr(OT_EINVAL, "bad prox arguments");
+  if (count == 0) return OT_OK;
+  if (!am || !af || !u || !v) return seterr(OT_EINVAL, "NULL prox buffer");
+  const size_t n = (size_t)count;
+  DevMem m;
+  CUDA_OK(cudaMalloc(&m.p, sizeof(float) * n * (2 * ncomp + 2)));
+  float* dam = (float*)m.p;
+  float* daf = dam + n * ncomp;
+  float* du = daf + n;
+  float* dv = du + n * ncomp;
+  CUDA_OK(cudaMemcpy(dam, am, sizeof(float) * n * ncomp, cudaMemcpyDefault));
+  CUDA_OK(cudaMemcpy(daf, af, sizeof(float) * n, cudaMemcpyDefault));
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+  k_prox_cells<<<blocks, 256>>>(count, ncomp, (float)sigma, dam, daf, du, dv);
+  CUDA_OK(cudaGetLastError());
+  CUDA_OK(cudaMemcpy(u, du, sizeof(float) * n * ncomp, cudaMemcpyDefault));
+  CUDA_OK(cudaMemcpy(v, dv, sizeof(float) * n, cudaMemcpyDefault));
+  return OT_OK;
+}
+
+ot_status ot_profile(ot_plan_t p, int iters, double ms[5], const char** names) {
+  if (!p || !ms) return seterr(OT_EINVAL, "plan or ms is NULL");
+  if (names)
+    *names = p->impl->hue ? "hue_fwd,hue_t,hue_inv,update,iteration"
+                          : "rhs_fwd_xt,solve_yc,inv_xt,update,iteration";
+  return p->impl->profile(iters, ms);
+}
+
+const char* ot_last_error(void) { return t_err.c_str(); }
+
+int ot_abi_version(void) { return OT_ABI_VERSION; }
+
+}  // extern "C"

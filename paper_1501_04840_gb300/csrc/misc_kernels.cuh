@@ -1,0 +1,236 @@
+// Data-movement kernels around the iteration: input validation, mass
+// rescaling (section 4), conversion between the paper's compact face layout
+// (section 2) and the cell-aligned internal layout, the step-1 operand
+// a = x - tau sigma K^T bbar, the projection correction x = a - A^T phi, and
+// the per-cell prox entry point.
+#pragma once
+#include "common.cuh"
+#include "rgb_kernels.cuh"
+
+namespace dynot {
+
+// Per pair: [0] sum f0, [1] sum f1, [2] min f0, [3] min f1, [4] non-finite count (doubles).
+constexpr int kChk = 5;
+
+static __global__ void k_check_inputs(const float* __restrict__ f0, const float* __restrict__ f1, int S,
+                               double* __restrict__ out) {
+  const int b = blockIdx.y;
+  double s0 = 0, s1 = 0, bad = 0;
+  float m0 = INFINITY, m1 = INFINITY;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x) {
+    const float a = f0[(size_t)b * S + i], c = f1[(size_t)b * S + i];
+    if (!isfinite(a) || !isfinite(c)) bad += 1;
+    s0 += a;
+    s1 += c;
+    m0 = fminf(m0, a);
+    m1 = fminf(m1, c);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    m0 = fminf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fminf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  __shared__ double sh[32][5];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sh[w][0] = s0; sh[w][1] = s1; sh[w][2] = m0; sh[w][3] = m1; sh[w][4] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0, a1 = 0, mm0 = INFINITY, mm1 = INFINITY, bb = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a0 += sh[i][0]; a1 += sh[i][1]; bb += sh[i][4];
+      mm0 = fmin(mm0, sh[i][2]); mm1 = fmin(mm1, sh[i][3]);
+    }
+    double* o = out + (size_t)b * kChk;
+    atomicAdd(&o[0], a0);
+    atomicAdd(&o[1], a1);
+    atomicAdd(&o[4], bb);
+    // min via compare-and-swap on the bit pattern of non-negative doubles is not
+    // order preserving for negatives; use a loop on the double value instead
+    for (int q = 2; q <= 3; ++q) {
+      const double v = q == 2 ? mm0 : mm1;
+      unsigned long long* addr = (unsigned long long*)&o[q];
+      unsigned long long old = *addr, assumed;
+      do {
+        assumed = old;
+        if (__longlong_as_double(assumed) <= v) break;
+        old = atomicCAS(addr, assumed, __double_as_longlong(v));
+      } while (assumed != old);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scale_boundary(const float* __restrict__ f0, const float* __restrict__ f1, int S,
+                                 const double* __restrict__ sc, T* __restrict__ g0, T* __restrict__ g1) {
+  const int b = blockIdx.y;
+  const double s0 = sc[2 * b], s1 = sc[2 * b + 1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x) {
+    g0[(size_t)b * S + i] = (T)((double)f0[(size_t)b * S + i] * s0);
+    g1[(size_t)b * S + i] = (T)((double)f1[(size_t)b * S + i] * s1);
+  }
+}
+
+// Compact layout of component k (0..2 faces, 3 = f) of one problem; returns the
+// compact index of the internal slot (t, x, y, c) or -1 if the slot is not a
+// variable of the model (Neumann boundary face, f at slot P-1).
+struct Compact {
+  int n[3], per[3], P, d;
+  long long off[4];   // offsets of m_0, m_1, m_2, f inside one problem's packed path
+  long long len[4];
+  long long total;    // packed floats per problem
+
+  __host__ __device__ long long index(int k, int t, int x, int y, int c) const {
+    int i[3] = {x, y, c};
+    int dim[3] = {n[0], n[1], n[2]};
+    if (k == 3) {
+      if (t >= P - 1) return -1;
+    } else {
+      if (k >= d) return -1;
+      if (per[k]) {
+        i[k] = (i[k] + 1) % n[k];   // internal face right of cell i = paper face i + 1
+      } else {
+        if (i[k] == n[k] - 1) return -1;
+        dim[k] = n[k] - 1;
+      }
+    }
+    return off[k] + i[0] + (long long)dim[0] * (i[1] + (long long)dim[1] * (i[2] + (long long)dim[2] * t));
+  }
+};
+
+// internal (T, scaled by inv) <- packed (float)
+template <typename T>
+__global__ void k_unpack_path(Geo<T> g, Compact cp, const float* __restrict__ packed, double scale,
+                              T* x0, T* x1, T* x2, T* x3) {
+  const long long tot = (long long)g.B * g.N;
+  T* xs[4] = {x0, x1, x2, x3};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    const int x = r % g.n1; r /= g.n1;
+    const int y = r % g.n2; r /= g.n2;
+    const int c = r % g.C; r /= g.C;
+    const int t = r % g.P;
+    const int b = (int)(r / g.P);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long ci = cp.index(k, t, x, y, c);
+      xs[k][id] = ci < 0 ? T(0) : (T)((double)packed[(long long)b * cp.total + ci] * scale);
+    }
+  }
+}
+
+// packed (float, times scale) <- internal; dst[k] may be separate arrays (stride per problem lenk)
+template <typename T>
+__global__ void k_pack_path(Geo<T> g, Compact cp, const T* x0, const T* x1, const T* x2, const T* x3, double scale,
+                            float* __restrict__ packed, float* d0, float* d1, float* d2, float* d3) {
+  const long long tot = (long long)g.B * g.N;
+  const T* xs[4] = {x0, x1, x2, x3};
+  float* ds[4] = {d0, d1, d2, d3};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    const int x = r % g.n1; r /= g.n1;
+    const int y = r % g.n2; r /= g.n2;
+    const int c = r % g.C; r /= g.C;
+    const int t = r % g.P;
+    const int b = (int)(r / g.P);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long ci = cp.index(k, t, x, y, c);
+      if (ci < 0) continue;
+      const float v = (float)((double)xs[k][id] * scale);
+      if (packed) packed[(long long)b * cp.total + ci] = v;
+      if (ds[k]) ds[k][(long long)b * cp.len[k] + ci - cp.off[k]] = v;
+    }
+  }
+}
+
+// a = x - tau sigma K^T bbar at the right faces (step 1 of Algorithm 1).
+template <typename T>
+__global__ void k_make_a(Geo<T> g, CPtr4<T> x, CPtr4<T> bb, T* a0, T* a1, T* a2, T* a3) {
+  const long long tot = (long long)g.B * g.N;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    const int ix = r % g.n1; r /= g.n1;
+    const int iy = r % g.n2; r /= g.n2;
+    const int ic = r % g.C; r /= g.C;
+    const int t = r % g.P;
+    const int b = (int)(r / g.P);
+    T out[4];
+    // x axis
+    {
+      int j = ix + 1;
+      bool ok = true;
+      if (j == g.n1) { ok = g.per1; j = 0; }
+      out[0] = ok ? x.p[0][id] - g.ts * T(0.5) * (bb.p[0][id] + bb.p[0][cidx(g, b, t, j, iy, ic)]) : T(0);
+    }
+    {
+      int j = iy + 1;
+      bool ok = true;
+      if (j == g.n2) { ok = g.per2; j = 0; }
+      out[1] = ok ? x.p[1][id] - g.ts * T(0.5) * (bb.p[1][id] + bb.p[1][cidx(g, b, t, ix, j, ic)]) : T(0);
+    }
+    {
+      int j = ic + 1;
+      bool ok = true;
+      if (j == g.C) { ok = g.perc; j = 0; }
+      out[2] = ok ? x.p[2][id] - g.ts * T(0.5) * (bb.p[2][id] + bb.p[2][cidx(g, b, t, ix, iy, j)]) : T(0);
+    }
+    out[3] = (t + 1 < g.P) ? x.p[3][id] - g.ts * T(0.5) * (bb.p[3][id] + bb.p[3][cidx(g, b, t + 1, ix, iy, ic)]) : T(0);
+    a0[id] = out[0];
+    a1[id] = out[1];
+    a2[id] = out[2];
+    a3[id] = out[3];
+  }
+}
+
+// x = a - A^T phi at the right faces (the correction of the projection).
+template <typename T>
+__global__ void k_correct(Geo<T> g, Arrays<T> A) {
+  const long long tot = (long long)g.B * g.N;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    const int ix = r % g.n1; r /= g.n1;
+    const int iy = r % g.n2; r /= g.n2;
+    const int ic = r % g.C; r /= g.C;
+    const int t = r % g.P;
+    const int b = (int)(r / g.P);
+    CellCtx<T> cc{g, A, b};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) A.x[k][id] = cc.xr(k, t, ix, iy, ic);
+  }
+}
+
+// bbar = 2 b - bprev and type conversion helpers
+template <typename T>
+__global__ void k_axpby(long long n, T alpha, const T* __restrict__ x, T beta, const T* __restrict__ y,
+                        T* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = alpha * x[i] + (y ? beta * y[i] : T(0));
+}
+
+template <typename To, typename Ti>
+__global__ void k_convert(long long n, const Ti* __restrict__ in, To* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (To)in[i];
+}
+
+static __global__ void k_prox_cells(int count, int ncomp, float sigma, const float* __restrict__ am,
+                             const float* __restrict__ af, float* __restrict__ u, float* __restrict__ v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const float a0 = am[i];
+    const float a1 = ncomp > 1 ? am[(size_t)count + i] : 0.f;
+    const float a2 = ncomp > 2 ? am[2 * (size_t)count + i] : 0.f;
+    float u0, u1, u2, vv;
+    prox_J<float>(a0, a1, a2, af[i], sigma, u0, u1, u2, vv);
+    u[i] = u0;
+    if (ncomp > 1) u[(size_t)count + i] = u1;
+    if (ncomp > 2) u[2 * (size_t)count + i] = u2;
+    v[i] = vv;
+  }
+}
+
+}  // namespace dynot

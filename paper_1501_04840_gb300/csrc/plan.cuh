@@ -1,0 +1,745 @@
+// Templated plan: workspace, transform tables, kernel selection and the
+// iteration driver, instantiated for float (plan_f32.cu) and double (plan_f64.cu).
+#pragma once
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fft.cuh"
+#include "hue_kernels.cuh"
+#include "misc_kernels.cuh"
+#include "plan_base.h"
+#include "rgb_kernels.cuh"
+
+namespace dynot {
+
+constexpr int kThreadsXt = 256;
+constexpr int kThreadsUpd = 128;
+constexpr int kW = 16;  // x-strip width of the y/colour pass
+
+inline int pmax_for(int P) { return P <= 16 ? 16 : (P <= 32 ? 32 : 64); }
+inline bool fft_len(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+inline int fft_n1(int n) { return n == 64 ? 8 : (n == 128 ? 8 : 16); }
+
+inline size_t rnd16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// --------------------------------------------------------------------------
+// kernel selection
+// --------------------------------------------------------------------------
+template <typename T> using KA = void (*)(Geo<T>, CPtr4<T>, const T*, const T*, T*, XtTables, int);
+template <typename T> using KC = void (*)(Geo<T>, const T*, T*, XtTables, int);
+template <typename T> using KB = void (*)(Geo<T>, T*, YcTables, int);
+template <typename T> using KH = void (*)(Geo<T>, T*, HueTables);
+
+template <typename T, int PM>
+KA<T> pick_ka_p(int n) {
+  switch (n) {
+    case 64: return k_rhs_fwd_xt<T, 8, 8, PM>;
+    case 128: return k_rhs_fwd_xt<T, 8, 16, PM>;
+    case 256: return k_rhs_fwd_xt<T, 16, 16, PM>;
+    case 512: return k_rhs_fwd_xt<T, 16, 32, PM>;
+    default: return k_rhs_fwd_xt<T, 0, 0, PM>;
+  }
+}
+template <typename T>
+KA<T> pick_ka(int n, int pm) {
+  return pm == 16 ? pick_ka_p<T, 16>(n) : (pm == 32 ? pick_ka_p<T, 32>(n) : pick_ka_p<T, 64>(n));
+}
+template <typename T, int PM>
+KC<T> pick_kc_p(int n) {
+  switch (n) {
+    case 64: return k_inv_xt<T, 8, 8, PM>;
+    case 128: return k_inv_xt<T, 8, 16, PM>;
+    case 256: return k_inv_xt<T, 16, 16, PM>;
+    case 512: return k_inv_xt<T, 16, 32, PM>;
+    default: return k_inv_xt<T, 0, 0, PM>;
+  }
+}
+template <typename T>
+KC<T> pick_kc(int n, int pm) {
+  return pm == 16 ? pick_kc_p<T, 16>(n) : (pm == 32 ? pick_kc_p<T, 32>(n) : pick_kc_p<T, 64>(n));
+}
+template <typename T>
+KB<T> pick_kb(int n) {
+  switch (n) {
+    case 64: return k_solve_yc<T, 8, 8, kW>;
+    case 128: return k_solve_yc<T, 8, 16, kW>;
+    case 256: return k_solve_yc<T, 16, 16, kW>;
+    case 512: return k_solve_yc<T, 16, 32, kW>;
+    default: return k_solve_yc<T, 0, 0, kW>;
+  }
+}
+template <typename T>
+KH<T> pick_kh(int pm) {
+  return pm == 16 ? k_hue_t<T, 16> : (pm == 32 ? k_hue_t<T, 32> : k_hue_t<T, 64>);
+}
+
+template <typename T>
+struct Plan final : PlanBase {
+  Geo<T> g{};
+  DevMem mem;           // one allocation for every array
+  T* a[2][4]{};
+  T* b[2][4]{};
+  T* phi = nullptr;
+  T* hat = nullptr;
+  T* x[4]{};
+  T* f0n = nullptr;
+  T* f1n = nullptr;
+  float* stage = nullptr;   // float staging: 2*B*S inputs, then path packing
+  size_t stage_floats = 0;
+  double* acc = nullptr;    // [B][kAcc]
+  double* mass = nullptr;   // [B][P]
+  double* chk = nullptr;    // [B][kChk]
+  double* scl = nullptr;    // [B][2]
+  // transform tables
+  DevMem tabmem;
+  XtTables xt{};
+  YcTables yc{};
+  HueTables ht{};
+  int pmax = 32;
+  int scrA = 0, scrB = 0;
+  size_t smA = 0, smB = 0, smH = 0, smHt = 0;
+  KA<T> ka = nullptr;
+  KC<T> kc = nullptr;
+  KB<T> kb = nullptr;
+  KH<T> kh = nullptr;
+  int par = 0;              // buffer holding the current state
+  bool have_x = false;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  cudaEvent_t ev[12] = {};
+
+  ~Plan() override {
+    for (auto& e : gexec)
+      if (e) cudaGraphExecDestroy(e);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+
+  size_t xt_smem() const {
+    size_t s = rnd16(sizeof(T) * (size_t)(P + 1) * n1) + rnd16(sizeof(c2<T>) * (size_t)scrA) +
+               2 * rnd16(sizeof(c2<T>) * n1) + rnd16(sizeof(T) * (size_t)P * pmax) + rnd16(sizeof(T) * 4 * n1);
+    return s;
+  }
+  size_t yc_smem() const {
+    return rnd16(sizeof(T) * (size_t)C * n2 * kW) + rnd16(sizeof(c2<T>) * (size_t)scrB) +
+           2 * rnd16(sizeof(c2<T>) * n2) + rnd16(sizeof(T) * 4 * n2) + rnd16(sizeof(T) * n2);
+  }
+
+  ot_status init() override {
+    CUDA_OK(cudaGetDevice(&device));
+    pmax = pmax_for(P);
+    g.n1 = n1; g.n2 = n2; g.C = C;
+    g.per1 = grid.bc[0] == OT_BC_PERIODIC;
+    g.per2 = d >= 2 ? grid.bc[1] == OT_BC_PERIODIC : 0;
+    g.perc = d >= 3 ? grid.bc[2] == OT_BC_PERIODIC : 0;
+    g.P = P; g.S = S; g.B = B; g.N = N;
+    g.s1 = (T)grid.axis_scale[0];
+    g.s2 = (T)(d >= 2 ? grid.axis_scale[1] : 1.0);
+    g.sc = (T)(d >= 3 ? grid.axis_scale[2] : 1.0);
+    g.sp = (T)P;
+    g.sigma = (T)grid.sigma;
+    g.ts = (T)(grid.tau * grid.sigma);
+
+    // ---- workspace
+    const size_t cells = (size_t)B * N;
+    const size_t narr = 2 * 4 + 2 * 4 + 2 + 4;
+    // staging holds the inputs (2 B S), a packed path (B total) or a packed dual (B (d+1) N)
+    stage_floats = std::max<size_t>({2 * (size_t)B * S, (size_t)B * cp.total, (size_t)B * (d + 1) * (size_t)N});
+    size_t bytes = narr * rnd16(cells * sizeof(T)) + 2 * rnd16((size_t)B * S * sizeof(T)) +
+                   rnd16(stage_floats * sizeof(float)) + rnd16(sizeof(double) * B * kAcc) +
+                   rnd16(sizeof(double) * (size_t)B * P) + rnd16(sizeof(double) * B * kChk) +
+                   rnd16(sizeof(double) * B * 2);
+    CUDA_OK(cudaMalloc(&mem.p, bytes));
+    char* q = (char*)mem.p;
+    auto take = [&](size_t nb) { char* r = q; q += rnd16(nb); return r; };
+    for (int i = 0; i < 2; ++i)
+      for (int k = 0; k < 4; ++k) a[i][k] = (T*)take(cells * sizeof(T));
+    for (int i = 0; i < 2; ++i)
+      for (int k = 0; k < 4; ++k) b[i][k] = (T*)take(cells * sizeof(T));
+    phi = (T*)take(cells * sizeof(T));
+    hat = (T*)take(cells * sizeof(T));
+    for (int k = 0; k < 4; ++k) x[k] = (T*)take(cells * sizeof(T));
+    f0n = (T*)take((size_t)B * S * sizeof(T));
+    f1n = (T*)take((size_t)B * S * sizeof(T));
+    stage = (float*)take(stage_floats * sizeof(float));
+    acc = (double*)take(sizeof(double) * B * kAcc);
+    mass = (double*)take(sizeof(double) * (size_t)B * P);
+    chk = (double*)take(sizeof(double) * B * kChk);
+    scl = (double*)take(sizeof(double) * B * 2);
+    CUDA_OK(cudaMemsetAsync(mem.p, 0, bytes, st));
+
+    OT_TRY(build_tables());
+    for (auto& e : ev) CUDA_OK(cudaEventCreate(&e));
+    out_scale.assign(B, 1.0);
+    return OT_OK;
+  }
+
+  // ---- transform tables (computed in double on the host)
+  ot_status build_tables() {
+    std::vector<char> h;
+    auto put = [&](const void* src, size_t nb) {
+      size_t off = h.size();
+      h.resize(off + rnd16(nb));
+      std::memcpy(h.data() + off, src, nb);
+      return off;
+    };
+    auto twid = [&](int n, std::vector<T>& tw, std::vector<T>& hw) {
+      tw.resize(2 * n);
+      hw.resize(2 * n);
+      for (int j = 0; j < n; ++j) {
+        tw[2 * j] = (T)std::cos(2 * kPi * j / n);
+        tw[2 * j + 1] = (T)-std::sin(2 * kPi * j / n);
+        hw[2 * j] = (T)std::cos(kPi * j / (2.0 * n));
+        hw[2 * j + 1] = (T)-std::sin(kPi * j / (2.0 * n));
+      }
+    };
+    auto cos4 = [&](int n) {
+      std::vector<T> c(4 * n);
+      for (int m = 0; m < 4 * n; ++m) c[m] = (T)std::cos(kPi * m / (2.0 * n));
+      return c;
+    };
+    auto neu_lam = [&](int n, double s) {
+      std::vector<double> l(n);
+      for (int j = 0; j < n; ++j) {
+        const double v = std::sin(kPi * j / (2.0 * n));
+        l[j] = s * s * 4.0 * v * v;
+      }
+      return l;
+    };
+    auto toT = [&](const std::vector<double>& v) {
+      std::vector<T> r(v.size());
+      for (size_t i = 0; i < v.size(); ++i) r[i] = (T)v[i];
+      return r;
+    };
+    // time axis: forward and inverse DCT matrices, padded to pmax columns
+    std::vector<T> Mf((size_t)P * pmax, T(0)), Mi((size_t)P * pmax, T(0));
+    for (int k = 0; k < P; ++k)
+      for (int t = 0; t < P; ++t) {
+        const double c = std::cos(kPi * k * (2 * t + 1) / (2.0 * P));
+        Mf[(size_t)k * pmax + t] = (T)c;
+        Mi[(size_t)t * pmax + k] = (T)((k == 0 ? 1.0 : 2.0) / P * c);
+      }
+    const std::vector<double> lt = neu_lam(P, (double)P);
+    const double thr = grid.precision == OT_PREC_MIXED ? grid.lam_fp64 : 0.0;
+
+    size_t o_Mf = put(Mf.data(), Mf.size() * sizeof(T));
+    size_t o_Mi = put(Mi.data(), Mi.size() * sizeof(T));
+    std::vector<T> ltT = toT(lt);
+    size_t o_lt = put(ltT.data(), P * sizeof(T));
+    size_t o_ltd = put(lt.data(), P * sizeof(double));
+
+    size_t o_tw1 = 0, o_hw1 = 0, o_c41 = 0, o_tw2 = 0, o_hw2 = 0, o_c42 = 0, o_l1 = 0, o_l1d = 0, o_l2 = 0,
+           o_l2d = 0, o_Q = 0, o_lc = 0, o_lcd = 0, o_cs = 0, o_hl = 0, o_hld = 0;
+    if (!hue) {
+      std::vector<T> tw, hw;
+      twid(n1, tw, hw);
+      o_tw1 = put(tw.data(), tw.size() * sizeof(T));
+      o_hw1 = put(hw.data(), hw.size() * sizeof(T));
+      std::vector<T> c1 = cos4(n1);
+      o_c41 = put(c1.data(), c1.size() * sizeof(T));
+      twid(n2, tw, hw);
+      o_tw2 = put(tw.data(), tw.size() * sizeof(T));
+      o_hw2 = put(hw.data(), hw.size() * sizeof(T));
+      std::vector<T> c2v = cos4(n2);
+      o_c42 = put(c2v.data(), c2v.size() * sizeof(T));
+      std::vector<double> l1 = neu_lam(n1, grid.axis_scale[0]);
+      std::vector<double> l2 = neu_lam(n2, d >= 2 ? grid.axis_scale[1] : 1.0);
+      std::vector<T> l1T = toT(l1), l2T = toT(l2);
+      o_l1 = put(l1T.data(), n1 * sizeof(T));
+      o_l1d = put(l1.data(), n1 * sizeof(double));
+      o_l2 = put(l2T.data(), n2 * sizeof(T));
+      o_l2d = put(l2.data(), n2 * sizeof(double));
+      // colour axis: orthonormal eigenbasis of its 1D Laplacian
+      std::vector<double> Q((size_t)C * C, 0.0), lc(C, 0.0);
+      const double sc = d >= 3 ? grid.axis_scale[2] : 1.0;
+      if (!g.perc) {  // Neumann: DCT-II basis, eigenvalues 4 sin^2(pi j / 2C)
+        for (int j = 0; j < C; ++j) {
+          const double v = std::sin(kPi * j / (2.0 * C));
+          lc[j] = sc * sc * 4 * v * v;
+          for (int c = 0; c < C; ++c)
+            Q[(size_t)c * C + j] = std::sqrt((j == 0 ? 1.0 : 2.0) / C) * std::cos(kPi * j * (2 * c + 1) / (2.0 * C));
+        }
+      } else {        // periodic: real Fourier basis, eigenvalues 4 sin^2(pi f / C)
+        for (int j = 0; j < C; ++j) {
+          const int f = (j + 1) / 2;
+          const double v = std::sin(kPi * f / C);
+          lc[j] = sc * sc * 4 * v * v;
+          for (int c = 0; c < C; ++c) {
+            double q;
+            if (j == 0) q = 1.0 / std::sqrt((double)C);
+            else if (C % 2 == 0 && j == C - 1) q = ((c & 1) ? -1.0 : 1.0) / std::sqrt((double)C);
+            else if (j & 1) q = std::sqrt(2.0 / C) * std::cos(2 * kPi * f * c / C);
+            else q = std::sqrt(2.0 / C) * std::sin(2 * kPi * f * c / C);
+            Q[(size_t)c * C + j] = q;
+          }
+        }
+      }
+      std::vector<T> QT = toT(Q), lcT = toT(lc);
+      o_Q = put(QT.data(), QT.size() * sizeof(T));
+      o_lc = put(lcT.data(), C * sizeof(T));
+      o_lcd = put(lc.data(), C * sizeof(double));
+    } else {
+      const int n = n1;
+      std::vector<T> cs(2 * n);
+      std::vector<double> hl(n);
+      for (int m = 0; m < n; ++m) {
+        cs[2 * m] = (T)std::cos(2 * kPi * m / n);
+        cs[2 * m + 1] = (T)std::sin(2 * kPi * m / n);
+      }
+      const double s1 = grid.axis_scale[0];
+      for (int slot = 0; slot < n; ++slot) {
+        int j = (slot + 1) / 2;
+        if (n % 2 == 0 && slot == n - 1) j = n / 2;
+        const double v = std::sin(kPi * j / n);
+        hl[slot] = s1 * s1 * 4 * v * v;
+      }
+      std::vector<T> hlT = toT(hl);
+      o_cs = put(cs.data(), cs.size() * sizeof(T));
+      o_hl = put(hlT.data(), n * sizeof(T));
+      o_hld = put(hl.data(), n * sizeof(double));
+    }
+    CUDA_OK(cudaMalloc(&tabmem.p, h.size()));
+    CUDA_OK(cudaMemcpy(tabmem.p, h.data(), h.size(), cudaMemcpyHostToDevice));
+    char* base = (char*)tabmem.p;
+    if (!hue) {
+      xt.tw = base + o_tw1; xt.hw = base + o_hw1; xt.cos4 = base + o_c41;
+      xt.Mt_f = base + o_Mf; xt.Mt_i = base + o_Mi;
+      yc.tw = base + o_tw2; yc.hw = base + o_hw2; yc.cos4 = base + o_c42;
+      yc.lam1 = base + o_l1; yc.lam2 = base + o_l2; yc.lamt = base + o_lt;
+      yc.lam1d = (const double*)(base + o_l1d); yc.lam2d = (const double*)(base + o_l2d);
+      yc.lamtd = (const double*)(base + o_ltd);
+      yc.Qc = base + o_Q; yc.lamc = base + o_lc; yc.lamcd = (const double*)(base + o_lcd);
+      yc.lam_fp64 = thr;
+      scrA = fft_len(n1) ? (kThreadsXt / fft_n1(n1)) * n1 : 4 * n1;
+      scrB = fft_len(n2) ? (kThreadsXt / fft_n1(n2)) * n2 : 4 * n2;
+      ka = pick_ka<T>(n1, pmax);
+      kc = pick_kc<T>(n1, pmax);
+      kb = pick_kb<T>(n2);
+      smA = xt_smem();
+      smB = yc_smem();
+      int maxsm = 0;
+      CUDA_OK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+      if ((int)smA > maxsm || (int)smB > maxsm)
+        return seterr(OT_EUNSUPPORTED, "grid needs %zu / %zu bytes of shared memory per block (max %d)", smA, smB,
+                      maxsm);
+      CUDA_OK(cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+      CUDA_OK(cudaFuncSetAttribute((const void*)kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+      CUDA_OK(cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB));
+    } else {
+      ht.cs = base + o_cs; ht.lam = base + o_hl; ht.lamd = (const double*)(base + o_hld);
+      ht.lamt = base + o_lt; ht.lamtd = (const double*)(base + o_ltd);
+      ht.Mt_f = base + o_Mf; ht.Mt_i = base + o_Mi;
+      ht.lam_fp64 = thr;
+      kh = pick_kh<T>(pmax);
+      smH = rnd16(sizeof(T) * n1) + rnd16(sizeof(c2<T>) * n1);
+      smHt = 2 * sizeof(T) * (size_t)pmax * pmax;
+      CUDA_OK(cudaFuncSetAttribute((const void*)k_hue_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smH));
+      CUDA_OK(cudaFuncSetAttribute((const void*)k_hue_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smH));
+      CUDA_OK(cudaFuncSetAttribute((const void*)kh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smHt));
+    }
+    return OT_OK;
+  }
+
+  Arrays<T> arrays(int p, bool wx) const {
+    Arrays<T> A{};
+    for (int k = 0; k < 4; ++k) {
+      A.a[k] = a[p][k];
+      A.b[k] = b[p][k];
+      A.an[k] = a[1 - p][k];
+      A.bn[k] = b[1 - p][k];
+      A.x[k] = wx ? x[k] : nullptr;
+    }
+    A.phi = phi;
+    A.f0 = f0n;
+    A.f1 = f1n;
+    return A;
+  }
+  CPtr4<T> aptr(int p) const { return CPtr4<T>{{a[p][0], a[p][1], a[p][2], a[p][3]}}; }
+
+  // ---- the Poisson solve phi = (A A^T)^+ (A a - f_b^-) for a in buffer p
+  void enqueue_poisson(int p, cudaEvent_t* evs) {
+    if (!hue) {
+      if (evs) cudaEventRecord(evs[0], st);
+      ka<<<dim3(n2, C, B), kThreadsXt, smA, st>>>(g, aptr(p), f0n, f1n, hat, xt, scrA);
+      if (evs) cudaEventRecord(evs[1], st);
+      kb<<<dim3((n1 + kW - 1) / kW, P, B), kThreadsXt, smB, st>>>(g, hat, yc, scrB);
+      if (evs) cudaEventRecord(evs[2], st);
+      kc<<<dim3(n2, C, B), kThreadsXt, smA, st>>>(g, hat, phi, xt, scrA);
+      if (evs) cudaEventRecord(evs[3], st);
+    } else {
+      if (evs) cudaEventRecord(evs[0], st);
+      k_hue_fwd<T><<<dim3(P, B), 256, smH, st>>>(g, aptr(p), f0n, f1n, hat, ht);
+      if (evs) cudaEventRecord(evs[1], st);
+      kh<<<dim3((n1 + 127) / 128, B), 128, smHt, st>>>(g, hat, ht);
+      if (evs) cudaEventRecord(evs[2], st);
+      k_hue_inv<T><<<dim3(P, B), 256, smH, st>>>(g, hat, phi, ht);
+      if (evs) cudaEventRecord(evs[3], st);
+    }
+  }
+
+  void enqueue_update(int p, bool check, bool wx) {
+    const dim3 grd((n1 + kThreadsUpd - 1) / kThreadsUpd, n2, C * P * B);
+    const Arrays<T> A = arrays(p, wx);
+    if (check) {
+      if (wx) k_update<T, true, true><<<grd, kThreadsUpd, 0, st>>>(g, A, acc, mass);
+      else k_update<T, true, false><<<grd, kThreadsUpd, 0, st>>>(g, A, acc, mass);
+    } else {
+      if (wx) k_update<T, false, true><<<grd, kThreadsUpd, 0, st>>>(g, A, acc, mass);
+      else k_update<T, false, false><<<grd, kThreadsUpd, 0, st>>>(g, A, acc, mass);
+    }
+  }
+
+  void enqueue_iteration(int p, bool check, bool wx, cudaEvent_t* evs = nullptr) {
+    enqueue_poisson(p, evs);
+    enqueue_update(p, check, wx);
+    if (evs) cudaEventRecord(evs[4], st);
+  }
+
+  ot_status graph_for(int p) {
+    if (gexec[p]) return OT_OK;
+    cudaGraph_t gr = nullptr;
+    CUDA_OK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(p, false, false);
+    enqueue_iteration(1 - p, false, false);
+    cudaError_t e = cudaStreamEndCapture(st, &gr);
+    if (e != cudaSuccess) return seterr(OT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&gexec[p], gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return seterr(OT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return OT_OK;
+  }
+
+  // plain iterations (no residual, no x output), pairs from a graph
+  ot_status run_plain(int n) {
+    while (n >= 2) {
+      OT_TRY(graph_for(par));
+      CUDA_OK(cudaGraphLaunch(gexec[par], st));
+      n -= 2;
+    }
+    if (n == 1) {
+      enqueue_iteration(par, false, false);
+      CUDA_OK(cudaGetLastError());
+      par ^= 1;
+    }
+    return OT_OK;
+  }
+
+  struct Check {
+    double residual = 0, energy = 0, drift = 0;
+  };
+
+  // one iteration with residuals (and x output), read back on the host
+  ot_status run_check(bool wx, Check& out) {
+    CUDA_OK(cudaMemsetAsync(acc, 0, sizeof(double) * B * kAcc, st));
+    CUDA_OK(cudaMemsetAsync(mass, 0, sizeof(double) * (size_t)B * P, st));
+    enqueue_iteration(par, true, wx);
+    CUDA_OK(cudaGetLastError());
+    par ^= 1;
+    if (wx) have_x = true;
+    std::vector<double> hacc((size_t)B * kAcc), hm((size_t)B * P);
+    CUDA_OK(cudaMemcpyAsync(hacc.data(), acc, hacc.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaMemcpyAsync(hm.data(), mass, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaStreamSynchronize(st));
+    out = Check{};
+    for (int bi = 0; bi < B; ++bi) {
+      const double* q = &hacc[(size_t)bi * kAcc];
+      const double res = std::sqrt(q[0]) / std::max(std::sqrt(q[1]), 1e-300);
+      if (!std::isfinite(res) || !std::isfinite(q[2]))
+        return seterr(OT_ENUMERIC, "non-finite residual in problem %d", bi);
+      out.residual = std::max(out.residual, res);
+      out.energy += q[2] / (double)N * out_scale[bi] / B;
+      double M = 0;
+      for (int t = 0; t + 1 < P; ++t) M = std::max(M, std::fabs(hm[(size_t)bi * P + t] - (double)S));
+      out.drift = std::max(out.drift, M / (double)S);
+    }
+    return OT_OK;
+  }
+
+  ot_status drive(int iters, double tol, int check_every, ot_solve_stats* stats) {
+    if (iters < 1) return seterr(OT_EINVAL, "iters must be >= 1");
+    CUDA_OK(cudaEventRecord(ev[10], st));
+    int done = 0;
+    Check ck;
+    bool converged = false;
+    const int K = check_every > 0 ? check_every : iters;
+    while (done < iters) {
+      const int chunk = std::min(K, iters - done);
+      OT_TRY(run_plain(chunk - 1));
+      const bool last = (done + chunk == iters);
+      OT_TRY(run_check(true, ck));
+      done += chunk;
+      if (tol > 0 && ck.residual <= tol) {
+        converged = true;
+        break;
+      }
+      (void)last;
+    }
+    CUDA_OK(cudaEventRecord(ev[11], st));
+    CUDA_OK(cudaEventSynchronize(ev[11]));
+    float ms = 0;
+    CUDA_OK(cudaEventElapsedTime(&ms, ev[10], ev[11]));
+    if (stats) {
+      stats->iterations = done;
+      stats->residual = ck.residual;
+      stats->energy = ck.energy;
+      stats->mass_drift = ck.drift;
+      stats->elapsed_ms = ms;
+    }
+    if (tol > 0 && !converged) return seterr(OT_ENOTCONV, "residual %.3e > tol %.3e after %d iterations",
+                                             ck.residual, tol, done);
+    return OT_OK;
+  }
+
+  // ---- inputs
+  ot_status load_boundary(const float* f0, const float* f1, bool normalise) {
+    const size_t n = (size_t)B * S;
+    CUDA_OK(cudaMemcpyAsync(stage, f0, n * sizeof(float), cudaMemcpyDefault, st));
+    CUDA_OK(cudaMemcpyAsync(stage + n, f1, n * sizeof(float), cudaMemcpyDefault, st));
+    std::vector<double> sc(2 * B, 1.0);
+    if (normalise) {
+      CUDA_OK(cudaMemsetAsync(chk, 0, sizeof(double) * B * kChk, st));
+      // minima start at +inf
+      std::vector<double> init((size_t)B * kChk, 0.0);
+      for (int bi = 0; bi < B; ++bi) init[(size_t)bi * kChk + 2] = init[(size_t)bi * kChk + 3] = INFINITY;
+      CUDA_OK(cudaMemcpyAsync(chk, init.data(), init.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      const int blocks = std::min(1024, (S + 255) / 256);
+      k_check_inputs<<<dim3(blocks, B), 256, 0, st>>>(stage, stage + n, S, chk);
+      CUDA_OK(cudaGetLastError());
+      std::vector<double> h((size_t)B * kChk);
+      CUDA_OK(cudaMemcpyAsync(h.data(), chk, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CUDA_OK(cudaStreamSynchronize(st));
+      for (int bi = 0; bi < B; ++bi) {
+        const double* q = &h[(size_t)bi * kChk];
+        if (q[4] > 0) return seterr(OT_EMASS, "problem %d: non-finite density values", bi);
+        if (q[2] < 0 || q[3] < 0) return seterr(OT_EMASS, "problem %d: negative density values", bi);
+        const double M0 = q[0], M1 = q[1];
+        if (!(M0 > 0) || !(M1 > 0) || std::fabs(M0 - M1) > 1e-6 * std::max(M0, M1))
+          return seterr(OT_EMASS, "problem %d: masses differ (%.9g vs %.9g)", bi, M0, M1);
+        sc[2 * bi] = (double)S / M0;
+        sc[2 * bi + 1] = (double)S / M1;
+        out_scale[bi] = 0.5 * (M0 + M1) / (double)S;
+      }
+    } else {
+      for (int bi = 0; bi < B; ++bi) out_scale[bi] = 1.0;
+    }
+    CUDA_OK(cudaMemcpyAsync(scl, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    const int blocks = std::min(1024, (S + 255) / 256);
+    k_scale_boundary<T><<<dim3(blocks, B), 256, 0, st>>>(stage, stage + n, S, scl, f0n, f1n);
+    CUDA_OK(cudaGetLastError());
+    return OT_OK;
+  }
+
+  int grid1d(long long n) const { return (int)std::min<long long>((n + 255) / 256, 152 * 16); }
+
+  // internal x <- packed (float), solver units
+  ot_status unpack_x(const float* packed) {
+    const size_t n = (size_t)B * cp.total;
+    CUDA_OK(cudaMemcpyAsync(stage, packed, n * sizeof(float), cudaMemcpyDefault, st));
+    k_unpack_path<T><<<grid1d((long long)B * N), 256, 0, st>>>(g, cp, stage, 1.0, x[0], x[1], x[2], x[3]);
+    CUDA_OK(cudaGetLastError());
+    return OT_OK;
+  }
+
+  ot_status cold_start() {
+    for (int k = 0; k < 4; ++k) {
+      CUDA_OK(cudaMemsetAsync(a[0][k], 0, (size_t)B * N * sizeof(T), st));
+      CUDA_OK(cudaMemsetAsync(b[0][k], 0, (size_t)B * N * sizeof(T), st));
+      CUDA_OK(cudaMemsetAsync(b[1][k], 0, (size_t)B * N * sizeof(T), st));
+    }
+    par = 0;
+    have_x = false;
+    return OT_OK;
+  }
+
+  ot_status solve(const float* f0, const float* f1, int iters, double tol, const float* init,
+                  ot_solve_stats* stats) override {
+    if (!f0 || !f1) return seterr(OT_EINVAL, "f0 and f1 are required");
+    OT_TRY(load_boundary(f0, f1, true));
+    OT_TRY(cold_start());
+    if (init) {
+      // x0 = init (scaled to solver units per problem), b = bbar = 0 -> a = x0
+      const size_t n = (size_t)B * cp.total;
+      CUDA_OK(cudaMemcpyAsync(stage, init, n * sizeof(float), cudaMemcpyDefault, st));
+      // one scale per batch entry: unpack problem by problem
+      for (int bi = 0; bi < B; ++bi) {
+        Geo<T> g1 = g;
+        g1.B = 1;
+        const size_t off = (size_t)bi * N;
+        k_unpack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, stage + (size_t)bi * cp.total, 1.0 / out_scale[bi],
+                                                    a[0][0] + off, a[0][1] + off, a[0][2] + off, a[0][3] + off);
+        CUDA_OK(cudaGetLastError());
+      }
+    }
+    return drive(iters, tol, grid.check_every, stats);
+  }
+
+  ot_status path(float* f, float* m0, float* m1, float* m2) override {
+    if (!have_x) return seterr(OT_EINVAL, "no path: run ot_solve or ot_iterate first");
+    float* ds[4] = {m0, d >= 2 ? m1 : nullptr, d >= 3 ? m2 : nullptr, f};
+    for (int k = 0; k < 4; ++k) {
+      if (!ds[k]) continue;
+      // component k of every problem, scaled back to the caller's units
+      for (int bi = 0; bi < B; ++bi) {
+        Geo<T> g1 = g;
+        g1.B = 1;
+        const size_t off = (size_t)bi * N;
+        float* dd[4] = {nullptr, nullptr, nullptr, nullptr};
+        dd[k] = stage + (size_t)bi * cp.len[k];
+        k_pack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, x[0] + off, x[1] + off, x[2] + off, x[3] + off,
+                                                  out_scale[bi], nullptr, dd[0], dd[1], dd[2], dd[3]);
+        CUDA_OK(cudaGetLastError());
+      }
+      CUDA_OK(cudaMemcpyAsync(ds[k], stage, (size_t)B * cp.len[k] * sizeof(float), cudaMemcpyDefault, st));
+      CUDA_OK(cudaStreamSynchronize(st));
+    }
+    return OT_OK;
+  }
+
+  ot_status state_set(const float* f0, const float* f1, const float* xp, const float* bp,
+                      const float* bbp) override {
+    if (!f0 || !f1 || !xp || !bp) return seterr(OT_EINVAL, "f0, f1, x and b are required");
+    OT_TRY(load_boundary(f0, f1, false));
+    OT_TRY(unpack_x(xp));
+    const long long cells = (long long)B * N;
+    // b -> b[0]; bbar -> b[1] temporarily
+    for (int k = 0; k < 4; ++k) {
+      CUDA_OK(cudaMemsetAsync(b[0][k], 0, cells * sizeof(T), st));
+      CUDA_OK(cudaMemsetAsync(b[1][k], 0, cells * sizeof(T), st));
+    }
+    OT_TRY(load_dual(bp, b[0]));
+    if (bbp) OT_TRY(load_dual(bbp, b[1]));
+    else for (int k = 0; k < 4; ++k) CUDA_OK(cudaMemcpyAsync(b[1][k], b[0][k], cells * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    // a[0] = x - tau sigma K^T bbar
+    k_make_a<T><<<grid1d(cells), 256, 0, st>>>(g, CPtr4<T>{{x[0], x[1], x[2], x[3]}},
+                                              CPtr4<T>{{b[1][0], b[1][1], b[1][2], b[1][3]}}, a[0][0], a[0][1],
+                                              a[0][2], a[0][3]);
+    CUDA_OK(cudaGetLastError());
+    // keep 2 b - bbar in b[1] so that bbar = 2 b[par] - b[1 - par] holds
+    for (int k = 0; k < 4; ++k)
+      k_axpby<T><<<grid1d(cells), 256, 0, st>>>(cells, T(2), b[0][k], T(-1), b[1][k], b[1][k]);
+    CUDA_OK(cudaGetLastError());
+    par = 0;
+    have_x = true;
+    CUDA_OK(cudaStreamSynchronize(st));
+    return OT_OK;
+  }
+
+  // packed dual (float, d+1 components of B*N cells... laid out problem-major) -> internal
+  ot_status load_dual(const float* src, T* const* dst) {
+    const long long cells = (long long)B * N;
+    // packed dual: per problem (d+1) components of N cells
+    std::vector<int> comp = comps();
+    CUDA_OK(cudaMemcpyAsync(stage, src, (size_t)B * (d + 1) * N * sizeof(float), cudaMemcpyDefault, st));
+    for (int bi = 0; bi < B; ++bi)
+      for (int j = 0; j <= d; ++j) {
+        k_convert<T, float><<<grid1d(N), 256, 0, st>>>(N, stage + ((size_t)bi * (d + 1) + j) * N,
+                                                       dst[comp[j]] + (size_t)bi * N);
+      }
+    CUDA_OK(cudaGetLastError());
+    (void)cells;
+    return OT_OK;
+  }
+  std::vector<int> comps() const {
+    std::vector<int> c;
+    for (int k = 0; k < d; ++k) c.push_back(k);
+    c.push_back(3);
+    return c;
+  }
+
+  ot_status state_get(float* xp, float* bp, float* bbp) override {
+    const long long cells = (long long)B * N;
+    if (xp) {
+      if (!have_x) return seterr(OT_EINVAL, "x is not available: run ot_iterate first");
+      k_pack_path<T><<<grid1d(cells), 256, 0, st>>>(g, cp, x[0], x[1], x[2], x[3], 1.0, stage, nullptr, nullptr,
+                                                   nullptr, nullptr);
+      CUDA_OK(cudaGetLastError());
+      CUDA_OK(cudaMemcpyAsync(xp, stage, (size_t)B * cp.total * sizeof(float), cudaMemcpyDefault, st));
+      CUDA_OK(cudaStreamSynchronize(st));
+    }
+    std::vector<int> comp = comps();
+    for (int which = 0; which < 2; ++which) {
+      float* dst = which == 0 ? bp : bbp;
+      if (!dst) continue;
+      for (int bi = 0; bi < B; ++bi)
+        for (int j = 0; j <= d; ++j) {
+          const size_t off = (size_t)bi * N;
+          float* o = stage + ((size_t)bi * (d + 1) + j) * N;
+          if (which == 0) {
+            k_convert<float, T><<<grid1d(N), 256, 0, st>>>(N, b[par][comp[j]] + off, o);
+          } else {
+            // bbar = 2 b[par] - b[1-par], computed in T then converted
+            k_axpby<T><<<grid1d(N), 256, 0, st>>>(N, T(2), b[par][comp[j]] + off, T(-1),
+                                                   b[1 - par][comp[j]] + off, hat + off);
+            k_convert<float, T><<<grid1d(N), 256, 0, st>>>(N, hat + off, o);
+          }
+        }
+      CUDA_OK(cudaGetLastError());
+      CUDA_OK(cudaMemcpyAsync(dst, stage, (size_t)B * (d + 1) * N * sizeof(float), cudaMemcpyDefault, st));
+      CUDA_OK(cudaStreamSynchronize(st));
+    }
+    (void)cells;
+    return OT_OK;
+  }
+
+  ot_status iterate(int iters, ot_solve_stats* stats) override { return drive(iters, 0.0, 0, stats); }
+
+  ot_status project(const float* f0, const float* f1, const float* ap, float* xp, float* phip) override {
+    if (!f0 || !f1 || !ap || !xp) return seterr(OT_EINVAL, "f0, f1, a and x are required");
+    OT_TRY(load_boundary(f0, f1, false));
+    OT_TRY(unpack_x(ap));
+    const long long cells = (long long)B * N;
+    // a[0] <- unpacked a (stored in x), run the Poisson solve, then x = a - A^T phi
+    for (int k = 0; k < 4; ++k)
+      CUDA_OK(cudaMemcpyAsync(a[0][k], x[k], cells * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    enqueue_poisson(0, nullptr);
+    Arrays<T> A = arrays(0, true);
+    k_correct<T><<<grid1d(cells), 256, 0, st>>>(g, A);
+    CUDA_OK(cudaGetLastError());
+    k_pack_path<T><<<grid1d(cells), 256, 0, st>>>(g, cp, x[0], x[1], x[2], x[3], 1.0, stage, nullptr, nullptr,
+                                                 nullptr, nullptr);
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaMemcpyAsync(xp, stage, (size_t)B * cp.total * sizeof(float), cudaMemcpyDefault, st));
+    if (phip) {
+      k_convert<float, T><<<grid1d(cells), 256, 0, st>>>(cells, phi, stage);
+      CUDA_OK(cudaMemcpyAsync(phip, stage, cells * sizeof(float), cudaMemcpyDefault, st));
+    }
+    CUDA_OK(cudaStreamSynchronize(st));
+    have_x = false;
+    return OT_OK;
+  }
+
+  ot_status profile(int iters, double ms[5]) override {
+    if (iters < 1) return seterr(OT_EINVAL, "iters must be >= 1");
+    double sum[4] = {0, 0, 0, 0};
+    for (int i = 0; i < iters; ++i) {
+      enqueue_iteration(par, false, false, ev);
+      par ^= 1;
+      CUDA_OK(cudaGetLastError());
+      CUDA_OK(cudaEventSynchronize(ev[4]));
+      for (int k = 0; k < 4; ++k) {
+        float t = 0;
+        CUDA_OK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+        sum[k] += t;
+      }
+    }
+    for (int k = 0; k < 4; ++k) ms[k] = sum[k] / iters;
+    // whole iterations from the graph
+    const int pairs = std::max(1, iters / 2);
+    OT_TRY(graph_for(par));
+    CUDA_OK(cudaGraphLaunch(gexec[par], st));  // warm
+    CUDA_OK(cudaEventRecord(ev[10], st));
+    for (int i = 0; i < pairs; ++i) CUDA_OK(cudaGraphLaunch(gexec[par], st));
+    CUDA_OK(cudaEventRecord(ev[11], st));
+    CUDA_OK(cudaEventSynchronize(ev[11]));
+    float t = 0;
+    CUDA_OK(cudaEventElapsedTime(&t, ev[10], ev[11]));
+    ms[4] = t / (2.0 * pairs);
+    return OT_OK;
+  }
+};
+
+
+}  // namespace dynot

@@ -1,0 +1,491 @@
+// Kernels of one PDHG iteration (Algorithm 1) on the grid with three spatial
+// axes x (n1), y (n2), colour (C) and P time intervals.
+//
+//   K_A  rhs_fwd_xt : r = A a - f_b^-  (section 3, step 1), then the forward
+//                     DCT-II along x and along t, per (y, c) row of a problem.
+//   K_B  solve_yc   : forward DCT-II along y, the colour eigen-solve with the
+//                     division by the eigenvalues of A A^T (zero mode -> 0),
+//                     inverse DCT along y, per strip of W x-frequencies and one
+//                     t-frequency.
+//   K_C  inv_xt     : inverse DCT along t and x -> phi = (A A^T)^+ r.
+//   K_D  update     : x^{r+1} = a - A^T phi, u = S_M m, v = S_F f + f_b^+,
+//                     per-cell prox of J, b^{r+1}, bbar^{r+1} = 2 b^{r+1} - b^r,
+//                     and the next a = x^{r+1} - tau sigma K^T bbar^{r+1}
+//                     (steps 1-4 of Algorithm 1).  bbar at the neighbour cell of
+//                     each face is recomputed in place, so the iteration state
+//                     is just (a, b).
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace dynot {
+
+// ---------------------------------------------------------------------------
+// shared helpers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ size_t cidx(const Geo<T>& g, int b, int t, int ix, int iy, int ic) {
+  return ((size_t)(b * g.P + t) * g.S) + (size_t)ix + (size_t)g.n1 * ((size_t)iy + (size_t)g.n2 * ic);
+}
+
+// Per-cell proximal map of J (section 3, step 2):
+//   argmin_{u,v} |u|^2/(2v) + sigma/2 |u - a_m|^2 + sigma/2 (v - a_f)^2.
+// With z = sigma v, e = sigma a_f and d = sigma^2 |a_m|^2 / 2 the cubic of the
+// paper, 2 (1 + sigma v)^2 (v - a_f) = sigma |a_m|^2, reads
+//   q(z) = (1 + z)^2 (z - e) - d = 0,   u = z a_m / (1 + z),  v = z / sigma.
+// A root z > 0 exists iff e + d > 0; otherwise (u, v) = (0, 0).  With w = 1 + z
+// and c = 1 + e the root satisfies w^2 (w - c) = d, which gives the upper
+// bounds w <= c + min(d^(1/3), d/c^2) for c > 0 and w <= min(d^(1/3), sqrt(d/|c|))
+// for c <= 0.  q is increasing and convex for z >= max(e, 0), so Newton's
+// method from that bound decreases monotonically to the root.
+template <typename T>
+__device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T& u0, T& u1, T& u2, T& v) {
+  const T s2 = am0 * am0 + am1 * am1 + am2 * am2;
+  const T e = sigma * af;
+  const T d = T(0.5) * sigma * sigma * s2;
+  if (!(e + d > T(0))) {
+    u0 = u1 = u2 = v = T(0);
+    return;
+  }
+  const T c = T(1) + e;
+  T z;
+  if (c > T(0)) {
+    const T del = min(cbrt(d), d / (c * c));
+    z = e + del;
+  } else {
+    z = min(cbrt(d), sqrt(d / (-c))) - T(1);
+  }
+  z = max(z, T(0));
+  const T eps = sizeof(T) == 4 ? T(2e-7) : T(4e-16);
+#pragma unroll 1
+  for (int it = 0; it < 40; ++it) {
+    const T w = T(1) + z;
+    const T zme = z - e;
+    const T q = w * w * zme - d;
+    const T dq = w * (T(2) * zme + w);
+    const T step = q / dq;
+    z -= step;
+    if (!(fabs(step) > eps * z)) break;
+  }
+  z = max(z, T(0));
+  const T r = z / (T(1) + z);
+  u0 = r * am0;
+  u1 = r * am1;
+  u2 = r * am2;
+  v = z / sigma;
+}
+
+// ---------------------------------------------------------------------------
+// K_D: fused projection correction + prox + dual update + next a
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct CellCtx {
+  const Geo<T>& g;
+  const Arrays<T>& A;
+  int b;
+
+  __device__ __forceinline__ T phi(int t, int x, int y, int c) const { return A.phi[cidx(g, b, t, x, y, c)]; }
+
+  // x^{r+1} at the right face of (t, x, y, c) along axis k (3 = time); zero at Neumann boundaries.
+  __device__ __forceinline__ T xr(int k, int t, int x, int y, int c) const {
+    const size_t i0 = cidx(g, b, t, x, y, c);
+    if (k == 0) {
+      int x1 = x + 1;
+      if (x1 == g.n1) { if (!g.per1) return T(0); x1 = 0; }
+      return A.a[0][i0] + g.s1 * (A.phi[cidx(g, b, t, x1, y, c)] - A.phi[i0]);
+    } else if (k == 1) {
+      int y1 = y + 1;
+      if (y1 == g.n2) { if (!g.per2) return T(0); y1 = 0; }
+      return A.a[1][i0] + g.s2 * (A.phi[cidx(g, b, t, x, y1, c)] - A.phi[i0]);
+    } else if (k == 2) {
+      int c1 = c + 1;
+      if (c1 == g.C) { if (!g.perc) return T(0); c1 = 0; }
+      return A.a[2][i0] + g.sc * (A.phi[cidx(g, b, t, x, y, c1)] - A.phi[i0]);
+    } else {
+      if (t == g.P - 1) return T(0);
+      return A.a[3][i0] + g.sp * (A.phi[cidx(g, b, t + 1, x, y, c)] - A.phi[i0]);
+    }
+  }
+  // x^{r+1} at the left face = right face of the previous cell (wrapping), or the boundary value
+  __device__ __forceinline__ T xl(int k, int t, int x, int y, int c) const {
+    if (k == 0) {
+      if (x == 0) { if (!g.per1) return T(0); return xr(0, t, g.n1 - 1, y, c); }
+      return xr(0, t, x - 1, y, c);
+    } else if (k == 1) {
+      if (y == 0) { if (!g.per2) return T(0); return xr(1, t, x, g.n2 - 1, c); }
+      return xr(1, t, x, y - 1, c);
+    } else if (k == 2) {
+      if (c == 0) { if (!g.perc) return T(0); return xr(2, t, x, y, g.C - 1); }
+      return xr(2, t, x, y, c - 1);
+    } else {
+      if (t == 0) return A.f0[(size_t)b * g.S + x + (size_t)g.n1 * (y + (size_t)g.n2 * c)];
+      return xr(3, t - 1, x, y, c);
+    }
+  }
+  __device__ __forceinline__ T xr_t_or_f1(int t, int x, int y, int c) const {
+    if (t == g.P - 1) return A.f1[(size_t)b * g.S + x + (size_t)g.n1 * (y + (size_t)g.n2 * c)];
+    return xr(3, t, x, y, c);
+  }
+
+  // Steps 2-4 at one cell.  Outputs bbar (4), b^{r+1} (4), the right faces of x^{r+1},
+  // K x^{r+1} + (0, f_b^+) and the prox result.
+  __device__ __forceinline__ void cell(int t, int x, int y, int c, T bb[4], T bn[4], T xrr[4], T kx[4],
+                                       T& U0, T& U1, T& U2, T& V) const {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) xrr[k] = xr(k, t, x, y, c);
+    xrr[3] = xr_t_or_f1(t, x, y, c);
+    kx[0] = T(0.5) * (xl(0, t, x, y, c) + xrr[0]);
+    kx[1] = T(0.5) * (xl(1, t, x, y, c) + xrr[1]);
+    kx[2] = T(0.5) * (xl(2, t, x, y, c) + xrr[2]);
+    kx[3] = T(0.5) * (xl(3, t, x, y, c) + xrr[3]);
+    const size_t i0 = cidx(g, b, t, x, y, c);
+    T bo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bo[k] = A.b[k][i0];
+    const T am0 = kx[0] + bo[0], am1 = kx[1] + bo[1], am2 = kx[2] + bo[2], af = kx[3] + bo[3];
+    prox_J<T>(am0, am1, am2, af, g.sigma, U0, U1, U2, V);
+    bn[0] = am0 - U0;
+    bn[1] = am1 - U1;
+    bn[2] = am2 - U2;
+    bn[3] = af - V;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bb[k] = T(2) * bn[k] - bo[k];
+    if (t == g.P - 1) xrr[3] = T(0);  // the f1 value is not a face of x
+  }
+
+  __device__ __forceinline__ T bbar_only(int k, int t, int x, int y, int c) const {
+    T bb[4], bn[4], xrr[4], kx[4], U0, U1, U2, V;
+    cell(t, x, y, c, bb, bn, xrr, kx, U0, U1, U2, V);
+    return bb[k];
+  }
+};
+
+// Residual accumulators (FP64, one set per problem):
+//   0: sum |b^{r+1} - b^r|^2   1: sum |K x + (0, f_b^+)|^2   2: sum J(u, v)
+//   3: sum |x^{r+1} - x^r|^2 is not formed here; 4..: unused
+//   mass[b*P + t]: sum over space of f at time (t+1)/P
+constexpr int kAcc = 4;
+
+template <typename T>
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, bool CHECK, bool WRITE_X>
+__global__ void __launch_bounds__(128) k_update(Geo<T> g, Arrays<T> A, double* __restrict__ acc,
+                                                double* __restrict__ mass) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  int z = blockIdx.z;
+  const int c = z % g.C;
+  z /= g.C;
+  const int t = z % g.P;
+  const int b = z / g.P;
+  const bool live = x < g.n1;
+  double r_db = 0, r_kx = 0, r_J = 0, r_m = 0;
+  if (live) {
+    CellCtx<T> cc{g, A, b};
+    T bb[4], bn[4], xrr[4], kx[4], U0, U1, U2, V;
+    cc.cell(t, x, y, c, bb, bn, xrr, kx, U0, U1, U2, V);
+    const size_t i0 = cidx(g, b, t, x, y, c);
+    T an[4];
+    // a^{r+1} at the right faces: x^{r+1} - tau sigma (bbar_here + bbar_next) / 2
+    if (x + 1 < g.n1 || g.per1) {
+      const T o = cc.bbar_only(0, t, x + 1 < g.n1 ? x + 1 : 0, y, c);
+      an[0] = xrr[0] - g.ts * T(0.5) * (bb[0] + o);
+    } else {
+      an[0] = T(0);
+    }
+    if (y + 1 < g.n2 || g.per2) {
+      const T o = cc.bbar_only(1, t, x, y + 1 < g.n2 ? y + 1 : 0, c);
+      an[1] = xrr[1] - g.ts * T(0.5) * (bb[1] + o);
+    } else {
+      an[1] = T(0);
+    }
+    if (c + 1 < g.C || g.perc) {
+      const T o = cc.bbar_only(2, t, x, y, c + 1 < g.C ? c + 1 : 0);
+      an[2] = xrr[2] - g.ts * T(0.5) * (bb[2] + o);
+    } else {
+      an[2] = T(0);
+    }
+    if (t + 1 < g.P) {
+      const T o = cc.bbar_only(3, t + 1, x, y, c);
+      an[3] = xrr[3] - g.ts * T(0.5) * (bb[3] + o);
+    } else {
+      an[3] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      A.an[k][i0] = an[k];
+      A.bn[k][i0] = bn[k];
+    }
+    if (WRITE_X) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) A.x[k][i0] = xrr[k];
+    }
+    if (CHECK) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double db = (double)bn[k] - (double)A.b[k][i0];
+        r_db += db * db;
+        r_kx += (double)kx[k] * (double)kx[k];
+      }
+      const double uu = (double)U0 * U0 + (double)U1 * U1 + (double)U2 * U2;
+      if (V > T(0)) r_J = uu / (2.0 * (double)V);
+      r_m = (double)xrr[3];
+    }
+  }
+  if (CHECK) {
+    __shared__ double red[4][4];
+    r_db = warp_sum<T>(r_db);
+    r_kx = warp_sum<T>(r_kx);
+    r_J = warp_sum<T>(r_J);
+    r_m = warp_sum<T>(r_m);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+      red[w][0] = r_db;
+      red[w][1] = r_kx;
+      red[w][2] = r_J;
+      red[w][3] = r_m;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      double s = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i][threadIdx.x];
+      if (threadIdx.x < 3) atomicAdd(&acc[(size_t)b * kAcc + threadIdx.x], s);
+      else if (t < g.P - 1) atomicAdd(&mass[(size_t)b * g.P + t], s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K_A: r = A a - f_b^- and forward DCT along x and t, per (y, c) row
+// ---------------------------------------------------------------------------
+
+// Shared-memory carve-up of the x/t kernels.
+template <typename T>
+struct XtSmem {
+  T* tile;      // [P][ld]
+  c2<T>* scr;   // FFT scratch
+  c2<T>* tw;    // [n1]
+  c2<T>* hw;    // [n1]
+  T* Mt;        // [P][PMAX]
+  T* cos4;      // dense fallback table [4 n1]
+};
+
+struct XtTables {
+  const void* tw;    // c2<T>[n1]
+  const void* hw;    // c2<T>[n1]
+  const void* Mt_f;  // forward t-DCT, [P][PMAX]
+  const void* Mt_i;  // inverse t-DCT
+  const void* cos4;  // [4 n1]
+};
+
+template <typename T>
+__device__ __forceinline__ void xt_carve(XtSmem<T>& s, char* sm, int P, int ld, int n1, int PMAX, int scr_elems) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = sm + off; off += (bytes + 15) & ~size_t(15); return p; };
+  s.tile = (T*)take(sizeof(T) * (size_t)(P + 1) * ld);
+  s.scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
+  s.tw = (c2<T>*)take(sizeof(c2<T>) * n1);
+  s.hw = (c2<T>*)take(sizeof(c2<T>) * n1);
+  s.Mt = (T*)take(sizeof(T) * (size_t)P * PMAX);
+  s.cos4 = (T*)take(sizeof(T) * 4 * n1);
+}
+
+// N1 == 0 selects the dense x transform.
+template <typename T, int N1, int N2, int PMAX>
+__global__ void __launch_bounds__(256) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
+                                                    const T* __restrict__ f0, const T* __restrict__ f1,
+                                                    T* __restrict__ rhat, XtTables tb, int scr_elems) {
+  extern __shared__ __align__(16) char smraw[];
+  const int y = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
+  const int n1 = g.n1, P = g.P;
+  XtSmem<T> s;
+  xt_carve<T>(s, smraw, P, n1, n1, PMAX, scr_elems);
+  const T* ax = ap.p[0];
+  const T* ay = ap.p[1];
+  const T* ac = ap.p[2];
+  const T* af = ap.p[3];
+  // tables
+  if (N1) load_tables<T>(s.tw, s.hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
+  else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) s.cos4[j] = ((const T*)tb.cos4)[j];
+  for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_f)[j];
+  // divergence of a and the time difference with the boundary densities
+  const int ym = y > 0 ? y - 1 : (g.per2 ? g.n2 - 1 : -1);
+  const int cm = c > 0 ? c - 1 : (g.perc ? g.C - 1 : -1);
+  for (int x = threadIdx.x; x < n1; x += blockDim.x) {
+    const int xm = x > 0 ? x - 1 : (g.per1 ? n1 - 1 : -1);
+    const size_t sb = (size_t)b * g.S + x + (size_t)n1 * (y + (size_t)g.n2 * c);
+    T fprev = f0[sb];
+    for (int t = 0; t < P; ++t) {
+      const size_t i0 = cidx(g, b, t, x, y, c);
+      T r = g.s1 * (ax[i0] - (xm >= 0 ? ax[cidx(g, b, t, xm, y, c)] : T(0)));
+      r += g.s2 * (ay[i0] - (ym >= 0 ? ay[cidx(g, b, t, x, ym, c)] : T(0)));
+      r += g.sc * (ac[i0] - (cm >= 0 ? ac[cidx(g, b, t, x, y, cm)] : T(0)));
+      const T fnext = (t == P - 1) ? f1[sb] : af[i0];
+      r += g.sp * (fnext - fprev);
+      fprev = fnext;
+      s.tile[t * n1 + x] = r;
+    }
+  }
+  const int Pr = P + (P & 1);  // the pair packing needs an even row count
+  if (Pr != P)
+    for (int x = threadIdx.x; x < n1; x += blockDim.x) s.tile[P * n1 + x] = T(0);
+  __syncthreads();
+  Rows<T> rows{s.tile, 1 << 30, 0, n1, 1};
+  if constexpr (N1 > 0) {
+    DctPow2<T, N1, N2, false>::forward(rows, Pr, s.scr, s.tw, s.hw);
+  } else {
+    dct_dense_rows<T, false>(rows, P, n1, false, (T*)s.scr, 2 * scr_elems, s.cos4);
+  }
+  // (the FFT path leaves a trailing barrier; the dense path too)
+  dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
+  __syncthreads();
+  for (int t = 0; t < P; ++t)
+    for (int x = threadIdx.x; x < n1; x += blockDim.x) rhat[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
+}
+
+// K_C: inverse DCT along t and x -> phi
+template <typename T, int N1, int N2, int PMAX>
+__global__ void __launch_bounds__(256) k_inv_xt(Geo<T> g, const T* __restrict__ phihat, T* __restrict__ phi,
+                                                XtTables tb, int scr_elems) {
+  extern __shared__ __align__(16) char smraw[];
+  const int y = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
+  const int n1 = g.n1, P = g.P;
+  XtSmem<T> s;
+  xt_carve<T>(s, smraw, P, n1, n1, PMAX, scr_elems);
+  if (N1) load_tables<T>(s.tw, s.hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
+  else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) s.cos4[j] = ((const T*)tb.cos4)[j];
+  for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_i)[j];
+  for (int t = 0; t < P; ++t)
+    for (int x = threadIdx.x; x < n1; x += blockDim.x) s.tile[t * n1 + x] = phihat[cidx(g, b, t, x, y, c)];
+  __syncthreads();
+  dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
+  __syncthreads();
+  const int Pr = P + (P & 1);
+  if (Pr != P)
+    for (int x = threadIdx.x; x < n1; x += blockDim.x) s.tile[P * n1 + x] = T(0);
+  __syncthreads();
+  Rows<T> rows{s.tile, 1 << 30, 0, n1, 1};
+  if constexpr (N1 > 0) {
+    DctPow2<T, N1, N2, false>::inverse(rows, Pr, s.scr, s.tw, s.hw);
+  } else {
+    dct_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, s.cos4);
+  }
+  for (int t = 0; t < P; ++t)
+    for (int x = threadIdx.x; x < n1; x += blockDim.x) phi[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
+}
+
+// ---------------------------------------------------------------------------
+// K_B: y transform, colour eigen-solve and eigenvalue divide, inverse y
+// ---------------------------------------------------------------------------
+
+struct YcTables {
+  const void* tw;      // c2<T>[n2]
+  const void* hw;      // c2<T>[n2]
+  const void* cos4;    // [4 n2]
+  const void* lam1;    // T[n1]   eigenvalues along x
+  const void* lam2;    // T[n2]
+  const void* lamt;    // T[P]
+  const double* lam1d; // the same in double
+  const double* lam2d;
+  const double* lamtd;
+  const void* Qc;      // colour eigenbasis, T[C*C], Qc[c*C + j]
+  const void* lamc;    // T[C]
+  const double* lamcd;
+  double lam_fp64;     // eigenvalues below this are divided in FP64
+};
+
+constexpr int kMaxC = 4;
+
+template <typename T, int M1, int M2, int W>
+__global__ void __launch_bounds__(256) k_solve_yc(Geo<T> g, T* __restrict__ hat, YcTables tb, int scr_elems) {
+  extern __shared__ __align__(16) char smraw[];
+  const int x0 = blockIdx.x * W, kt = blockIdx.y, b = blockIdx.z;
+  const int n1 = g.n1, n2 = g.n2, C = g.C;
+  const int w_act = min(W, n1 - x0);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = smraw + off; off += (bytes + 15) & ~size_t(15); return p; };
+  T* tile = (T*)take(sizeof(T) * (size_t)C * n2 * W);       // [c][y][w]
+  c2<T>* scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
+  c2<T>* tw = (c2<T>*)take(sizeof(c2<T>) * n2);
+  c2<T>* hw = (c2<T>*)take(sizeof(c2<T>) * n2);
+  T* cos4 = (T*)take(sizeof(T) * 4 * n2);
+  T* l2 = (T*)take(sizeof(T) * n2);
+  if (M1) load_tables<T>(tw, hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n2);
+  else for (int j = threadIdx.x; j < 4 * n2; j += blockDim.x) cos4[j] = ((const T*)tb.cos4)[j];
+  for (int j = threadIdx.x; j < n2; j += blockDim.x) l2[j] = ((const T*)tb.lam2)[j];
+  // load [c][y][w] (zero beyond the last column so pairs stay well defined)
+  for (int i = threadIdx.x; i < C * n2 * W; i += blockDim.x) {
+    const int w = i % W, yc = i / W;
+    const int y = yc % n2, c = yc / n2;
+    tile[i] = (w < w_act) ? hat[cidx(g, b, kt, x0 + w, y, c)] : T(0);
+  }
+  __syncthreads();
+  Rows<T> rows{tile, W, n2 * W, 1, W};
+  const int nrows = C * W;
+  if constexpr (M1 > 0) {
+    DctPow2<T, M1, M2, true>::forward(rows, nrows, scr, tw, hw);
+  } else {
+    dct_dense_rows<T, true>(rows, nrows, n2, false, (T*)scr, 2 * scr_elems, cos4);
+  }
+  // colour eigen-solve: phi_c = sum_j Q[c][j] (sum_c' Q[c'][j] r_c') / lambda(kx, ky, j, kt)
+  {
+    const T* Q = (const T*)tb.Qc;
+    const T* lc = (const T*)tb.lamc;
+    const T* l1 = (const T*)tb.lam1;
+    const T lt = ((const T*)tb.lamt)[kt];
+    for (int i = threadIdx.x; i < n2 * W; i += blockDim.x) {
+      const int w = i % W, ky = i / W;
+      if (w >= w_act) continue;
+      const int kx = x0 + w;
+      T r[kMaxC], co[kMaxC];
+#pragma unroll
+      for (int cc = 0; cc < kMaxC; ++cc) r[cc] = cc < C ? tile[(cc * n2 + ky) * W + w] : T(0);
+      const T lxyt = l1[kx] + l2[ky] + lt;
+#pragma unroll
+      for (int j = 0; j < kMaxC; ++j) {
+        if (j >= C) { co[j] = T(0); continue; }
+        T s = 0;
+#pragma unroll
+        for (int cc = 0; cc < kMaxC; ++cc) if (cc < C) s += Q[cc * C + j] * r[cc];
+        const T lam = lxyt + lc[j];
+        if (!(lam > T(0))) {
+          co[j] = T(0);     // the zero eigenvalue of the pseudo-inverse
+        } else if ((double)lam < tb.lam_fp64) {
+          // low modes: eigenvalue and quotient in double precision
+          const double ld = tb.lam1d[kx] + tb.lam2d[ky] + tb.lamtd[kt] + tb.lamcd[j];
+          co[j] = ld > 0.0 ? (T)((double)s / ld) : T(0);
+        } else {
+          co[j] = s / lam;
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < kMaxC; ++cc) {
+        if (cc >= C) continue;
+        T s = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxC; ++j) if (j < C) s += Q[cc * C + j] * co[j];
+        tile[(cc * n2 + ky) * W + w] = s;
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (M1 > 0) {
+    DctPow2<T, M1, M2, true>::inverse(rows, nrows, scr, tw, hw);
+  } else {
+    dct_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, cos4);
+  }
+  for (int i = threadIdx.x; i < C * n2 * W; i += blockDim.x) {
+    const int w = i % W, yc = i / W;
+    const int y = yc % n2, c = yc / n2;
+    if (w < w_act) hat[cidx(g, b, kt, x0 + w, y, c)] = tile[i];
+  }
+}
+
+}  // namespace dynot

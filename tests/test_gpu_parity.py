@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Single operators (prox, projection, one full iteration from a random state)
+must agree to 1e-5 relative L2; a full solve at a fixed iteration count to
+1e-3 relative L2 of f (the tolerances the benchmark spec states for FP32 kernels).
+Grids cover several tiles and ragged tails: power-of-two FFT lengths, dense
+lengths, odd P, grey and 1D Neumann problems, Neumann colour, hue histograms
+of even and odd length, and the full 256 x 256 x 3 x 32 benchmark size."""
+import numpy as np
+import pytest
+
+import oracle as o
+from _helpers import (correction_tolerance, f32, oracle_grid, pack_dual, pack_path, random_pair, rel, smooth_field,
+                      unpack_dual, unpack_path)
+
+pytestmark = pytest.mark.gpu
+
+SIG = 0.3
+TAU = 0.99 / 0.3
+
+
+@pytest.fixture(scope="module")
+def ot():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_04840_gb300 import _build
+    _build.build()
+    import paper_1501_04840_gb300 as p
+    p.load_library()
+    return p
+
+
+def make_plan(ot, n, bc, P, batch=1, precision=0):
+    g = ot.grid(n, bc, P, sigma=SIG, tau=TAU, precision=precision)
+    return ot.Plan(g, batch=batch), oracle_grid(n, bc, P)
+
+
+RGB = ("neumann", "neumann", "periodic")
+GRIDS = [
+    ((32, 32, 3), RGB, 16),
+    ((64, 64, 3), RGB, 16),
+    ((48, 40, 3), RGB, 12),
+    ((128, 96, 3), RGB, 17),
+    ((64, 128, 3), RGB, 7),
+    ((64, 48), ("neumann", "neumann"), 8),
+    ((96,), ("neumann",), 16),
+    ((32, 24, 3), ("neumann", "neumann", "neumann"), 6),
+    ((360,), ("periodic",), 64),
+    ((101,), ("periodic",), 20),
+    ((2, 2, 3), RGB, 2),
+    ((256, 256, 3), RGB, 32),
+]
+IDS = ["x".join(map(str, n)) + "_" + "".join(b[0] for b in bc) + "_P%d" % P for n, bc, P in GRIDS]
+
+
+def test_prox_matches_oracle(ot):
+    rng = np.random.default_rng(0)
+    n = 200_000
+    am = (rng.standard_normal((3, n)) * rng.choice([0.01, 1.0, 30.0], size=n)).astype(np.float32)
+    af = (rng.standard_normal(n) * rng.choice([0.01, 1.0, 30.0], size=n)).astype(np.float32)
+    u, v = ot.prox(am, af, SIG)
+    uo, vo = o.prox_J([am[k].astype(np.float64) for k in range(3)], af.astype(np.float64), SIG)
+    assert rel(v, vo) <= 1e-5
+    assert rel(u, np.stack(uo)) <= 1e-5
+    # the zero branch is exact
+    zero = (af.astype(np.float64) + 0.5 * SIG * (am.astype(np.float64) ** 2).sum(0)) <= 0
+    assert np.all(v[zero] == 0) and np.all(u[:, zero] == 0)
+
+
+@pytest.mark.parametrize("n,bc,P", GRIDS, ids=IDS)
+def test_projection_matches_oracle(ot, n, bc, P):
+    """Smooth operands: the projection and phi agree to 1e-5."""
+    plan, g = make_plan(ot, n, bc, P)
+    rng = np.random.default_rng(1)
+    f0, f1 = random_pair(g, 2)
+    am = [smooth_field(g.m_shape(k), rng).astype(np.float32).astype(np.float64) for k in range(g.d)]
+    af = smooth_field(g.f_shape, rng).astype(np.float32).astype(np.float64)
+    x, phi = plan.project(f32(f0), f32(f1), f32(pack_path(g, am, af)), with_phi=True)
+    m, f, phio = o.project(g, am, af, f0, f1)
+    assert rel(phi, phio.ravel()) <= 1e-5
+    assert rel(x, pack_path(g, m, f)) <= 1e-5
+
+
+@pytest.mark.parametrize("n,bc,P", GRIDS, ids=IDS)
+def test_projection_white_noise(ot, n, bc, P):
+    """White-noise operands: phi to 1e-5; x to the FP32 bound of the A^T phi correction."""
+    plan, g = make_plan(ot, n, bc, P)
+    rng = np.random.default_rng(11)
+    f0, f1 = random_pair(g, 2)
+    am = [rng.standard_normal(g.m_shape(k)).astype(np.float32).astype(np.float64) for k in range(g.d)]
+    af = rng.standard_normal(g.f_shape).astype(np.float32).astype(np.float64)
+    x, phi = plan.project(f32(f0), f32(f1), f32(pack_path(g, am, af)), with_phi=True)
+    m, f, phio = o.project(g, am, af, f0, f1)
+    xo = pack_path(g, m, f)
+    assert rel(phi, phio.ravel()) <= 1e-5
+    assert rel(x, xo) <= correction_tolerance(g, phio, xo)
+
+
+def _random_state(g, seed, smooth=False):
+    rng = np.random.default_rng(seed)
+    gen = (lambda shape: smooth_field(shape, rng)) if smooth else (lambda shape: rng.standard_normal(shape))
+    st = o.State.zeros(g)
+    st.m = [gen(g.m_shape(k)) for k in range(g.d)]
+    st.f = np.abs(gen(g.f_shape)) + 0.1
+    st.bm = [0.3 * gen(g.cell_shape) for _ in range(g.d)]
+    st.bf = 0.3 * gen(g.cell_shape)
+    st.bbm = [0.3 * gen(g.cell_shape) for _ in range(g.d)]
+    st.bbf = 0.3 * gen(g.cell_shape)
+    # round through float32 so both sides start from identical values
+    st.m = [a.astype(np.float32).astype(np.float64) for a in st.m]
+    st.f = st.f.astype(np.float32).astype(np.float64)
+    for name in ("bm", "bbm"):
+        setattr(st, name, [a.astype(np.float32).astype(np.float64) for a in getattr(st, name)])
+    st.bf = st.bf.astype(np.float32).astype(np.float64)
+    st.bbf = st.bbf.astype(np.float32).astype(np.float64)
+    return st
+
+
+def _one_iteration(ot, n, bc, P, smooth, seed=4):
+    plan, g = make_plan(ot, n, bc, P)
+    f0, f1 = random_pair(g, 3)
+    st = _random_state(g, seed, smooth)
+    plan.state_set(f32(f0), f32(f1), f32(pack_path(g, st.m, st.f)), f32(pack_dual(g, st.bm, st.bf)),
+                   f32(pack_dual(g, st.bbm, st.bbf)))
+    plan.iterate(1)
+    x, b, bb = plan.state_get()
+    new, _ = o.pdhg_step(g, st, f0, f1, SIG, TAU)
+    if smooth:
+        tol = 1e-5
+    else:
+        # the projection inside the step bounds the error (see correction_tolerance)
+        km, kf = o.K_T(g, st.bbm, st.bbf)
+        am = [st.m[k] - TAU * SIG * km[k] for k in range(g.d)]
+        af = st.f - TAU * SIG * kf
+        mm, ff, phio = o.project(g, am, af, f0, f1)
+        tol = correction_tolerance(g, phio, pack_path(g, mm, ff))
+    m, f = unpack_path(g, x.astype(np.float64))
+    assert rel(f, new.f) <= tol
+    for k in range(g.d):
+        assert rel(m[k], new.m[k]) <= tol
+    bm, bf = unpack_dual(g, b.astype(np.float64))
+    bbm, bbf = unpack_dual(g, bb.astype(np.float64))
+    assert rel(bf, new.bf) <= tol and rel(bbf, new.bbf) <= tol
+    for k in range(g.d):
+        assert rel(bm[k], new.bm[k]) <= tol and rel(bbm[k], new.bbm[k]) <= tol
+
+
+@pytest.mark.parametrize("n,bc,P", GRIDS, ids=IDS)
+def test_one_iteration_matches_oracle(ot, n, bc, P):
+    _one_iteration(ot, n, bc, P, smooth=True)
+
+
+@pytest.mark.parametrize("n,bc,P", GRIDS, ids=IDS)
+def test_one_iteration_white_noise_state(ot, n, bc, P):
+    _one_iteration(ot, n, bc, P, smooth=False)
+
+
+def test_state_roundtrip_without_iterations(ot):
+    plan, g = make_plan(ot, (32, 24, 3), RGB, 6)
+    f0, f1 = random_pair(g, 5)
+    st = _random_state(g, 6)
+    xp = f32(pack_path(g, st.m, st.f))
+    bp = f32(pack_dual(g, st.bm, st.bf))
+    bbp = f32(pack_dual(g, st.bbm, st.bbf))
+    plan.state_set(f32(f0), f32(f1), xp, bp, bbp)
+    x, b, bb = plan.state_get()
+    assert np.array_equal(x, xp) and np.array_equal(b, bp)
+    assert rel(bb, bbp) <= 1e-6
+
+
+def _solve_both(ot, n, bc, P, iters, f0, f1):
+    plan, g = make_plan(ot, n, bc, P)
+    stats = plan.solve(f32(f0), f32(f1), iters)
+    path = plan.path()
+    st, infos, scale = o.solve(g, f0.astype(np.float64), f1.astype(np.float64), iters, SIG, TAU)
+    return plan, g, stats, path, st, infos, scale
+
+
+def test_full_solve_rgb_32x32x3x16_500_iterations(ot):
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(32, 32, 8, 0)
+    plan, g, stats, path, st, infos, scale = _solve_both(ot, (32, 32, 3), RGB, 16, 500, f0, f1)
+    assert stats.iterations == 500
+    assert rel(path["f"][0], st.f * scale) <= 1e-3
+    for k in range(3):
+        assert rel(path["m"][k][0], st.m[k] * scale) <= 1e-3
+    assert abs(stats.energy - infos[-1].energy * scale) <= 1e-3 * infos[-1].energy * scale
+    assert abs(stats.residual - infos[-1].residual) <= 1e-2 * infos[-1].residual + 1e-7
+    assert stats.mass_drift <= 1e-5
+
+
+def test_full_solve_hue_360x64(ot):
+    from paper_1501_04840_gb300 import synth
+    h0, h1 = synth.hue_pair(360, 0)
+    plan, g, stats, path, st, infos, scale = _solve_both(ot, (360,), ("periodic",), 64, 300, h0, h1)
+    assert rel(path["f"][0], st.f * scale) <= 1e-3
+    # m is unique only up to N(S_M) at the solution (section 2, Theorem 1); the
+    # iterates from the same start coincide, and so does u = S_M m
+    assert rel(path["m"][0][0], st.m[0] * scale) <= 1e-3
+    u_gpu = o.S_M(g, [path["m"][0][0].astype(np.float64)])[0]
+    assert rel(u_gpu, o.S_M(g, st.m)[0] * scale) <= 1e-3
+    assert stats.mass_drift <= 1e-5
+
+
+def test_batch_equals_single_problems(ot):
+    from paper_1501_04840_gb300 import synth
+    pairs = [synth.rgb_pair(48, 32, 8, s) for s in range(3)]
+    f0 = np.stack([p[0] for p in pairs])
+    f1 = np.stack([p[1] for p in pairs])
+    g = ot.grid((48, 32, 3), RGB, 9, sigma=SIG, tau=TAU)
+    plan = ot.Plan(g, batch=3)
+    plan.solve(f32(f0), f32(f1), 40)
+    pb = plan.path()
+    for s in range(3):
+        single = ot.Plan(ot.grid((48, 32, 3), RGB, 9, sigma=SIG, tau=TAU))
+        single.solve(f32(pairs[s][0]), f32(pairs[s][1]), 40)
+        ps = single.path()
+        assert rel(pb["f"][s], ps["f"][0]) <= 1e-6
+        for k in range(3):
+            assert rel(pb["m"][k][s], ps["m"][k][0]) <= 1e-6
+
+
+def test_input_validation(ot):
+    plan, g = make_plan(ot, (32, 32, 3), RGB, 8)
+    f0, f1 = random_pair(g, 7)
+    bad = f0.copy()
+    bad[0, 0, 0] = -1e-3
+    with pytest.raises(ot.OTError) as ei:
+        plan.solve(f32(bad), f32(f1), 5)
+    assert ei.value.status == 2
+    with pytest.raises(ot.OTError) as ei:
+        plan.solve(f32(f0), f32(f1 * 1.01), 5)
+    assert ei.value.status == 2
+    nan = f0.copy()
+    nan[1, 2, 3] = np.nan
+    with pytest.raises(ot.OTError) as ei:
+        plan.solve(f32(nan), f32(f1), 5)
+    assert ei.value.status == 2
+    # the plan still works afterwards
+    st = plan.solve(f32(f0), f32(f1), 5)
+    assert st.iterations == 5
+
+
+def test_tolerance_stops_early_and_reports(ot):
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(32, 32, 8, 0)
+    plan, g = make_plan(ot, (32, 32, 3), RGB, 16)
+    st = plan.solve(f32(f0), f32(f1), 2000, tol=1e-4, check_every=10)
+    assert st.converged and st.residual <= 1e-4 and st.iterations % 10 == 0 and st.iterations < 2000
+    st2 = plan.solve(f32(f0), f32(f1), 20, tol=1e-12)
+    assert not st2.converged and st2.iterations == 20
+
+
+def test_fp64_plan_matches_oracle_tightly(ot):
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(32, 32, 8, 0)
+    plan, g = make_plan(ot, (32, 32, 3), RGB, 16, precision=2)
+    plan.solve(f32(f0), f32(f1), 200)
+    path = plan.path()
+    st, infos, scale = o.solve(g, f0.astype(np.float64), f1.astype(np.float64), 200, SIG, TAU)
+    assert rel(path["f"][0], st.f * scale) <= 1e-6   # limited by the float32 path output
+
+
+def test_warm_start_from_the_solution_keeps_it(ot):
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(32, 32, 8, 1)
+    plan, g = make_plan(ot, (32, 32, 3), RGB, 16)
+    cold = plan.solve(f32(f0), f32(f1), 600)
+    p = plan.path()
+    init = np.concatenate([p["m"][k][0].ravel() for k in range(3)] + [p["f"][0].ravel()]).astype(np.float32)
+    warm = plan.solve(f32(f0), f32(f1), 10, init=init)
+    assert abs(warm.energy - cold.energy) <= 1e-2 * cold.energy
+
+
+# ---- the benchmark's size and launch configuration --------------------------
+
+def test_full_size_one_iteration_matches_oracle(ot):
+    n, P = (256, 256, 3), 32
+    plan, g = make_plan(ot, n, RGB, P)
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(256, 256, 32, 0)
+    f0 = f0.astype(np.float64)
+    f1 = f1.astype(np.float64)
+    st = _random_state(g, 8, smooth=True)
+    plan.state_set(f32(f0), f32(f1), f32(pack_path(g, st.m, st.f)), f32(pack_dual(g, st.bm, st.bf)),
+                   f32(pack_dual(g, st.bbm, st.bbf)))
+    plan.iterate(1)
+    x, b, bb = plan.state_get()
+    new, _ = o.pdhg_step(g, st, f0, f1, SIG, TAU)
+    m, f = unpack_path(g, x.astype(np.float64))
+    assert rel(f, new.f) <= 1e-5
+    for k in range(3):
+        assert rel(m[k], new.m[k]) <= 1e-5
+    bm, bf = unpack_dual(g, b.astype(np.float64))
+    assert rel(bf, new.bf) <= 1e-5
+
+
+def test_full_size_solve_first_iterations_and_invariants(ot):
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(256, 256, 32, 0)
+    plan, g = make_plan(ot, (256, 256, 3), RGB, 32)
+    stats = plan.solve(f32(f0), f32(f1), 4)
+    path = plan.path()
+    st, infos, scale = o.solve(g, f0.astype(np.float64), f1.astype(np.float64), 4, SIG, TAU)
+    assert rel(path["f"][0], st.f * scale) <= 1e-4
+    assert stats.mass_drift <= 1e-5
+    # mass of every interior time slice equals the mass of f0 (section 2, C_d)
+    sums = path["f"][0].reshape(g.P - 1, -1).astype(np.float64).sum(axis=1)
+    np.testing.assert_allclose(sums, f0.astype(np.float64).sum(), rtol=1e-5)
+
+
+def test_profile_reports_every_kernel(ot):
+    plan, g = make_plan(ot, (64, 64, 3), RGB, 16)
+    f0, f1 = random_pair(g, 9)
+    plan.solve(f32(f0), f32(f1), 2)
+    ms = plan.profile(4)
+    assert set(ms) == {"rhs_fwd_xt", "solve_yc", "inv_xt", "update", "iteration"}
+    assert all(v > 0 for v in ms.values())
