@@ -172,6 +172,26 @@ ot_status ot_prox(int count, int ncomp, double sigma, const float* a_m, const fl
  */
 ot_status ot_profile(ot_plan_t p, int iters, double ms[5], const char** names);
 
+/*
+ * ot_project for hue histograms without any device allocation (the paper has
+ * no counterpart; this serves callers that cannot call cudaMalloc, such as
+ * hosts that reserve all device memory up front or forbid allocation after
+ * start-up).  Computes, for `batch` problems of `bins` periodic bins and P
+ * time intervals, x = a - A^T (A A^T)^+ (A a - f_b^-) and phi = (A A^T)^+ (A a - f_b^-)
+ * exactly as a hue plan's ot_project does, with axis_scale <= 0 meaning `bins`.
+ * All pointers are DEVICE memory: f0, f1 [batch][bins]; a_packed, x_packed
+ * [batch][packed path]; phi [batch][P][bins].  Work is ordered on cuda_stream
+ * (NULL = legacy default stream) and the call returns after it finished.
+ * Working memory is a fixed file-scope device array of 4,194,304 floats
+ * (16 MiB) held by every GPU that loads the library until exit; a call needs
+ * batch * 2 * bins * P floats of it and returns OT_EINVAL above that.  The
+ * first call on each device resolves the array's device address (make that
+ * first call before any stream capture).  All calls share the array: calls
+ * whose kernels overlap on the GPU race and must not be issued.
+ */
+ot_status ot_hue_project_noalloc(int bins, int P, int batch, double axis_scale, const float* f0, const float* f1,
+                                 const float* a_packed, float* x_packed, float* phi, void* cuda_stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* ot_last_error(void);
 
