@@ -212,6 +212,12 @@ __global__ void k_axpby(long long n, T alpha, const T* __restrict__ x, T beta, c
     out[i] = alpha * x[i] + (y ? beta * y[i] : T(0));
 }
 
+template <typename T>
+__global__ void k_fill(long long n, T v, T* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = v;
+}
+
 template <typename To, typename Ti>
 __global__ void k_convert(long long n, const Ti* __restrict__ in, To* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

@@ -72,6 +72,23 @@ KB<T> pick_kb(int n) {
     default: return k_solve_yc<T, 0, 0, kW>;
   }
 }
+template <typename T> using KD = void (*)(Geo<T>, Arrays<T>, int, double*, double*);
+
+template <typename T, int C>
+KD<T> pick_kd_c(bool check, bool wx) {
+  if (check) return wx ? k_update_tiled<T, C, true, true> : k_update_tiled<T, C, true, false>;
+  return wx ? k_update_tiled<T, C, false, true> : k_update_tiled<T, C, false, false>;
+}
+template <typename T>
+KD<T> pick_kd(int C, bool check, bool wx) {
+  switch (C) {
+    case 1: return pick_kd_c<T, 1>(check, wx);
+    case 2: return pick_kd_c<T, 2>(check, wx);
+    case 3: return pick_kd_c<T, 3>(check, wx);
+    default: return pick_kd_c<T, 4>(check, wx);
+  }
+}
+
 template <typename T>
 KH<T> pick_kh(int pm) {
   return pm == 16 ? k_hue_t<T, 16> : (pm == 32 ? k_hue_t<T, 32> : k_hue_t<T, 64>);
@@ -106,6 +123,8 @@ struct Plan final : PlanBase {
   KC<T> kc = nullptr;
   KB<T> kb = nullptr;
   KH<T> kh = nullptr;
+  bool tiled = false;       // tiled update kernel (Neumann x and y)
+  int tc = 0;               // time-chunk length of the tiled update (autotuned)
   int par = 0;              // buffer holding the current state
   bool have_x = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -174,8 +193,53 @@ struct Plan final : PlanBase {
     OT_TRY(build_tables());
     for (auto& e : ev) CUDA_OK(cudaEventCreate(&e));
     out_scale.assign(B, 1.0);
+    tiled = !hue && !g.per1 && !g.per2 && C <= 4;
+    if (tiled) OT_TRY(tune_update());
     return OT_OK;
   }
+
+  // Autotuner of the tiled update: time chunk lengths P, P/2, P/4, P/8 on the
+  // zeroed workspace and keep the fastest (ties go to the longer chunk).
+  ot_status tune_update() {
+    std::vector<int> cands;
+    for (int d = 1; d <= 8; d *= 2) {
+      const int c = (P + d - 1) / d;
+      if (c >= 4 || d == 1)
+        if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
+    }
+    tc = cands[0];
+    if (cands.size() == 1) return OT_OK;
+    // a state on which the prox takes its Newton branch: b_f = 1, b_m = 0.5, a = phi = 0
+    const long long cells = (long long)B * N;
+    for (int k = 0; k < 4; ++k)
+      k_fill<T><<<grid1d(cells), 256, 0, st>>>(cells, k == 3 ? T(1) : T(0.5), b[0][k]);
+    CUDA_OK(cudaGetLastError());
+    float best = 1e30f;
+    for (int c : cands) {
+      tc = c;
+      enqueue_update(0, false, false);  // warm
+      CUDA_OK(cudaGetLastError());
+      CUDA_OK(cudaEventRecord(ev[10], st));
+      for (int r = 0; r < 3; ++r) enqueue_update(0, false, false);
+      CUDA_OK(cudaEventRecord(ev[11], st));
+      CUDA_OK(cudaEventSynchronize(ev[11]));
+      float ms = 0;
+      CUDA_OK(cudaEventElapsedTime(&ms, ev[10], ev[11]));
+      if (ms < 0.97f * best) {
+        best = ms;
+        tune_tc = c;
+      }
+    }
+    tc = tune_tc;
+    // clear both buffer sets again
+    for (int i = 0; i < 2; ++i)
+      for (int k = 0; k < 4; ++k) {
+        CUDA_OK(cudaMemsetAsync(a[i][k], 0, (size_t)B * N * sizeof(T), st));
+        CUDA_OK(cudaMemsetAsync(b[i][k], 0, (size_t)B * N * sizeof(T), st));
+      }
+    return OT_OK;
+  }
+  int tune_tc = 0;
 
   // ---- transform tables (computed in double on the host)
   ot_status build_tables() {
@@ -380,9 +444,20 @@ struct Plan final : PlanBase {
     }
   }
 
+  dim3 tiled_grid(int tchunk) const {
+    const int nbx = std::max(1, (n1 - 1 + kTX - 2) / (kTX - 1));
+    const int nby = std::max(1, (n2 - 1 + kTY - 2) / (kTY - 1));
+    const int nch = (P + tchunk - 1) / tchunk;
+    return dim3(nbx, nby, B * nch);
+  }
+
   void enqueue_update(int p, bool check, bool wx) {
-    const dim3 grd((n1 + kThreadsUpd - 1) / kThreadsUpd, n2, C * P * B);
     const Arrays<T> A = arrays(p, wx);
+    if (tiled) {
+      pick_kd<T>(C, check, wx)<<<tiled_grid(tc), dim3(kTX, kTY), 0, st>>>(g, A, tc, acc, mass);
+      return;
+    }
+    const dim3 grd((n1 + kThreadsUpd - 1) / kThreadsUpd, n2, C * P * B);
     if (check) {
       if (wx) k_update<T, true, true><<<grd, kThreadsUpd, 0, st>>>(g, A, acc, mass);
       else k_update<T, true, false><<<grd, kThreadsUpd, 0, st>>>(g, A, acc, mass);

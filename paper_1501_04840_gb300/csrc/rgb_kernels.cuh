@@ -489,3 +489,204 @@ __global__ void __launch_bounds__(256) k_solve_yc(Geo<T> g, T* __restrict__ hat,
 }
 
 }  // namespace dynot
+
+namespace dynot {
+
+// ---------------------------------------------------------------------------
+// K_D, tiled: the same steps as k_update for grids whose x and y axes are
+// Neumann, with every neighbour's prox result shared instead of recomputed.
+//
+// A block of 32 x 8 threads covers 32 x-columns and 8 y-rows; each thread owns
+// one (x, y) column with all C colour cells and streams over a chunk of time
+// planes, carrying the time neighbour in registers.  bbar at x+1 comes from
+// the next lane (warp shuffle), bbar at y+1 from the next row (shared memory),
+// bbar at c+1 from the same thread.  Blocks overlap by one column and one row:
+// the last lane and the last row only compute the prox their neighbours need
+// and write nothing, unless they sit on the last column / row of the grid.
+// A time chunk [t0, t0 + TC) also computes plane t0 + TC for bbar_f of its last face.
+// ---------------------------------------------------------------------------
+constexpr int kTX = 32, kTY = 8;
+
+template <typename T, int C, bool CHECK, bool WRITE_X>
+__global__ void __launch_bounds__(kTX * kTY) k_update_tiled(Geo<T> g, Arrays<T> A, int TC, double* __restrict__ acc,
+                                                             double* __restrict__ mass) {
+  __shared__ T sbb[2][kTY][kTX][C];   // bbar_y exchange, double-buffered by plane parity
+  __shared__ double smass[64];
+  const int lane = threadIdx.x, row = threadIdx.y;
+  const int x = blockIdx.x * (kTX - 1) + lane;
+  const int y = blockIdx.y * (kTY - 1) + row;
+  const int nch = (g.P + TC - 1) / TC;
+  const int b = blockIdx.z / nch;
+  const int t0 = (blockIdx.z % nch) * TC;
+  const int tend = min(t0 + TC, g.P);           // planes [t0, tend) are written
+  const int tlast = min(tend, g.P - 1);          // planes [t0, tlast] are computed
+  const bool vx = x < g.n1, vy = y < g.n2;
+  const bool live = vx && vy;
+  const int xs = vx ? x : g.n1 - 1, ys = vy ? y : g.n2 - 1;   // clamped for safe loads
+  const bool out = live && (lane < kTX - 1 || x == g.n1 - 1) && (row < kTY - 1 || y == g.n2 - 1);
+  const bool hasR = xs < g.n1 - 1, hasL = xs > 0;
+  const bool hasU = ys < g.n2 - 1, hasD = ys > 0;
+  const size_t S = g.S, n1 = g.n1, sy = g.n1;
+  const size_t sc = (size_t)g.n1 * g.n2;
+  const size_t colbase = (size_t)b * g.P * S + xs + sy * ys;   // + t S + c sc
+  const T s1 = g.s1, s2 = g.s2, scl = g.sc, sp = g.sp, ts = g.ts, half = T(0.5);
+  (void)n1;
+  if (CHECK) {
+    for (int i = threadIdx.x + kTX * threadIdx.y; i < 64; i += kTX * kTY) smass[i] = 0.0;
+  }
+  double r_db = 0, r_kx = 0, r_J = 0;
+
+  T phic[C], xfp[C], bbfp[C];
+  // state entering plane t0: phi(t0), x_f at the face t0 - 1 (or f0)
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const size_t i0 = colbase + (size_t)t0 * S + c * sc;
+    phic[c] = A.phi[i0];
+    if (t0 == 0) xfp[c] = A.f0[(size_t)b * S + xs + sy * ys + c * sc];
+    else xfp[c] = A.a[3][i0 - S] + sp * (phic[c] - A.phi[i0 - S]);
+    bbfp[c] = T(0);
+  }
+
+  for (int t = t0; t <= tlast; ++t) {
+    const size_t pb = colbase + (size_t)t * S;
+    const bool write_plane = t < tend;
+    T bb[C][4], bn[C][4], xr[C][4];
+    T phn[C];
+    T Uacc = 0, kxacc = 0;
+    // right faces of x^{r+1} for every channel
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const size_t i0 = pb + c * sc;
+      const T ph = phic[c];
+      // x face: phi(x+1) from the next lane; the last lane loads it
+      T phx = __shfl_down_sync(0xffffffffu, ph, 1);
+      if (lane == kTX - 1 && hasR) phx = A.phi[i0 + 1];
+      xr[c][0] = hasR ? A.a[0][i0] + s1 * (phx - ph) : T(0);
+      xr[c][1] = hasU ? A.a[1][i0] + s2 * (A.phi[i0 + sy] - ph) : T(0);
+      phn[c] = (t + 1 < g.P) ? A.phi[i0 + S] : T(0);
+      xr[c][3] = (t + 1 < g.P) ? A.a[3][i0] + sp * (phn[c] - ph) : A.f1[(size_t)b * S + xs + sy * ys + c * sc];
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int c1 = (c + 1 == C) ? 0 : c + 1;
+      const bool hasC = g.perc || (c + 1 < C);
+      xr[c][2] = hasC ? A.a[2][pb + c * sc] + scl * (phic[c1] - phic[c]) : T(0);
+    }
+    // left faces, interpolation to the cell, prox, dual update
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const size_t i0 = pb + c * sc;
+      T xlx = __shfl_up_sync(0xffffffffu, xr[c][0], 1);
+      if (lane == 0) xlx = hasL ? A.a[0][i0 - 1] + s1 * (phic[c] - A.phi[i0 - 1]) : T(0);
+      if (!hasL) xlx = T(0);
+      const T xly = hasD ? A.a[1][i0 - sy] + s2 * (phic[c] - A.phi[i0 - sy]) : T(0);
+      const int cm = (c == 0) ? C - 1 : c - 1;
+      const T xlc = (g.perc || c > 0) ? xr[cm][2] : T(0);
+      const T k0 = half * (xlx + xr[c][0]);
+      const T k1 = half * (xly + xr[c][1]);
+      const T k2 = half * (xlc + xr[c][2]);
+      const T k3 = half * (xfp[c] + xr[c][3]);
+      T bo[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) bo[k] = A.b[k][i0];
+      const T am0 = k0 + bo[0], am1 = k1 + bo[1], am2 = k2 + bo[2], af = k3 + bo[3];
+      T U0, U1, U2, V;
+      prox_J<T>(am0, am1, am2, af, g.sigma, U0, U1, U2, V);
+      bn[c][0] = am0 - U0;
+      bn[c][1] = am1 - U1;
+      bn[c][2] = am2 - U2;
+      bn[c][3] = af - V;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) bb[c][k] = T(2) * bn[c][k] - bo[k];
+      if (CHECK && out && write_plane) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double db = (double)bn[c][k] - (double)bo[k];
+          r_db += db * db;
+        }
+        r_kx += (double)k0 * k0 + (double)k1 * k1 + (double)k2 * k2 + (double)k3 * k3;
+        const double uu = (double)U0 * U0 + (double)U1 * U1 + (double)U2 * U2;
+        if (V > T(0)) r_J += uu / (2.0 * (double)V);
+      }
+    }
+    // neighbours' bbar: x+1 by shuffle, y+1 through shared memory
+    const int par = t & 1;
+#pragma unroll
+    for (int c = 0; c < C; ++c) sbb[par][row][lane][c] = bb[c][1];
+    __syncthreads();
+    if (out) {
+      // the f face t-1 (between planes t-1 and t), owned by this chunk when t > t0
+      if (t > t0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const size_t im = pb - S + c * sc;
+          A.an[3][im] = xfp[c] - ts * half * (bbfp[c] + bb[c][3]);
+        }
+      }
+    }
+    if (write_plane) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T bxn = __shfl_down_sync(0xffffffffu, bb[c][0], 1);
+        const T byn = (row + 1 < kTY) ? sbb[par][row + 1][lane][c] : T(0);
+        if (out) {
+          const size_t i0 = pb + c * sc;
+          const int c1 = (c + 1 == C) ? 0 : c + 1;
+          const bool hasC = g.perc || (c + 1 < C);
+          A.an[0][i0] = hasR ? xr[c][0] - ts * half * (bb[c][0] + bxn) : T(0);
+          A.an[1][i0] = hasU ? xr[c][1] - ts * half * (bb[c][1] + byn) : T(0);
+          A.an[2][i0] = hasC ? xr[c][2] - ts * half * (bb[c][2] + bb[c1][2]) : T(0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) A.bn[k][i0] = bn[c][k];
+          if (WRITE_X) {
+            A.x[0][i0] = xr[c][0];
+            A.x[1][i0] = xr[c][1];
+            A.x[2][i0] = xr[c][2];
+            A.x[3][i0] = (t + 1 < g.P) ? xr[c][3] : T(0);
+          }
+        }
+      }
+      if (CHECK && t + 1 < g.P) {
+        double m = 0;
+        if (out) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) m += (double)xr[c][3];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        if (lane == 0) atomicAdd(&smass[t], m);
+      }
+    }
+    // carry to the next plane
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      xfp[c] = xr[c][3];
+      bbfp[c] = bb[c][3];
+      phic[c] = phn[c];
+    }
+  }
+  if (CHECK) {
+    __shared__ double red[kTY][3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      r_db += __shfl_xor_sync(0xffffffffu, r_db, o);
+      r_kx += __shfl_xor_sync(0xffffffffu, r_kx, o);
+      r_J += __shfl_xor_sync(0xffffffffu, r_J, o);
+    }
+    if (lane == 0) {
+      red[row][0] = r_db;
+      red[row][1] = r_kx;
+      red[row][2] = r_J;
+    }
+    __syncthreads();
+    const int tid = threadIdx.x + kTX * threadIdx.y;
+    if (tid < 3) {
+      double s = 0;
+      for (int i = 0; i < kTY; ++i) s += red[i][tid];
+      atomicAdd(&acc[(size_t)b * kAcc + tid], s);
+    }
+    for (int t = t0 + tid; t < tend && t < g.P - 1; t += kTX * kTY) atomicAdd(&mass[(size_t)b * g.P + t], smass[t]);
+  }
+}
+
+}  // namespace dynot
