@@ -76,155 +76,174 @@ __device__ __forceinline__ void load_tables(c2<T>* tw, c2<T>* hw, const c2<T>* g
   }
 }
 
-// Rows of a shared-memory tile.  Row r starts at base + (r / W) * rs_hi + (r % W) * rs_lo,
-// element n of a row is at + n * es.  (W, rs_hi, rs_lo, es) describe both the
-// row-major x tile ([t][x]: W huge, rs_lo = ld, es = 1) and the column layout
-// of the y pass ([c][y][w]: rows are (c, w), es = W).
-template <typename T>
+// Rows of a shared-memory tile.  Row r = g*RW + j (j < RW) starts at
+// base + g*rs_hi + j*rs_lo; element n of a row sits at + n*ES.  RW = 1, ES = 1
+// describes the row-major x tile ([t][x], rs_hi = row length); RW = ES = W the
+// column layout of the y pass ([c][y][w]: rows are (c, w), rs_hi = n2*W, rs_lo = 1).
+template <typename T, int RW, int ES>
 struct Rows {
   T* base;
-  int W, rs_hi, rs_lo, es;
-  __device__ __forceinline__ T* row(int r) const { return base + (r / W) * rs_hi + (r % W) * rs_lo; }
+  int rs_hi, rs_lo;
+  static constexpr int es = ES;
+  __device__ __forceinline__ T* row(int r) const { return base + (r / RW) * rs_hi + (r % RW) * rs_lo; }
 };
 
-// Power-of-two DCT via the four-step DFT.  PFAST selects the work-item order:
-// false = element index fastest (rows contiguous in memory), true = row-pair
-// index fastest (rows interleaved, as in the y pass).  The scratch holds
-// npairs_per_chunk * N complex values.
-template <typename T, int N1, int N2, bool PFAST>
+// Power-of-two DCT via the four-step DFT for a block of NT threads.  PFAST
+// selects the work-item order: false = element index fastest (rows contiguous
+// in memory), true = row-pair index fastest (rows interleaved, as in the y
+// pass).  Pairs are processed in chunks of CP = NT / N1; the scratch holds
+// CP * N complex values.  Every index divisor is a compile-time constant.
+template <typename T, int N1, int N2, bool PFAST, int NT>
 struct DctPow2 {
   static constexpr int N = N1 * N2;
+  static constexpr int CP = NT / N1;
   static_assert((N1 & (N1 - 1)) == 0 && (N2 & (N2 - 1)) == 0, "power-of-two factors");
+  static_assert(CP >= 1 && CP * N1 == NT, "block size must be a multiple of N1");
 
-  __device__ static __forceinline__ int perm(int n) { return n < N / 2 ? 2 * n : 2 * N - 1 - 2 * n; }
-
-  // scratch address of (pair p, slot j in [0, N)) for a chunk of cp pairs
-  __device__ static __forceinline__ int sidx(int p, int j, int cp) { return PFAST ? j * cp + p : p * N + j; }
+  // scratch address of (pair p, slot j in [0, N))
+  __device__ static __forceinline__ int sidx(int p, int j) { return PFAST ? j * CP + p : p * N + j; }
   // transpose slot of (k1, n2) with an XOR swizzle against bank conflicts (element-fast order)
   __device__ static __forceinline__ int tslot(int k1, int n2) {
     return PFAST ? k1 * N2 + n2 : k1 * N2 + (n2 ^ (k1 & (N2 - 1)));
   }
+  // split a work item into (pair, index) with `per` indices per pair
+  template <int PER>
+  __device__ static __forceinline__ void split(int it, int& p, int& j) {
+    if (PFAST) { p = it % CP; j = it / CP; } else { p = it / PER; j = it % PER; }
+  }
 
-  // largest chunk of pairs such that pass 2 has one work item per thread
-  __device__ static __forceinline__ int chunk_pairs() { return blockDim.x / N1; }
-
-  __device__ static void forward(const Rows<T>& rows, int nrows, c2<T>* __restrict__ scr,
-                                 const c2<T>* __restrict__ tw, const c2<T>* __restrict__ hw) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+  template <class R>
+  __device__ static void forward(const R& rows, int nrows, c2<T>* __restrict__ scr, const c2<T>* __restrict__ tw,
+                                 const c2<T>* __restrict__ hw) {
+    const int tid = threadIdx.x;
     const int npairs = nrows / 2;
-    const int CP = chunk_pairs();
     for (int p0 = 0; p0 < npairs; p0 += CP) {
       const int cp = min(CP, npairs - p0);
       // pass 1: N1-point DFTs over n1 (stride N2), twiddle W_N^{n2 k1}
-      for (int it = tid; it < cp * N2; it += nt) {
+#pragma unroll
+      for (int q = 0; q < (CP * N2 + NT - 1) / NT; ++q) {
+        const int it = tid + q * NT;
         int p, n2;
-        if (PFAST) { n2 = it / cp; p = it - n2 * cp; } else { p = it / N2; n2 = it - p * N2; }
-        const T* ra = rows.row(2 * (p0 + p));
-        const T* rb = rows.row(2 * (p0 + p) + 1);
-        c2<T> z[N1];
+        split<N2>(it, p, n2);
+        if (it < CP * N2 && p < cp) {
+          const T* ra = rows.row(2 * (p0 + p));
+          const T* rb = rows.row(2 * (p0 + p) + 1);
+          c2<T> z[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) {
-          const int q = perm(N2 * n1 + n2) * rows.es;
-          z[n1] = mk2<T>(ra[q], rb[q]);
-        }
-        dft_reg<T, N1, N, false>(z, tw);
+          for (int n1 = 0; n1 < N1; ++n1) {
+            const int n = N2 * n1 + n2;
+            const int e = (n1 < N1 / 2 ? 2 * n : 2 * N - 1 - 2 * n) * R::es;   // Makhoul order
+            z[n1] = mk2<T>(ra[e], rb[e]);
+          }
+          dft_reg<T, N1, N, false>(z, tw);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          c2<T> v = z[k1];
-          if (k1 != 0) v = cmul<T>(v, tw[(n2 * k1) & (N - 1)]);
-          scr[sidx(p, tslot(k1, n2), cp)] = v;
+          for (int k1 = 0; k1 < N1; ++k1) {
+            c2<T> v = z[k1];
+            if (k1 != 0) v = cmul<T>(v, tw[n2 * k1]);
+            scr[sidx(p, tslot(k1, n2))] = v;
+          }
         }
       }
       __syncthreads();
       // pass 2: N2-point DFTs over n2 -> Z[k1 + N1 k2], in place (one item per thread)
       {
-        const int it = tid;
-        const bool act = it < cp * N1;
-        int p = 0, k1 = 0;
+        int p, k1;
+        split<N1>(tid, p, k1);
+        const bool act = p < cp;
         c2<T> y[N2];
         if (act) {
-          if (PFAST) { k1 = it / cp; p = it - k1 * cp; } else { p = it / N1; k1 = it - p * N1; }
 #pragma unroll
-          for (int n2 = 0; n2 < N2; ++n2) y[n2] = scr[sidx(p, tslot(k1, n2), cp)];
+          for (int n2 = 0; n2 < N2; ++n2) y[n2] = scr[sidx(p, tslot(k1, n2))];
           dft_reg<T, N2, N, false>(y, tw);
         }
         __syncthreads();
         if (act) {
 #pragma unroll
-          for (int k2 = 0; k2 < N2; ++k2) scr[sidx(p, k1 + N1 * k2, cp)] = y[k2];
+          for (int k2 = 0; k2 < N2; ++k2) scr[sidx(p, k1 + N1 * k2)] = y[k2];
         }
       }
       __syncthreads();
       // post: split the packed spectra and rotate by exp(-i pi k / (2N))
-      for (int it = tid; it < cp * N; it += nt) {
+#pragma unroll 4
+      for (int q = 0; q < CP * N / NT; ++q) {
+        const int it = tid + q * NT;
         int p, k;
-        if (PFAST) { k = it / cp; p = it - k * cp; } else { p = it / N; k = it - p * N; }
-        const c2<T> zk = scr[sidx(p, k, cp)];
-        const c2<T> zm = scr[sidx(p, (N - k) & (N - 1), cp)];
-        // V_a = (Z_k + conj Z_m)/2 ; V_b = (Z_k - conj Z_m)/(2i)
-        const T vax = T(0.5) * (zk.x + zm.x), vay = T(0.5) * (zk.y - zm.y);
-        const T vbx = T(0.5) * (zk.y + zm.y), vby = T(0.5) * (zm.x - zk.x);
-        const c2<T> h = hw[k];  // (cos, -sin) of pi k/(2N)
-        T* ra = rows.row(2 * (p0 + p));
-        T* rb = rows.row(2 * (p0 + p) + 1);
-        ra[k * rows.es] = h.x * vax - h.y * vay;
-        rb[k * rows.es] = h.x * vbx - h.y * vby;
+        split<N>(it, p, k);
+        if (p < cp) {
+          const c2<T> zk = scr[sidx(p, k)];
+          const c2<T> zm = scr[sidx(p, (N - k) & (N - 1))];
+          // V_a = (Z_k + conj Z_m)/2 ; V_b = (Z_k - conj Z_m)/(2i)
+          const T vax = T(0.5) * (zk.x + zm.x), vay = T(0.5) * (zk.y - zm.y);
+          const T vbx = T(0.5) * (zk.y + zm.y), vby = T(0.5) * (zm.x - zk.x);
+          const c2<T> h = hw[k];  // (cos, -sin) of pi k/(2N)
+          T* ra = rows.row(2 * (p0 + p));
+          T* rb = rows.row(2 * (p0 + p) + 1);
+          ra[k * R::es] = h.x * vax - h.y * vay;
+          rb[k * R::es] = h.x * vbx - h.y * vby;
+        }
       }
       __syncthreads();
     }
   }
 
-  __device__ static void inverse(const Rows<T>& rows, int nrows, c2<T>* __restrict__ scr,
-                                 const c2<T>* __restrict__ tw, const c2<T>* __restrict__ hw) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+  template <class R>
+  __device__ static void inverse(const R& rows, int nrows, c2<T>* __restrict__ scr, const c2<T>* __restrict__ tw,
+                                 const c2<T>* __restrict__ hw) {
+    const int tid = threadIdx.x;
     const int npairs = nrows / 2;
-    const int CP = chunk_pairs();
     const T invN = T(1) / T(N);
     for (int p0 = 0; p0 < npairs; p0 += CP) {
       const int cp = min(CP, npairs - p0);
       // pre + pass 1: V[k] = exp(i pi k/(2N)) (X[k] - i X[N-k]), Z = V_a + i V_b; inverse DFT over n1
-      for (int it = tid; it < cp * N2; it += nt) {
+#pragma unroll
+      for (int q = 0; q < (CP * N2 + NT - 1) / NT; ++q) {
+        const int it = tid + q * NT;
         int p, n2;
-        if (PFAST) { n2 = it / cp; p = it - n2 * cp; } else { p = it / N2; n2 = it - p * N2; }
-        const T* ra = rows.row(2 * (p0 + p));
-        const T* rb = rows.row(2 * (p0 + p) + 1);
-        c2<T> z[N1];
+        split<N2>(it, p, n2);
+        if (it < CP * N2 && p < cp) {
+          const T* ra = rows.row(2 * (p0 + p));
+          const T* rb = rows.row(2 * (p0 + p) + 1);
+          c2<T> z[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) {
-          const int k = N2 * n1 + n2;
-          const T xa = ra[k * rows.es], xb = rb[k * rows.es];
-          const T xam = k ? ra[(N - k) * rows.es] : T(0);
-          const T xbm = k ? rb[(N - k) * rows.es] : T(0);
-          const c2<T> h = hw[k];                 // conj(h) = (cos, +sin)
-          // V_a = (h.x - i h.y) (xa - i xam)
-          const T vax = h.x * xa - h.y * xam, vay = -h.x * xam - h.y * xa;
-          const T vbx = h.x * xb - h.y * xbm, vby = -h.x * xbm - h.y * xb;
-          z[n1] = mk2<T>(vax - vby, vay + vbx);  // V_a + i V_b
-        }
-        dft_reg<T, N1, N, true>(z, tw);
+          for (int n1 = 0; n1 < N1; ++n1) {
+            const int k = N2 * n1 + n2;
+            const T xa = ra[k * R::es], xb = rb[k * R::es];
+            const T xam = k ? ra[(N - k) * R::es] : T(0);
+            const T xbm = k ? rb[(N - k) * R::es] : T(0);
+            const c2<T> h = hw[k];                 // conj(h) = (cos, +sin)
+            // V_a = (h.x - i h.y) (xa - i xam)
+            const T vax = h.x * xa - h.y * xam, vay = -h.x * xam - h.y * xa;
+            const T vbx = h.x * xb - h.y * xbm, vby = -h.x * xbm - h.y * xb;
+            z[n1] = mk2<T>(vax - vby, vay + vbx);  // V_a + i V_b
+          }
+          dft_reg<T, N1, N, true>(z, tw);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          c2<T> v = z[k1];
-          if (k1 != 0) v = cmulc<T>(v, tw[(n2 * k1) & (N - 1)]);
-          scr[sidx(p, tslot(k1, n2), cp)] = v;
+          for (int k1 = 0; k1 < N1; ++k1) {
+            c2<T> v = z[k1];
+            if (k1 != 0) v = cmulc<T>(v, tw[n2 * k1]);
+            scr[sidx(p, tslot(k1, n2))] = v;
+          }
         }
       }
       __syncthreads();
       // pass 2: inverse N2-point DFTs; v = IDFT(Z)/N; x[perm(m)] = v[m]
-      for (int it = tid; it < cp * N1; it += nt) {
+      {
         int p, k1;
-        if (PFAST) { k1 = it / cp; p = it - k1 * cp; } else { p = it / N1; k1 = it - p * N1; }
-        c2<T> y[N2];
+        split<N1>(tid, p, k1);
+        if (p < cp) {
+          c2<T> y[N2];
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) y[n2] = scr[sidx(p, tslot(k1, n2), cp)];
-        dft_reg<T, N2, N, true>(y, tw);
-        T* ra = rows.row(2 * (p0 + p));
-        T* rb = rows.row(2 * (p0 + p) + 1);
+          for (int n2 = 0; n2 < N2; ++n2) y[n2] = scr[sidx(p, tslot(k1, n2))];
+          dft_reg<T, N2, N, true>(y, tw);
+          T* ra = rows.row(2 * (p0 + p));
+          T* rb = rows.row(2 * (p0 + p) + 1);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-          const int q = perm(k1 + N1 * k2) * rows.es;
-          ra[q] = y[k2].x * invN;
-          rb[q] = y[k2].y * invN;
+          for (int k2 = 0; k2 < N2; ++k2) {
+            const int m = k1 + N1 * k2;
+            const int e = (k2 < N2 / 2 ? 2 * m : 2 * N - 1 - 2 * m) * R::es;
+            ra[e] = y[k2].x * invN;
+            rb[e] = y[k2].y * invN;
+          }
         }
       }
       __syncthreads();
@@ -235,9 +254,9 @@ struct DctPow2 {
 // Dense DCT of arbitrary length along rows: cos4[m] = cos(pi m / (2N)), m < 4N.
 // scr holds one chunk of rows * N values.  Forward X[k] = sum_n x[n] cos4[k(2n+1) mod 4N];
 // inverse x[n] = (1/N) (X[0] + 2 sum_{k>=1} X[k] cos4[k(2n+1) mod 4N]).
-template <typename T, bool PFAST>
-__device__ void dct_dense_rows(const Rows<T>& rows, int nrows, int N, bool inverse, T* __restrict__ scr,
-                               int scr_cap, const T* __restrict__ cos4) {
+template <typename T, bool PFAST, class R>
+__device__ void dct_dense_rows(const R& rows, int nrows, int N, bool inverse, T* __restrict__ scr, int scr_cap,
+                               const T* __restrict__ cos4) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int M4 = 4 * N;
   const int CR = max(1, scr_cap / N);
@@ -252,7 +271,7 @@ __device__ void dct_dense_rows(const Rows<T>& rows, int nrows, int N, bool inver
         int m = k;  // k (2n+1) mod 4N, stepping n
         const int step = (2 * k) % M4;
         for (int n = 0; n < N; ++n) {
-          acc += x[n * rows.es] * cos4[m];
+          acc += x[n * R::es] * cos4[m];
           m += step;
           if (m >= M4) m -= M4;
         }
@@ -265,7 +284,7 @@ __device__ void dct_dense_rows(const Rows<T>& rows, int nrows, int N, bool inver
         for (int j = 1; j < N; ++j) {
           m += step;
           if (m >= M4) m -= M4;
-          acc += x[j * rows.es] * cos4[m];
+          acc += x[j * R::es] * cos4[m];
         }
         acc *= T(2) / T(N);
       }
@@ -275,7 +294,7 @@ __device__ void dct_dense_rows(const Rows<T>& rows, int nrows, int N, bool inver
     for (int it = tid; it < cr * N; it += nt) {
       int r, k;
       if (PFAST) { k = it / cr; r = it - k * cr; } else { r = it / N; k = it - r * N; }
-      rows.row(r0 + r)[k * rows.es] = scr[PFAST ? k * cr + r : r * N + k];
+      rows.row(r0 + r)[k * R::es] = scr[PFAST ? k * cr + r : r * N + k];
     }
     __syncthreads();
   }
@@ -286,16 +305,32 @@ __device__ void dct_dense_rows(const Rows<T>& rows, int nrows, int N, bool inver
 // padding: out[k] = sum_t Mt[k*PMAX + t] in[t].
 template <typename T, int PMAX>
 __device__ void dct_cols(T* __restrict__ buf, int ld, int ncols, int P, const T* __restrict__ Mt) {
+  static_assert(PMAX % 4 == 0, "PMAX must be a multiple of 4");
   for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
     T v[PMAX];
 #pragma unroll
     for (int t = 0; t < PMAX; ++t) v[t] = (t < P) ? buf[t * ld + col] : T(0);
     for (int k = 0; k < P; ++k) {
       const T* row = Mt + k * PMAX;
-      T acc = 0;
+      T acc0 = 0, acc1 = 0;
+      if constexpr (sizeof(T) == 4) {
+        const float4* r4 = reinterpret_cast<const float4*>(row);
 #pragma unroll
-      for (int t = 0; t < PMAX; ++t) acc = fma(row[t], v[t], acc);
-      buf[k * ld + col] = acc;
+        for (int t = 0; t < PMAX / 4; ++t) {
+          const float4 m = r4[t];
+          acc0 = fma(m.x, v[4 * t], acc0);
+          acc1 = fma(m.y, v[4 * t + 1], acc1);
+          acc0 = fma(m.z, v[4 * t + 2], acc0);
+          acc1 = fma(m.w, v[4 * t + 3], acc1);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < PMAX; t += 2) {
+          acc0 = fma(row[t], v[t], acc0);
+          acc1 = fma(row[t + 1], v[t + 1], acc1);
+        }
+      }
+      buf[k * ld + col] = acc0 + acc1;
     }
   }
 }

@@ -18,7 +18,7 @@ namespace dynot {
 
 constexpr int kThreadsXt = 256;
 constexpr int kThreadsUpd = 128;
-constexpr int kW = 16;  // x-strip width of the y/colour pass
+constexpr int kW = 8;   // x-strip width of the y/colour pass
 
 inline int pmax_for(int P) { return P <= 16 ? 16 : (P <= 32 ? 32 : 64); }
 inline bool fft_len(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
@@ -137,14 +137,11 @@ struct Plan final : PlanBase {
       if (e) cudaEventDestroy(e);
   }
 
-  size_t xt_smem() const {
-    size_t s = rnd16(sizeof(T) * (size_t)(P + 1) * n1) + rnd16(sizeof(c2<T>) * (size_t)scrA) +
-               2 * rnd16(sizeof(c2<T>) * n1) + rnd16(sizeof(T) * (size_t)P * pmax) + rnd16(sizeof(T) * 4 * n1);
-    return s;
-  }
+  size_t xt_smem() const { return xt_layout<T>(nullptr, nullptr, P, n1, pmax, scrA, !fft_len(n1)); }
   size_t yc_smem() const {
-    return rnd16(sizeof(T) * (size_t)C * n2 * kW) + rnd16(sizeof(c2<T>) * (size_t)scrB) +
-           2 * rnd16(sizeof(c2<T>) * n2) + rnd16(sizeof(T) * 4 * n2) + rnd16(sizeof(T) * n2);
+    T *t0, *t1, *t2;
+    c2<T> *c0, *c1, *c3;
+    return yc_layout<T>(nullptr, C, n2, kW, scrB, !fft_len(n2), &t0, &c0, &c1, &c3, &t1, &t2);
   }
 
   ot_status init() override {

@@ -29,6 +29,9 @@ __device__ __forceinline__ size_t cidx(const Geo<T>& g, int b, int t, int ix, in
   return ((size_t)(b * g.P + t) * g.S) + (size_t)ix + (size_t)g.n1 * ((size_t)iy + (size_t)g.n2 * ic);
 }
 
+__device__ __forceinline__ float fdiv_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv_fast(double a, double b) { return a / b; }
+
 // Per-cell proximal map of J (section 3, step 2):
 //   argmin_{u,v} |u|^2/(2v) + sigma/2 |u - a_m|^2 + sigma/2 (v - a_f)^2.
 // With z = sigma v, e = sigma a_f and d = sigma^2 |a_m|^2 / 2 the cubic of the
@@ -51,20 +54,22 @@ __device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T& u0
   const T c = T(1) + e;
   T z;
   if (c > T(0)) {
-    const T del = min(cbrt(d), d / (c * c));
+    const T del = min(cbrt(d), fdiv_fast(d, c * c));
     z = e + del;
   } else {
-    z = min(cbrt(d), sqrt(d / (-c))) - T(1);
+    z = min(cbrt(d), sqrt(fdiv_fast(d, -c))) - T(1);
   }
   z = max(z, T(0));
   const T eps = sizeof(T) == 4 ? T(2e-7) : T(4e-16);
+  // Newton's method corrects its own rounding, so its steps use the fast
+  // division; the result below uses the correctly rounded one.
 #pragma unroll 1
   for (int it = 0; it < 40; ++it) {
     const T w = T(1) + z;
     const T zme = z - e;
     const T q = w * w * zme - d;
     const T dq = w * (T(2) * zme + w);
-    const T step = q / dq;
+    const T step = fdiv_fast(q, dq);
     z -= step;
     if (!(fabs(step) > eps * z)) break;
   }
@@ -285,28 +290,35 @@ struct XtTables {
   const void* cos4;  // [4 n1]
 };
 
+// Shared-memory layout of the x/t kernels; the same function sizes it on the host.
+// The FFT path needs the twiddle tables, the dense path the cosine table.
 template <typename T>
-__device__ __forceinline__ void xt_carve(XtSmem<T>& s, char* sm, int P, int ld, int n1, int PMAX, int scr_elems) {
+__host__ __device__ __forceinline__ size_t xt_layout(XtSmem<T>* s, char* sm, int P, int n1, int PMAX, int scr_elems,
+                                                     bool dense) {
   size_t off = 0;
   auto take = [&](size_t bytes) { char* p = sm + off; off += (bytes + 15) & ~size_t(15); return p; };
-  s.tile = (T*)take(sizeof(T) * (size_t)(P + 1) * ld);
-  s.scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
-  s.tw = (c2<T>*)take(sizeof(c2<T>) * n1);
-  s.hw = (c2<T>*)take(sizeof(c2<T>) * n1);
-  s.Mt = (T*)take(sizeof(T) * (size_t)P * PMAX);
-  s.cos4 = (T*)take(sizeof(T) * 4 * n1);
+  T* tile = (T*)take(sizeof(T) * (size_t)(P + 1) * n1);
+  c2<T>* scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
+  c2<T>* tw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n1);
+  c2<T>* hw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n1);
+  T* Mt = (T*)take(sizeof(T) * (size_t)P * PMAX);
+  T* cos4 = dense ? (T*)take(sizeof(T) * 4 * n1) : nullptr;
+  if (s) {
+    s->tile = tile; s->scr = scr; s->tw = tw; s->hw = hw; s->Mt = Mt; s->cos4 = cos4;
+  }
+  return off;
 }
 
 // N1 == 0 selects the dense x transform.
 template <typename T, int N1, int N2, int PMAX>
-__global__ void __launch_bounds__(256) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
+__global__ void __launch_bounds__(256, 3) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
                                                     const T* __restrict__ f0, const T* __restrict__ f1,
                                                     T* __restrict__ rhat, XtTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int y = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   const int n1 = g.n1, P = g.P;
   XtSmem<T> s;
-  xt_carve<T>(s, smraw, P, n1, n1, PMAX, scr_elems);
+  xt_layout<T>(&s, smraw, P, n1, PMAX, scr_elems, N1 == 0);
   const T* ax = ap.p[0];
   const T* ay = ap.p[1];
   const T* ac = ap.p[2];
@@ -318,18 +330,30 @@ __global__ void __launch_bounds__(256) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
   // divergence of a and the time difference with the boundary densities
   const int ym = y > 0 ? y - 1 : (g.per2 ? g.n2 - 1 : -1);
   const int cm = c > 0 ? c - 1 : (g.perc ? g.C - 1 : -1);
+  const size_t S = g.S;
+  const size_t rowbase = (size_t)b * P * S + (size_t)n1 * (y + (size_t)g.n2 * c);
+  const long long dy = ym >= 0 ? (long long)n1 * (ym - y) : 0;                 // offset to the y-1 row
+  const long long dc = cm >= 0 ? (long long)n1 * g.n2 * (cm - c) : 0;          // offset to channel c-1
   for (int x = threadIdx.x; x < n1; x += blockDim.x) {
     const int xm = x > 0 ? x - 1 : (g.per1 ? n1 - 1 : -1);
-    const size_t sb = (size_t)b * g.S + x + (size_t)n1 * (y + (size_t)g.n2 * c);
-    T fprev = f0[sb];
+    const size_t sb = (size_t)b * S + x + (size_t)n1 * (y + (size_t)g.n2 * c);
+    const T f0v = f0[sb], f1v = f1[sb];
+    const T* px = ax + rowbase + x;
+    const T* py = ay + rowbase + x;
+    const T* pc = ac + rowbase + x;
+    const T* pf = af + rowbase + x;
+    const T* pxm = px + (xm - x);   // dereferenced only when the face exists
+    const T* pym = py + dy;
+    const T* pcm = pc + dc;
+#pragma unroll 4
     for (int t = 0; t < P; ++t) {
-      const size_t i0 = cidx(g, b, t, x, y, c);
-      T r = g.s1 * (ax[i0] - (xm >= 0 ? ax[cidx(g, b, t, xm, y, c)] : T(0)));
-      r += g.s2 * (ay[i0] - (ym >= 0 ? ay[cidx(g, b, t, x, ym, c)] : T(0)));
-      r += g.sc * (ac[i0] - (cm >= 0 ? ac[cidx(g, b, t, x, y, cm)] : T(0)));
-      const T fnext = (t == P - 1) ? f1[sb] : af[i0];
+      const size_t o = (size_t)t * S;
+      T r = g.s1 * (px[o] - (xm >= 0 ? pxm[o] : T(0)));
+      r += g.s2 * (py[o] - (ym >= 0 ? pym[o] : T(0)));
+      r += g.sc * (pc[o] - (cm >= 0 ? pcm[o] : T(0)));
+      const T fnext = (t == P - 1) ? f1v : pf[o];
+      const T fprev = (t == 0) ? f0v : pf[o - S];
       r += g.sp * (fnext - fprev);
-      fprev = fnext;
       s.tile[t * n1 + x] = r;
     }
   }
@@ -337,9 +361,9 @@ __global__ void __launch_bounds__(256) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
   if (Pr != P)
     for (int x = threadIdx.x; x < n1; x += blockDim.x) s.tile[P * n1 + x] = T(0);
   __syncthreads();
-  Rows<T> rows{s.tile, 1 << 30, 0, n1, 1};
+  Rows<T, 1, 1> rows{s.tile, n1, 0};
   if constexpr (N1 > 0) {
-    DctPow2<T, N1, N2, false>::forward(rows, Pr, s.scr, s.tw, s.hw);
+    DctPow2<T, N1, N2, false, 256>::forward(rows, Pr, s.scr, s.tw, s.hw);
   } else {
     dct_dense_rows<T, false>(rows, P, n1, false, (T*)s.scr, 2 * scr_elems, s.cos4);
   }
@@ -352,13 +376,13 @@ __global__ void __launch_bounds__(256) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
 
 // K_C: inverse DCT along t and x -> phi
 template <typename T, int N1, int N2, int PMAX>
-__global__ void __launch_bounds__(256) k_inv_xt(Geo<T> g, const T* __restrict__ phihat, T* __restrict__ phi,
+__global__ void __launch_bounds__(256, 3) k_inv_xt(Geo<T> g, const T* __restrict__ phihat, T* __restrict__ phi,
                                                 XtTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int y = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
   const int n1 = g.n1, P = g.P;
   XtSmem<T> s;
-  xt_carve<T>(s, smraw, P, n1, n1, PMAX, scr_elems);
+  xt_layout<T>(&s, smraw, P, n1, PMAX, scr_elems, N1 == 0);
   if (N1) load_tables<T>(s.tw, s.hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
   else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) s.cos4[j] = ((const T*)tb.cos4)[j];
   for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_i)[j];
@@ -371,9 +395,9 @@ __global__ void __launch_bounds__(256) k_inv_xt(Geo<T> g, const T* __restrict__ 
   if (Pr != P)
     for (int x = threadIdx.x; x < n1; x += blockDim.x) s.tile[P * n1 + x] = T(0);
   __syncthreads();
-  Rows<T> rows{s.tile, 1 << 30, 0, n1, 1};
+  Rows<T, 1, 1> rows{s.tile, n1, 0};
   if constexpr (N1 > 0) {
-    DctPow2<T, N1, N2, false>::inverse(rows, Pr, s.scr, s.tw, s.hw);
+    DctPow2<T, N1, N2, false, 256>::inverse(rows, Pr, s.scr, s.tw, s.hw);
   } else {
     dct_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, s.cos4);
   }
@@ -403,20 +427,31 @@ struct YcTables {
 
 constexpr int kMaxC = 4;
 
+// Shared-memory layout of the y/colour kernel; the same function sizes it on the host.
+template <typename T>
+__host__ __device__ __forceinline__ size_t yc_layout(char* sm, int C, int n2, int W, int scr_elems, bool dense,
+                                                     T** tile, c2<T>** scr, c2<T>** tw, c2<T>** hw, T** cos4,
+                                                     T** l2) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = sm + off; off += (bytes + 15) & ~size_t(15); return p; };
+  *tile = (T*)take(sizeof(T) * (size_t)C * n2 * W);   // [c][y][w]
+  *scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
+  *tw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n2);
+  *hw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n2);
+  *cos4 = dense ? (T*)take(sizeof(T) * 4 * n2) : nullptr;
+  *l2 = (T*)take(sizeof(T) * n2);
+  return off;
+}
+
 template <typename T, int M1, int M2, int W>
-__global__ void __launch_bounds__(256) k_solve_yc(Geo<T> g, T* __restrict__ hat, YcTables tb, int scr_elems) {
+__global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ hat, YcTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int x0 = blockIdx.x * W, kt = blockIdx.y, b = blockIdx.z;
   const int n1 = g.n1, n2 = g.n2, C = g.C;
   const int w_act = min(W, n1 - x0);
-  size_t off = 0;
-  auto take = [&](size_t bytes) { char* p = smraw + off; off += (bytes + 15) & ~size_t(15); return p; };
-  T* tile = (T*)take(sizeof(T) * (size_t)C * n2 * W);       // [c][y][w]
-  c2<T>* scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
-  c2<T>* tw = (c2<T>*)take(sizeof(c2<T>) * n2);
-  c2<T>* hw = (c2<T>*)take(sizeof(c2<T>) * n2);
-  T* cos4 = (T*)take(sizeof(T) * 4 * n2);
-  T* l2 = (T*)take(sizeof(T) * n2);
+  T *tile, *cos4, *l2;
+  c2<T> *scr, *tw, *hw;
+  yc_layout<T>(smraw, C, n2, W, scr_elems, M1 == 0, &tile, &scr, &tw, &hw, &cos4, &l2);
   if (M1) load_tables<T>(tw, hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n2);
   else for (int j = threadIdx.x; j < 4 * n2; j += blockDim.x) cos4[j] = ((const T*)tb.cos4)[j];
   for (int j = threadIdx.x; j < n2; j += blockDim.x) l2[j] = ((const T*)tb.lam2)[j];
@@ -427,10 +462,10 @@ __global__ void __launch_bounds__(256) k_solve_yc(Geo<T> g, T* __restrict__ hat,
     tile[i] = (w < w_act) ? hat[cidx(g, b, kt, x0 + w, y, c)] : T(0);
   }
   __syncthreads();
-  Rows<T> rows{tile, W, n2 * W, 1, W};
+  Rows<T, W, W> rows{tile, n2 * W, 1};
   const int nrows = C * W;
   if constexpr (M1 > 0) {
-    DctPow2<T, M1, M2, true>::forward(rows, nrows, scr, tw, hw);
+    DctPow2<T, M1, M2, true, 256>::forward(rows, nrows, scr, tw, hw);
   } else {
     dct_dense_rows<T, true>(rows, nrows, n2, false, (T*)scr, 2 * scr_elems, cos4);
   }
@@ -477,7 +512,7 @@ __global__ void __launch_bounds__(256) k_solve_yc(Geo<T> g, T* __restrict__ hat,
   }
   __syncthreads();
   if constexpr (M1 > 0) {
-    DctPow2<T, M1, M2, true>::inverse(rows, nrows, scr, tw, hw);
+    DctPow2<T, M1, M2, true, 256>::inverse(rows, nrows, scr, tw, hw);
   } else {
     dct_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, cos4);
   }
