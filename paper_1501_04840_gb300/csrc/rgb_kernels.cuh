@@ -60,7 +60,11 @@ __device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T& u0
     z = min(cbrt(d), sqrt(fdiv_fast(d, -c))) - T(1);
   }
   z = max(z, T(0));
-  const T eps = sizeof(T) == 4 ? T(2e-7) : T(4e-16);
+  // Stop when the step is below a few units in the last place of the data
+  // scale |e| + d + z: near e + d = 0 the root cannot be resolved more finely
+  // in this precision, and a purely relative test would never be met there.
+  const T tol = (sizeof(T) == 4 ? T(4.0 / 16777216.0) : T(4.0 / 9007199254740992.0)) * (fabs(e) + d);
+  const T eps = sizeof(T) == 4 ? T(4.0 / 16777216.0) : T(4.0 / 9007199254740992.0);
   // Newton's method corrects its own rounding, so its steps use the fast
   // division; the result below uses the correctly rounded one.
 #pragma unroll 1
@@ -71,7 +75,7 @@ __device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T& u0
     const T dq = w * (T(2) * zme + w);
     const T step = fdiv_fast(q, dq);
     z -= step;
-    if (!(fabs(step) > eps * z)) break;
+    if (!(fabs(step) > eps * z + tol)) break;
   }
   z = max(z, T(0));
   const T r = z / (T(1) + z);
