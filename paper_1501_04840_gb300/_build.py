@@ -17,6 +17,8 @@ LIB = os.path.join(HERE, "libdynot.so")
 UNITS = ["api", "plan_f32", "plan_f64", "noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC"]
+# extra nvcc flags for tuning experiments (e.g. -DDYNOT_UPD_MINB=2); empty by default
+EXTRA = os.environ.get("DYNOT_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:
@@ -48,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_unit(u):
         src = os.path.join(CSRC, u + ".cu")
         obj = os.path.join(BUILD, u + ".o")
-        cmd = [nvcc] + FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + FLAGS + EXTRA + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (u, r.stdout, r.stderr))

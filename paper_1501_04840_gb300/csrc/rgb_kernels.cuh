@@ -545,10 +545,13 @@ namespace dynot {
 // A time chunk [t0, t0 + TC) also computes plane t0 + TC for bbar_f of its last face.
 // ---------------------------------------------------------------------------
 constexpr int kTX = 32, kTY = 8;
+#ifndef DYNOT_UPD_MINB
+#define DYNOT_UPD_MINB 3   // blocks per SM the tiled update is compiled for
+#endif
 
 template <typename T, int C, bool CHECK, bool WRITE_X>
-__global__ void __launch_bounds__(kTX * kTY) k_update_tiled(Geo<T> g, Arrays<T> A, int TC, double* __restrict__ acc,
-                                                             double* __restrict__ mass) {
+__global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<T> g, Arrays<T> A, int TC,
+                                                                double* __restrict__ acc, double* __restrict__ mass) {
   __shared__ T sbb[2][kTY][kTX][C];   // bbar_y exchange, double-buffered by plane parity
   __shared__ double smass[64];
   const int lane = threadIdx.x, row = threadIdx.y;
@@ -565,11 +568,31 @@ __global__ void __launch_bounds__(kTX * kTY) k_update_tiled(Geo<T> g, Arrays<T> 
   const bool out = live && (lane < kTX - 1 || x == g.n1 - 1) && (row < kTY - 1 || y == g.n2 - 1);
   const bool hasR = xs < g.n1 - 1, hasL = xs > 0;
   const bool hasU = ys < g.n2 - 1, hasD = ys > 0;
-  const size_t S = g.S, n1 = g.n1, sy = g.n1;
-  const size_t sc = (size_t)g.n1 * g.n2;
-  const size_t colbase = (size_t)b * g.P * S + xs + sy * ys;   // + t S + c sc
+  // 32-bit offsets from per-thread column bases (problem sizes stay below 2^31 cells)
+  const int S = g.S, sy = g.n1, sc = g.n1 * g.n2;
+  const size_t col = (size_t)b * g.P * S + xs + (size_t)sy * ys;
+  const size_t col2 = (size_t)b * S + xs + (size_t)sy * ys;
+  const T* __restrict__ pa0 = A.a[0] + col;
+  const T* __restrict__ pa1 = A.a[1] + col;
+  const T* __restrict__ pa2 = A.a[2] + col;
+  const T* __restrict__ pa3 = A.a[3] + col;
+  const T* __restrict__ pb0 = A.b[0] + col;
+  const T* __restrict__ pb1 = A.b[1] + col;
+  const T* __restrict__ pb2 = A.b[2] + col;
+  const T* __restrict__ pb3 = A.b[3] + col;
+  const T* __restrict__ pph = A.phi + col;
+  const T* __restrict__ pf0 = A.f0 + col2;
+  const T* __restrict__ pf1 = A.f1 + col2;
+  T* __restrict__ qa0 = A.an[0] + col;
+  T* __restrict__ qa1 = A.an[1] + col;
+  T* __restrict__ qa2 = A.an[2] + col;
+  T* __restrict__ qa3 = A.an[3] + col;
+  T* __restrict__ qb0 = A.bn[0] + col;
+  T* __restrict__ qb1 = A.bn[1] + col;
+  T* __restrict__ qb2 = A.bn[2] + col;
+  T* __restrict__ qb3 = A.bn[3] + col;
   const T s1 = g.s1, s2 = g.s2, scl = g.sc, sp = g.sp, ts = g.ts, half = T(0.5);
-  (void)n1;
+  const bool perc = g.perc;
   if (CHECK) {
     for (int i = threadIdx.x + kTX * threadIdx.y; i < 64; i += kTX * kTY) smass[i] = 0.0;
   }
@@ -579,56 +602,68 @@ __global__ void __launch_bounds__(kTX * kTY) k_update_tiled(Geo<T> g, Arrays<T> 
   // state entering plane t0: phi(t0), x_f at the face t0 - 1 (or f0)
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    const size_t i0 = colbase + (size_t)t0 * S + c * sc;
-    phic[c] = A.phi[i0];
-    if (t0 == 0) xfp[c] = A.f0[(size_t)b * S + xs + sy * ys + c * sc];
-    else xfp[c] = A.a[3][i0 - S] + sp * (phic[c] - A.phi[i0 - S]);
+    const int o = t0 * S + c * sc;
+    phic[c] = pph[o];
+    xfp[c] = (t0 == 0) ? pf0[c * sc] : pa3[o - S] + sp * (phic[c] - pph[o - S]);
     bbfp[c] = T(0);
   }
 
+#pragma unroll 1
   for (int t = t0; t <= tlast; ++t) {
-    const size_t pb = colbase + (size_t)t * S;
+    const int pt = t * S;
     const bool write_plane = t < tend;
-    T bb[C][4], bn[C][4], xr[C][4];
-    T phn[C];
-    T Uacc = 0, kxacc = 0;
-    // right faces of x^{r+1} for every channel
+    const bool tnext = t + 1 < g.P;
+    T bb[C][4], bn[C][4], xr[C][4], phn[C];
+    // loads of this plane (all channels first, so that they overlap)
+    T la0[C], la1[C], la2[C], la3[C], lb[C][4], phy[C], phd[C], la1d[C], la0l[C], phl[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const size_t i0 = pb + c * sc;
+      const int o = pt + c * sc;
+      la0[c] = pa0[o];
+      la1[c] = pa1[o];
+      la2[c] = pa2[o];
+      la3[c] = pa3[o];
+      lb[c][0] = pb0[o];
+      lb[c][1] = pb1[o];
+      lb[c][2] = pb2[o];
+      lb[c][3] = pb3[o];
+      phn[c] = tnext ? pph[o + S] : T(0);
+      phy[c] = hasU ? pph[o + sy] : T(0);
+      phd[c] = hasD ? pph[o - sy] : T(0);
+      la1d[c] = hasD ? pa1[o - sy] : T(0);
+      la0l[c] = (lane == 0 && hasL) ? pa0[o - 1] : T(0);
+      phl[c] = (lane == 0 && hasL) ? pph[o - 1] : T(0);
+    }
+    // right faces of x^{r+1}
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
       const T ph = phic[c];
-      // x face: phi(x+1) from the next lane; the last lane loads it
       T phx = __shfl_down_sync(0xffffffffu, ph, 1);
-      if (lane == kTX - 1 && hasR) phx = A.phi[i0 + 1];
-      xr[c][0] = hasR ? A.a[0][i0] + s1 * (phx - ph) : T(0);
-      xr[c][1] = hasU ? A.a[1][i0] + s2 * (A.phi[i0 + sy] - ph) : T(0);
-      phn[c] = (t + 1 < g.P) ? A.phi[i0 + S] : T(0);
-      xr[c][3] = (t + 1 < g.P) ? A.a[3][i0] + sp * (phn[c] - ph) : A.f1[(size_t)b * S + xs + sy * ys + c * sc];
+      if (lane == kTX - 1 && hasR) phx = pph[pt + c * sc + 1];
+      xr[c][0] = hasR ? la0[c] + s1 * (phx - ph) : T(0);
+      xr[c][1] = hasU ? la1[c] + s2 * (phy[c] - ph) : T(0);
+      xr[c][3] = tnext ? la3[c] + sp * (phn[c] - ph) : pf1[c * sc];
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const int c1 = (c + 1 == C) ? 0 : c + 1;
-      const bool hasC = g.perc || (c + 1 < C);
-      xr[c][2] = hasC ? A.a[2][pb + c * sc] + scl * (phic[c1] - phic[c]) : T(0);
+      const bool hasC = perc || (c + 1 < C);
+      xr[c][2] = hasC ? la2[c] + scl * (phic[c1] - phic[c]) : T(0);
     }
     // left faces, interpolation to the cell, prox, dual update
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const size_t i0 = pb + c * sc;
       T xlx = __shfl_up_sync(0xffffffffu, xr[c][0], 1);
-      if (lane == 0) xlx = hasL ? A.a[0][i0 - 1] + s1 * (phic[c] - A.phi[i0 - 1]) : T(0);
+      if (lane == 0) xlx = la0l[c] + s1 * (phic[c] - phl[c]);
       if (!hasL) xlx = T(0);
-      const T xly = hasD ? A.a[1][i0 - sy] + s2 * (phic[c] - A.phi[i0 - sy]) : T(0);
+      const T xly = hasD ? la1d[c] + s2 * (phic[c] - phd[c]) : T(0);
       const int cm = (c == 0) ? C - 1 : c - 1;
-      const T xlc = (g.perc || c > 0) ? xr[cm][2] : T(0);
+      const T xlc = (perc || c > 0) ? xr[cm][2] : T(0);
       const T k0 = half * (xlx + xr[c][0]);
       const T k1 = half * (xly + xr[c][1]);
       const T k2 = half * (xlc + xr[c][2]);
       const T k3 = half * (xfp[c] + xr[c][3]);
-      T bo[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) bo[k] = A.b[k][i0];
-      const T am0 = k0 + bo[0], am1 = k1 + bo[1], am2 = k2 + bo[2], af = k3 + bo[3];
+      const T am0 = k0 + lb[c][0], am1 = k1 + lb[c][1], am2 = k2 + lb[c][2], af = k3 + lb[c][3];
       T U0, U1, U2, V;
       prox_J<T>(am0, am1, am2, af, g.sigma, U0, U1, U2, V);
       bn[c][0] = am0 - U0;
@@ -636,11 +671,11 @@ __global__ void __launch_bounds__(kTX * kTY) k_update_tiled(Geo<T> g, Arrays<T> 
       bn[c][2] = am2 - U2;
       bn[c][3] = af - V;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) bb[c][k] = T(2) * bn[c][k] - bo[k];
+      for (int k = 0; k < 4; ++k) bb[c][k] = T(2) * bn[c][k] - lb[c][k];
       if (CHECK && out && write_plane) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const double db = (double)bn[c][k] - (double)bo[k];
+          const double db = (double)bn[c][k] - (double)lb[c][k];
           r_db += db * db;
         }
         r_kx += (double)k0 * k0 + (double)k1 * k1 + (double)k2 * k2 + (double)k3 * k3;
@@ -653,15 +688,10 @@ __global__ void __launch_bounds__(kTX * kTY) k_update_tiled(Geo<T> g, Arrays<T> 
 #pragma unroll
     for (int c = 0; c < C; ++c) sbb[par][row][lane][c] = bb[c][1];
     __syncthreads();
-    if (out) {
+    if (out && t > t0) {
       // the f face t-1 (between planes t-1 and t), owned by this chunk when t > t0
-      if (t > t0) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const size_t im = pb - S + c * sc;
-          A.an[3][im] = xfp[c] - ts * half * (bbfp[c] + bb[c][3]);
-        }
-      }
+      for (int c = 0; c < C; ++c) qa3[pt - S + c * sc] = xfp[c] - ts * half * (bbfp[c] + bb[c][3]);
     }
     if (write_plane) {
 #pragma unroll
@@ -669,23 +699,25 @@ __global__ void __launch_bounds__(kTX * kTY) k_update_tiled(Geo<T> g, Arrays<T> 
         const T bxn = __shfl_down_sync(0xffffffffu, bb[c][0], 1);
         const T byn = (row + 1 < kTY) ? sbb[par][row + 1][lane][c] : T(0);
         if (out) {
-          const size_t i0 = pb + c * sc;
+          const int o = pt + c * sc;
           const int c1 = (c + 1 == C) ? 0 : c + 1;
-          const bool hasC = g.perc || (c + 1 < C);
-          A.an[0][i0] = hasR ? xr[c][0] - ts * half * (bb[c][0] + bxn) : T(0);
-          A.an[1][i0] = hasU ? xr[c][1] - ts * half * (bb[c][1] + byn) : T(0);
-          A.an[2][i0] = hasC ? xr[c][2] - ts * half * (bb[c][2] + bb[c1][2]) : T(0);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) A.bn[k][i0] = bn[c][k];
+          const bool hasC = perc || (c + 1 < C);
+          qa0[o] = hasR ? xr[c][0] - ts * half * (bb[c][0] + bxn) : T(0);
+          qa1[o] = hasU ? xr[c][1] - ts * half * (bb[c][1] + byn) : T(0);
+          qa2[o] = hasC ? xr[c][2] - ts * half * (bb[c][2] + bb[c1][2]) : T(0);
+          qb0[o] = bn[c][0];
+          qb1[o] = bn[c][1];
+          qb2[o] = bn[c][2];
+          qb3[o] = bn[c][3];
           if (WRITE_X) {
-            A.x[0][i0] = xr[c][0];
-            A.x[1][i0] = xr[c][1];
-            A.x[2][i0] = xr[c][2];
-            A.x[3][i0] = (t + 1 < g.P) ? xr[c][3] : T(0);
+            A.x[0][col + o] = xr[c][0];
+            A.x[1][col + o] = xr[c][1];
+            A.x[2][col + o] = xr[c][2];
+            A.x[3][col + o] = tnext ? xr[c][3] : T(0);
           }
         }
       }
-      if (CHECK && t + 1 < g.P) {
+      if (CHECK && tnext) {
         double m = 0;
         if (out) {
 #pragma unroll
@@ -720,9 +752,9 @@ __global__ void __launch_bounds__(kTX * kTY) k_update_tiled(Geo<T> g, Arrays<T> 
     __syncthreads();
     const int tid = threadIdx.x + kTX * threadIdx.y;
     if (tid < 3) {
-      double s = 0;
-      for (int i = 0; i < kTY; ++i) s += red[i][tid];
-      atomicAdd(&acc[(size_t)b * kAcc + tid], s);
+      double sum = 0;
+      for (int i = 0; i < kTY; ++i) sum += red[i][tid];
+      atomicAdd(&acc[(size_t)b * kAcc + tid], sum);
     }
     for (int t = t0 + tid; t < tend && t < g.P - 1; t += kTX * kTY) atomicAdd(&mass[(size_t)b * g.P + t], smass[t]);
   }
