@@ -66,6 +66,35 @@ __device__ __forceinline__ void dft_reg(c2<T> (&z)[R], const c2<T>* __restrict__
   for (int i = 0; i < R; ++i) z[i] = a[i];
 }
 
+// The same DFT for input already stored in bit-reversed order (z[bitrev(i)] = input i),
+// computed in place without a second register array.
+template <typename T, int R, int NT, bool INV>
+__device__ __forceinline__ void dft_reg_br(c2<T> (&a)[R], const c2<T>* __restrict__ twN) {
+  constexpr int L = Log2<R>::v;
+#pragma unroll
+  for (int stage = 0; stage < L; ++stage) {
+    const int m = 2 << stage;
+#pragma unroll
+    for (int k = 0; k < R; k += m) {
+#pragma unroll
+      for (int j = 0; j < m / 2; ++j) {
+        c2<T> t = a[k + j + m / 2];
+        if (j != 0) {
+          if (4 * j == m) {
+            t = INV ? mk2<T>(-t.y, t.x) : mk2<T>(t.y, -t.x);
+          } else {
+            const c2<T> w = twN[j * (NT / m)];
+            t = INV ? cmulc<T>(t, w) : cmul<T>(t, w);
+          }
+        }
+        const c2<T> u = a[k + j];
+        a[k + j] = cadd<T>(u, t);
+        a[k + j + m / 2] = csub<T>(u, t);
+      }
+    }
+  }
+}
+
 // Fill twiddle tables in shared memory: tw[j] = exp(-2 pi i j/N), hw[k] = exp(-i pi k/(2N)).
 // gtw / ghw are the same tables precomputed in double on the host.
 template <typename T>
@@ -331,6 +360,69 @@ __device__ void dct_cols(T* __restrict__ buf, int ld, int ncols, int P, const T*
         }
       }
       buf[k * ld + col] = acc0 + acc1;
+    }
+  }
+}
+
+// Register DCT along the columns of a [P][ld] tile for P a power of two: each
+// thread owns whole columns.  The row length ld is a compile-time constant so
+// that every element address is an immediate offset.  Forward is the unnormalised DCT-II, inverse its
+// exact inverse, both by Makhoul's reordering and a P/2-point complex DFT of the
+// packed even/odd samples (z[m] = v[2m] + i v[2m+1]).
+// twP[j] = exp(-2 pi i j / P), hwP[k] = exp(-i pi k / (2P)).
+template <typename T, int P, bool INV, int ld>
+__device__ void dct_cols_fft(T* __restrict__ buf, int ncols, const c2<T>* __restrict__ twP,
+                             const c2<T>* __restrict__ hwP) {
+  constexpr int M = P / 2;
+#pragma unroll 1
+  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+    T* cb = buf + col;
+    c2<T> z[M];
+    if (!INV) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int j0 = 2 * m, j1 = 2 * m + 1;   // v[j] = x[2j] (j < M), x[2(P-1-j)+1] (j >= M)
+        const T v0 = cb[(j0 < M ? 2 * j0 : 2 * (P - 1 - j0) + 1) * ld];
+        const T v1 = cb[(j1 < M ? 2 * j1 : 2 * (P - 1 - j1) + 1) * ld];
+        z[bitrev_c(m, Log2<M>::v)] = mk2<T>(v0, v1);
+      }
+      dft_reg_br<T, M, P, false>(z, twP);
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const c2<T> zk = z[k];
+        const c2<T> zm = z[(M - k) % M];
+        // even-sample spectrum E = (Z_k + conj Z_{M-k})/2, odd-sample O = (Z_k - conj Z_{M-k})/(2i)
+        const T ex = T(0.5) * (zk.x + zm.x), ey = T(0.5) * (zk.y - zm.y);
+        const T ox = T(0.5) * (zk.y + zm.y), oy = T(0.5) * (zm.x - zk.x);
+        const c2<T> w = twP[k];
+        const T tx = w.x * ox - w.y * oy, ty = w.x * oy + w.y * ox;
+        const c2<T> h0 = hwP[k], h1 = hwP[k + M];
+        cb[k * ld] = h0.x * (ex + tx) - h0.y * (ey + ty);          // V[k] = E + W^k O
+        cb[(k + M) * ld] = h1.x * (ex - tx) - h1.y * (ey - ty);    // V[k+M] = E - W^k O
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        // V[j] = exp(i pi j / 2P) (X[j] - i X[P-j]) for j = k and j = k + M
+        const T a0 = cb[k * ld], b0 = k ? cb[(P - k) * ld] : T(0);
+        const T a1 = cb[(k + M) * ld], b1 = cb[(M - k) * ld];
+        const c2<T> h0 = hwP[k], h1 = hwP[k + M];
+        const T v0x = h0.x * a0 - h0.y * b0, v0y = -h0.x * b0 - h0.y * a0;
+        const T v1x = h1.x * a1 - h1.y * b1, v1y = -h1.x * b1 - h1.y * a1;
+        const T ex = T(0.5) * (v0x + v1x), ey = T(0.5) * (v0y + v1y);
+        const T dx = T(0.5) * (v0x - v1x), dy = T(0.5) * (v0y - v1y);
+        const c2<T> w = twP[k];                                   // O = (V[k] - V[k+M])/2 * conj(W^k)
+        const T ox = dx * w.x + dy * w.y, oy = dy * w.x - dx * w.y;
+        z[bitrev_c(k, Log2<M>::v)] = mk2<T>(ex - oy, ey + ox);   // E + i O
+      }
+      dft_reg_br<T, M, P, true>(z, twP);
+      const T invM = T(1) / T(M);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int j0 = 2 * m, j1 = 2 * m + 1;
+        cb[(j0 < M ? 2 * j0 : 2 * (P - 1 - j0) + 1) * ld] = z[m].x * invM;
+        cb[(j1 < M ? 2 * j1 : 2 * (P - 1 - j1) + 1) * ld] = z[m].y * invM;
+      }
     }
   }
 }

@@ -139,9 +139,9 @@ struct Plan final : PlanBase {
 
   size_t xt_smem() const { return xt_layout<T>(nullptr, nullptr, P, n1, pmax, scrA, !fft_len(n1)); }
   size_t yc_smem() const {
-    T *t0, *t1, *t2;
+    T *t0, *t1, *t2, *t3;
     c2<T> *c0, *c1, *c3;
-    return yc_layout<T>(nullptr, C, n2, kW, scrB, !fft_len(n2), &t0, &c0, &c1, &c3, &t1, &t2);
+    return yc_layout<T>(nullptr, C, n2, kW, scrB, !fft_len(n2), &t0, &c0, &c1, &c3, &t1, &t2, &t3);
   }
 
   ot_status init() override {
@@ -286,6 +286,15 @@ struct Plan final : PlanBase {
     const std::vector<double> lt = neu_lam(P, (double)P);
     const double thr = grid.precision == OT_PREC_MIXED ? grid.lam_fp64 : 0.0;
 
+    std::vector<T> twt(2 * P), hwt(2 * P);
+    for (int j = 0; j < P; ++j) {
+      twt[2 * j] = (T)std::cos(2 * kPi * j / P);
+      twt[2 * j + 1] = (T)-std::sin(2 * kPi * j / P);
+      hwt[2 * j] = (T)std::cos(kPi * j / (2.0 * P));
+      hwt[2 * j + 1] = (T)-std::sin(kPi * j / (2.0 * P));
+    }
+    size_t o_twt = put(twt.data(), twt.size() * sizeof(T));
+    size_t o_hwt = put(hwt.data(), hwt.size() * sizeof(T));
     size_t o_Mf = put(Mf.data(), Mf.size() * sizeof(T));
     size_t o_Mi = put(Mi.data(), Mi.size() * sizeof(T));
     std::vector<T> ltT = toT(lt);
@@ -368,6 +377,7 @@ struct Plan final : PlanBase {
     if (!hue) {
       xt.tw = base + o_tw1; xt.hw = base + o_hw1; xt.cos4 = base + o_c41;
       xt.Mt_f = base + o_Mf; xt.Mt_i = base + o_Mi;
+      xt.twt = base + o_twt; xt.hwt = base + o_hwt;
       yc.tw = base + o_tw2; yc.hw = base + o_hw2; yc.cos4 = base + o_c42;
       yc.lam1 = base + o_l1; yc.lam2 = base + o_l2; yc.lamt = base + o_lt;
       yc.lam1d = (const double*)(base + o_l1d); yc.lam2d = (const double*)(base + o_l2d);

@@ -292,7 +292,20 @@ struct XtTables {
   const void* Mt_f;  // forward t-DCT, [P][PMAX]
   const void* Mt_i;  // inverse t-DCT
   const void* cos4;  // [4 n1]
+  const void* twt;   // c2<T>[P]: exp(-2 pi i j / P)   (register t-DCT when P == PMAX <= 32)
+  const void* hwt;   // c2<T>[P]: exp(-i pi k / (2P))
 };
+
+// The time transform runs in registers by FFT when P fills the template width
+// (16 or 32) and DYNOT_TFFT is set; otherwise it is the dense matrix product.
+#ifndef DYNOT_TFFT
+#define DYNOT_TFFT 1
+#endif
+#ifndef DYNOT_XT_MINB
+#define DYNOT_XT_MINB 2   // blocks per SM the x/t kernels are compiled for
+#endif
+template <int PMAX, int N1>
+__device__ __forceinline__ bool t_by_fft(int P) { return DYNOT_TFFT && N1 > 0 && PMAX <= 32 && P == PMAX; }
 
 // Shared-memory layout of the x/t kernels; the same function sizes it on the host.
 // The FFT path needs the twiddle tables, the dense path the cosine table.
@@ -315,7 +328,7 @@ __host__ __device__ __forceinline__ size_t xt_layout(XtSmem<T>* s, char* sm, int
 
 // N1 == 0 selects the dense x transform.
 template <typename T, int N1, int N2, int PMAX>
-__global__ void __launch_bounds__(256, 3) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
+__global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
                                                     const T* __restrict__ f0, const T* __restrict__ f1,
                                                     T* __restrict__ rhat, XtTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
@@ -330,7 +343,16 @@ __global__ void __launch_bounds__(256, 3) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
   // tables
   if (N1) load_tables<T>(s.tw, s.hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
   else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) s.cos4[j] = ((const T*)tb.cos4)[j];
-  for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_f)[j];
+  const bool tfft = t_by_fft<PMAX, N1>(P);
+  if (tfft) {
+    c2<T>* tt = (c2<T>*)s.Mt;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+      tt[j] = ((const c2<T>*)tb.twt)[j];
+      tt[P + j] = ((const c2<T>*)tb.hwt)[j];
+    }
+  } else {
+    for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_f)[j];
+  }
   // divergence of a and the time difference with the boundary densities
   const int ym = y > 0 ? y - 1 : (g.per2 ? g.n2 - 1 : -1);
   const int cm = c > 0 ? c - 1 : (g.perc ? g.C - 1 : -1);
@@ -372,7 +394,12 @@ __global__ void __launch_bounds__(256, 3) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
     dct_dense_rows<T, false>(rows, P, n1, false, (T*)s.scr, 2 * scr_elems, s.cos4);
   }
   // (the FFT path leaves a trailing barrier; the dense path too)
-  dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
+  if constexpr (PMAX <= 32 && N1 > 0) {
+    if (tfft) dct_cols_fft<T, PMAX, false, N1 * N2>(s.tile, n1, (const c2<T>*)s.Mt, (const c2<T>*)s.Mt + P);
+    else dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
+  } else {
+    dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
+  }
   __syncthreads();
   for (int t = 0; t < P; ++t)
     for (int x = threadIdx.x; x < n1; x += blockDim.x) rhat[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
@@ -380,7 +407,7 @@ __global__ void __launch_bounds__(256, 3) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
 
 // K_C: inverse DCT along t and x -> phi
 template <typename T, int N1, int N2, int PMAX>
-__global__ void __launch_bounds__(256, 3) k_inv_xt(Geo<T> g, const T* __restrict__ phihat, T* __restrict__ phi,
+__global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_inv_xt(Geo<T> g, const T* __restrict__ phihat, T* __restrict__ phi,
                                                 XtTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int y = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
@@ -389,11 +416,25 @@ __global__ void __launch_bounds__(256, 3) k_inv_xt(Geo<T> g, const T* __restrict
   xt_layout<T>(&s, smraw, P, n1, PMAX, scr_elems, N1 == 0);
   if (N1) load_tables<T>(s.tw, s.hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
   else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) s.cos4[j] = ((const T*)tb.cos4)[j];
-  for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_i)[j];
+  const bool tfft = t_by_fft<PMAX, N1>(P);
+  if (tfft) {
+    c2<T>* tt = (c2<T>*)s.Mt;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+      tt[j] = ((const c2<T>*)tb.twt)[j];
+      tt[P + j] = ((const c2<T>*)tb.hwt)[j];
+    }
+  } else {
+    for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_i)[j];
+  }
   for (int t = 0; t < P; ++t)
     for (int x = threadIdx.x; x < n1; x += blockDim.x) s.tile[t * n1 + x] = phihat[cidx(g, b, t, x, y, c)];
   __syncthreads();
-  dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
+  if constexpr (PMAX <= 32 && N1 > 0) {
+    if (tfft) dct_cols_fft<T, PMAX, true, N1 * N2>(s.tile, n1, (const c2<T>*)s.Mt, (const c2<T>*)s.Mt + P);
+    else dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
+  } else {
+    dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
+  }
   __syncthreads();
   const int Pr = P + (P & 1);
   if (Pr != P)
@@ -413,6 +454,34 @@ __global__ void __launch_bounds__(256, 3) k_inv_xt(Geo<T> g, const T* __restrict
 // K_B: y transform, colour eigen-solve and eigenvalue divide, inverse y
 // ---------------------------------------------------------------------------
 
+
+
+constexpr int kMaxC = 4;
+
+// Shared-memory layout of the y/colour kernel; the same function sizes it on the host.
+// The tile is [c][y][w] with a channel stride padded to 8 (mod 32) words so that
+// the interleaved row pairs of the y transform fall into distinct banks.
+__host__ __device__ __forceinline__ int yc_cstride(int n2, int W) {
+  const int base = n2 * W;
+  return base + ((8 - base % 32) + 32) % 32;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ size_t yc_layout(char* sm, int C, int n2, int W, int scr_elems, bool dense,
+                                                     T** tile, c2<T>** scr, c2<T>** tw, c2<T>** hw, T** cos4,
+                                                     T** l2, T** tabs) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = sm + off; off += (bytes + 15) & ~size_t(15); return p; };
+  *tile = (T*)take(sizeof(T) * (size_t)C * yc_cstride(n2, W));
+  *scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
+  *tw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n2);
+  *hw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n2);
+  *cos4 = dense ? (T*)take(sizeof(T) * 4 * n2) : nullptr;
+  *l2 = (T*)take(sizeof(T) * n2);
+  *tabs = (T*)take(sizeof(T) * (kMaxC * kMaxC + kMaxC + W));   // Q (padded 4x4), lambda_c, lambda_x of the strip
+  return off;
+}
+
 struct YcTables {
   const void* tw;      // c2<T>[n2]
   const void* hw;      // c2<T>[n2]
@@ -429,44 +498,40 @@ struct YcTables {
   double lam_fp64;     // eigenvalues below this are divided in FP64
 };
 
-constexpr int kMaxC = 4;
-
-// Shared-memory layout of the y/colour kernel; the same function sizes it on the host.
-template <typename T>
-__host__ __device__ __forceinline__ size_t yc_layout(char* sm, int C, int n2, int W, int scr_elems, bool dense,
-                                                     T** tile, c2<T>** scr, c2<T>** tw, c2<T>** hw, T** cos4,
-                                                     T** l2) {
-  size_t off = 0;
-  auto take = [&](size_t bytes) { char* p = sm + off; off += (bytes + 15) & ~size_t(15); return p; };
-  *tile = (T*)take(sizeof(T) * (size_t)C * n2 * W);   // [c][y][w]
-  *scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
-  *tw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n2);
-  *hw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n2);
-  *cos4 = dense ? (T*)take(sizeof(T) * 4 * n2) : nullptr;
-  *l2 = (T*)take(sizeof(T) * n2);
-  return off;
-}
-
 template <typename T, int M1, int M2, int W>
 __global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ hat, YcTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int x0 = blockIdx.x * W, kt = blockIdx.y, b = blockIdx.z;
   const int n1 = g.n1, n2 = g.n2, C = g.C;
   const int w_act = min(W, n1 - x0);
-  T *tile, *cos4, *l2;
+  const int cst = yc_cstride(n2, W);
+  T *tile, *cos4, *l2, *tabs;
   c2<T> *scr, *tw, *hw;
-  yc_layout<T>(smraw, C, n2, W, scr_elems, M1 == 0, &tile, &scr, &tw, &hw, &cos4, &l2);
+  yc_layout<T>(smraw, C, n2, W, scr_elems, M1 == 0, &tile, &scr, &tw, &hw, &cos4, &l2, &tabs);
+  T* Qs = tabs;                      // [4][4], zero outside C x C
+  T* lcs = tabs + kMaxC * kMaxC;     // [4]
+  T* l1s = lcs + kMaxC;              // [W]
   if (M1) load_tables<T>(tw, hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n2);
   else for (int j = threadIdx.x; j < 4 * n2; j += blockDim.x) cos4[j] = ((const T*)tb.cos4)[j];
   for (int j = threadIdx.x; j < n2; j += blockDim.x) l2[j] = ((const T*)tb.lam2)[j];
+  if (threadIdx.x < kMaxC * kMaxC) {
+    const int c = threadIdx.x / kMaxC, j = threadIdx.x % kMaxC;
+    Qs[threadIdx.x] = (c < C && j < C) ? ((const T*)tb.Qc)[c * C + j] : T(0);
+  }
+  if (threadIdx.x < kMaxC) lcs[threadIdx.x] = threadIdx.x < C ? ((const T*)tb.lamc)[threadIdx.x] : T(0);
+  if (threadIdx.x < W) l1s[threadIdx.x] = threadIdx.x < w_act ? ((const T*)tb.lam1)[x0 + threadIdx.x] : T(0);
   // load [c][y][w] (zero beyond the last column so pairs stay well defined)
-  for (int i = threadIdx.x; i < C * n2 * W; i += blockDim.x) {
-    const int w = i % W, yc = i / W;
-    const int y = yc % n2, c = yc / n2;
-    tile[i] = (w < w_act) ? hat[cidx(g, b, kt, x0 + w, y, c)] : T(0);
+  const size_t plane = ((size_t)b * g.P + kt) * g.S + x0;
+  for (int c = 0; c < C; ++c) {
+    const T* src = hat + plane + (size_t)c * n1 * n2;
+    T* dst = tile + c * cst;
+    for (int j = threadIdx.x; j < n2 * W; j += blockDim.x) {
+      const int w = j % W, y = j / W;
+      dst[j] = (w < w_act) ? src[(size_t)y * n1 + w] : T(0);
+    }
   }
   __syncthreads();
-  Rows<T, W, W> rows{tile, n2 * W, 1};
+  Rows<T, W, W> rows{tile, cst, 1};
   const int nrows = C * W;
   if constexpr (M1 > 0) {
     DctPow2<T, M1, M2, true, 256>::forward(rows, nrows, scr, tw, hw);
@@ -475,30 +540,33 @@ __global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ h
   }
   // colour eigen-solve: phi_c = sum_j Q[c][j] (sum_c' Q[c'][j] r_c') / lambda(kx, ky, j, kt)
   {
-    const T* Q = (const T*)tb.Qc;
-    const T* lc = (const T*)tb.lamc;
-    const T* l1 = (const T*)tb.lam1;
     const T lt = ((const T*)tb.lamt)[kt];
+    const float thr = (float)tb.lam_fp64;
+    T Q[kMaxC][kMaxC], lc[kMaxC];
+#pragma unroll
+    for (int c = 0; c < kMaxC; ++c) {
+      lc[c] = lcs[c];
+#pragma unroll
+      for (int j = 0; j < kMaxC; ++j) Q[c][j] = Qs[c * kMaxC + j];
+    }
     for (int i = threadIdx.x; i < n2 * W; i += blockDim.x) {
       const int w = i % W, ky = i / W;
       if (w >= w_act) continue;
-      const int kx = x0 + w;
       T r[kMaxC], co[kMaxC];
 #pragma unroll
-      for (int cc = 0; cc < kMaxC; ++cc) r[cc] = cc < C ? tile[(cc * n2 + ky) * W + w] : T(0);
-      const T lxyt = l1[kx] + l2[ky] + lt;
+      for (int cc = 0; cc < kMaxC; ++cc) r[cc] = cc < C ? tile[cc * cst + i] : T(0);
+      const T lxyt = l1s[w] + l2[ky] + lt;
 #pragma unroll
       for (int j = 0; j < kMaxC; ++j) {
-        if (j >= C) { co[j] = T(0); continue; }
         T s = 0;
 #pragma unroll
-        for (int cc = 0; cc < kMaxC; ++cc) if (cc < C) s += Q[cc * C + j] * r[cc];
+        for (int cc = 0; cc < kMaxC; ++cc) s = fma(Q[cc][j], r[cc], s);
         const T lam = lxyt + lc[j];
-        if (!(lam > T(0))) {
-          co[j] = T(0);     // the zero eigenvalue of the pseudo-inverse
-        } else if ((double)lam < tb.lam_fp64) {
+        if (j >= C || !(lam > T(0))) {
+          co[j] = T(0);     // padding, or the zero eigenvalue of the pseudo-inverse
+        } else if ((float)lam < thr) {
           // low modes: eigenvalue and quotient in double precision
-          const double ld = tb.lam1d[kx] + tb.lam2d[ky] + tb.lamtd[kt] + tb.lamcd[j];
+          const double ld = tb.lam1d[x0 + w] + tb.lam2d[ky] + tb.lamtd[kt] + tb.lamcd[j];
           co[j] = ld > 0.0 ? (T)((double)s / ld) : T(0);
         } else {
           co[j] = s / lam;
@@ -509,8 +577,8 @@ __global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ h
         if (cc >= C) continue;
         T s = 0;
 #pragma unroll
-        for (int j = 0; j < kMaxC; ++j) if (j < C) s += Q[cc * C + j] * co[j];
-        tile[(cc * n2 + ky) * W + w] = s;
+        for (int j = 0; j < kMaxC; ++j) s = fma(Q[cc][j], co[j], s);
+        tile[cc * cst + i] = s;
       }
     }
   }
@@ -520,10 +588,13 @@ __global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ h
   } else {
     dct_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, cos4);
   }
-  for (int i = threadIdx.x; i < C * n2 * W; i += blockDim.x) {
-    const int w = i % W, yc = i / W;
-    const int y = yc % n2, c = yc / n2;
-    if (w < w_act) hat[cidx(g, b, kt, x0 + w, y, c)] = tile[i];
+  for (int c = 0; c < C; ++c) {
+    T* dst = hat + plane + (size_t)c * n1 * n2;
+    const T* src = tile + c * cst;
+    for (int j = threadIdx.x; j < n2 * W; j += blockDim.x) {
+      const int w = j % W, y = j / W;
+      if (w < w_act) dst[(size_t)y * n1 + w] = src[j];
+    }
   }
 }
 
