@@ -72,7 +72,7 @@ KB<T> pick_kb(int n) {
     default: return k_solve_yc<T, 0, 0, kW>;
   }
 }
-template <typename T> using KD = void (*)(Geo<T>, Arrays<T>, int, double*, double*);
+template <typename T> using KD = void (*)(Geo<T>, Arrays<T>, int, double*);
 
 template <typename T, int C>
 KD<T> pick_kd_c(bool check, bool wx) {
@@ -111,6 +111,7 @@ struct Plan final : PlanBase {
   double* mass = nullptr;   // [B][P]
   double* chk = nullptr;    // [B][kChk]
   double* scl = nullptr;    // [B][2]
+  double* part = nullptr;   // per-block partial sums of the residual check
   // transform tables
   DevMem tabmem;
   XtTables xt{};
@@ -167,7 +168,7 @@ struct Plan final : PlanBase {
     size_t bytes = narr * rnd16(cells * sizeof(T)) + 2 * rnd16((size_t)B * S * sizeof(T)) +
                    rnd16(stage_floats * sizeof(float)) + rnd16(sizeof(double) * B * kAcc) +
                    rnd16(sizeof(double) * (size_t)B * P) + rnd16(sizeof(double) * B * kChk) +
-                   rnd16(sizeof(double) * B * 2);
+                   rnd16(sizeof(double) * B * 2) + rnd16(part_bytes());
     CUDA_OK(cudaMalloc(&mem.p, bytes));
     char* q = (char*)mem.p;
     auto take = [&](size_t nb) { char* r = q; q += rnd16(nb); return r; };
@@ -185,6 +186,7 @@ struct Plan final : PlanBase {
     mass = (double*)take(sizeof(double) * (size_t)B * P);
     chk = (double*)take(sizeof(double) * B * kChk);
     scl = (double*)take(sizeof(double) * B * 2);
+    part = (double*)take(part_bytes());
     CUDA_OK(cudaMemsetAsync(mem.p, 0, bytes, st));
 
     OT_TRY(build_tables());
@@ -451,6 +453,12 @@ struct Plan final : PlanBase {
     }
   }
 
+  // partials for the largest grid the autotuner may pick (time chunks of at least 1 plane)
+  size_t part_bytes() const {
+    const dim3 g1 = tiled_grid(1);
+    return sizeof(double) * (size_t)g1.x * g1.y * g1.z * kPart;
+  }
+
   dim3 tiled_grid(int tchunk) const {
     const int nbx = std::max(1, (n1 - 1 + kTX - 2) / (kTX - 1));
     const int nby = std::max(1, (n2 - 1 + kTY - 2) / (kTY - 1));
@@ -461,7 +469,9 @@ struct Plan final : PlanBase {
   void enqueue_update(int p, bool check, bool wx) {
     const Arrays<T> A = arrays(p, wx);
     if (tiled) {
-      pick_kd<T>(C, check, wx)<<<tiled_grid(tc), dim3(kTX, kTY), 0, st>>>(g, A, tc, acc, mass);
+      const dim3 grd = tiled_grid(tc);
+      pick_kd<T>(C, check, wx)<<<grd, dim3(kTX, kTY), 0, st>>>(g, A, tc, part);
+      if (check) k_reduce_check<<<B, 256, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass);
       return;
     }
     const dim3 grd((n1 + kThreadsUpd - 1) / kThreadsUpd, n2, C * P * B);

@@ -620,9 +620,13 @@ constexpr int kTX = 32, kTY = 8;
 #define DYNOT_UPD_MINB 3   // blocks per SM the tiled update is compiled for
 #endif
 
+// Per-block partial sums of the residual check: [problem][block][kPart] with
+// 0: |b+ - b|^2, 1: |K x + (0, f_b^+)|^2, 2: J(u, v), 3 + t: mass of the time slice t.
+constexpr int kPart = 68;
+
 template <typename T, int C, bool CHECK, bool WRITE_X>
 __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<T> g, Arrays<T> A, int TC,
-                                                                double* __restrict__ acc, double* __restrict__ mass) {
+                                                                double* __restrict__ part) {
   __shared__ T sbb[2][kTY][kTX][C];   // bbar_y exchange, double-buffered by plane parity
   __shared__ double smass[64];
   const int lane = threadIdx.x, row = threadIdx.y;
@@ -744,14 +748,16 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
 #pragma unroll
       for (int k = 0; k < 4; ++k) bb[c][k] = T(2) * bn[c][k] - lb[c][k];
       if (CHECK && out && write_plane) {
+        // per-cell terms in the working precision, sums in FP64
+        T db2 = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const double db = (double)bn[c][k] - (double)lb[c][k];
-          r_db += db * db;
+          const T db = bn[c][k] - lb[c][k];
+          db2 = fma(db, db, db2);
         }
-        r_kx += (double)k0 * k0 + (double)k1 * k1 + (double)k2 * k2 + (double)k3 * k3;
-        const double uu = (double)U0 * U0 + (double)U1 * U1 + (double)U2 * U2;
-        if (V > T(0)) r_J += uu / (2.0 * (double)V);
+        r_db += (double)db2;
+        r_kx += (double)(k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3);
+        if (V > T(0)) r_J += (double)((U0 * U0 + U1 * U1 + U2 * U2) / (T(2) * V));
       }
     }
     // neighbours' bbar: x+1 by shuffle, y+1 through shared memory
@@ -822,12 +828,38 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
     }
     __syncthreads();
     const int tid = threadIdx.x + kTX * threadIdx.y;
+    const int nblk = gridDim.x * gridDim.y * nch;    // blocks of one problem
+    const int jb = ((blockIdx.z % nch) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    double* pp = part + ((size_t)b * nblk + jb) * kPart;
     if (tid < 3) {
       double sum = 0;
       for (int i = 0; i < kTY; ++i) sum += red[i][tid];
-      atomicAdd(&acc[(size_t)b * kAcc + tid], sum);
+      pp[tid] = sum;
     }
-    for (int t = t0 + tid; t < tend && t < g.P - 1; t += kTX * kTY) atomicAdd(&mass[(size_t)b * g.P + t], smass[t]);
+    for (int t = tid; t < 64; t += kTX * kTY) pp[3 + t] = (t >= t0 && t < tend && t < g.P - 1) ? smass[t] : 0.0;
+  }
+}
+
+// Sum the per-block partials of each problem (one block per problem) into acc and mass.
+static __global__ void k_reduce_check(const double* __restrict__ part, int nblk, int P, double* __restrict__ acc,
+                               double* __restrict__ mass) {
+  const int b = blockIdx.x;
+  const double* pb = part + (size_t)b * nblk * kPart;
+  __shared__ double red[32];
+  for (int q = 0; q < 3 + P; ++q) {
+    double s = 0;
+    for (int j = threadIdx.x; j < nblk; j += blockDim.x) s += pb[(size_t)j * kPart + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+      if (q < 3) acc[(size_t)b * kAcc + q] = t;
+      else if (q - 3 < P) mass[(size_t)b * P + (q - 3)] = t;
+    }
+    __syncthreads();
   }
 }
 
