@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters", type=int, default=1000, help="PDHG iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="errors of the FP32 / mixed plans against the FP64 plan and the oracle (2000 iterations)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the kernel profile, time-to-tolerance and end-to-end legs (for profiler runs)")
     return ap.parse_args()
@@ -338,9 +340,91 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# precision study (not part of the default run): errors of the FP32 variants
+# ---------------------------------------------------------------------------
+
+def _oracle_crop_solve(f0, f1, P, iters, q):
+    import oracle as o
+    g = o.rgb_grid(f0.shape[2], f0.shape[1], P)
+    t = time.perf_counter()
+    st, infos, scale = o.solve(g, f0.astype(np.float64), f1.astype(np.float64), iters, 0.3, 0.99 / 0.3)
+    m = np.concatenate([a.ravel() for a in st.m]) * scale
+    q.put({"f": st.f * scale, "m": m, "energy": infos[-1].energy * scale, "residual": infos[-1].residual,
+           "seconds": time.perf_counter() - t})
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def precision_study(iters: int):
+    """FP32 and mixed plans against the FP64 plan and against the FP64 oracle (64 x 64 crop)."""
+    import multiprocessing as mp
+    from paper_1501_04840_gb300 import synth
+    F0, F1 = synth.rgb_pair(512, 512, BLOBS, 0)
+    c0 = F0[:, :64, :64].astype(np.float64)
+    c1 = F1[:, :64, :64].astype(np.float64)
+    c0 /= c0.sum()
+    c1 /= c1.sum()
+    c0 = c0.astype(np.float32)
+    c1 = c1.astype(np.float32)
+    # the oracle runs in a process started before any GPU work
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    proc = ctx.Process(target=_oracle_crop_solve, args=(c0, c1, 64, iters, q))
+    proc.start()
+    import torch  # noqa: F401  (device memory for the plans)
+    import paper_1501_04840_gb300 as ot
+    from paper_1501_04840_gb300 import _build
+    _build.build()
+    out = {"iters": iters}
+
+    def run(n1, n2, P, prec, f0, f1):
+        plan = ot.Plan(ot.rgb_grid(n1, n2, P, precision=prec))
+        t = time.perf_counter()
+        st = plan.solve(f0, f1, iters, check_every=iters)
+        sec = time.perf_counter() - t
+        p = plan.path()
+        plan.close()
+        m = np.concatenate([a[0].ravel() for a in p["m"]])
+        return {"f": p["f"][0], "m": m, "energy": st.energy, "residual": st.residual, "mass_drift": st.mass_drift,
+                "seconds": sec}
+
+    # (1) 256 x 256 x 3 x 32: FP32 variants against the all-FP64 GPU plan
+    f0, f1 = synth.rgb_pair(256, 256, BLOBS, 0)
+    ref = run(256, 256, P, 2, f0, f1)
+    rows = {"fp64": {k: ref[k] for k in ("energy", "residual", "mass_drift", "seconds")}}
+    for name, prec in (("mixed", 0), ("fp32", 1)):
+        r = run(256, 256, P, prec, f0, f1)
+        rows[name] = {"rel_f": _rel(r["f"], ref["f"]), "rel_m": _rel(r["m"], ref["m"]), "energy": r["energy"],
+                      "residual": r["residual"], "mass_drift": r["mass_drift"], "seconds": r["seconds"]}
+    out["256x256x3x32_vs_fp64_gpu"] = rows
+    # (2) 512 x 512 x 3 x 64: mixed against fp32 (the FP64 plan's x/t tile exceeds shared memory here)
+    a = run(512, 512, 64, 0, F0, F1)
+    b = run(512, 512, 64, 1, F0, F1)
+    out["512x512x3x64"] = {"mixed": {k: a[k] for k in ("energy", "residual", "mass_drift", "seconds")},
+                           "fp32": {k: b[k] for k in ("energy", "residual", "mass_drift", "seconds")},
+                           "rel_f_mixed_vs_fp32": _rel(a["f"], b["f"]), "rel_m_mixed_vs_fp32": _rel(a["m"], b["m"])}
+    # (3) 64 x 64 crop of the 512 pair (renormalised), every GPU variant against the oracle
+    orc = q.get()
+    proc.join()
+    rows = {"oracle": {"energy": orc["energy"], "residual": orc["residual"], "seconds": orc["seconds"]}}
+    for name, prec in (("fp64", 2), ("mixed", 0), ("fp32", 1)):
+        r = run(64, 64, 64, prec, c0, c1)
+        rows[name] = {"rel_f": _rel(r["f"], orc["f"]), "rel_m": _rel(r["m"], orc["m"]), "energy": r["energy"],
+                      "residual": r["residual"], "seconds": r["seconds"]}
+    out["crop64x64x3x64_vs_oracle"] = rows
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.precision_study:
+        precision_study(args.iters if args.iters != 1000 else 2000)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
