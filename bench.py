@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters", type=int, default=1000, help="PDHG iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="mixed-size batch: one-by-one solves against one batched graph, time to residual 1e-4")
     ap.add_argument("--precision-study", action="store_true",
                     help="errors of the FP32 / mixed plans against the FP64 plan and the oracle (2000 iterations)")
     ap.add_argument("--no-extras", action="store_true",
@@ -420,8 +422,69 @@ def precision_study(iters: int):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# mixed-size batch (not part of the default run): one-by-one cold solves
+# against the batched graph, both to residual 1e-4
+# ---------------------------------------------------------------------------
+
+def batch_bench(tol: float = 1e-4, check_every: int = 10):
+    import torch
+    import paper_1501_04840_gb300 as ot
+    from paper_1501_04840_gb300 import _build, synth
+    _build.build()
+    rgb, hue = synth.mixed_batch(seed=0)
+    grids, f0s, f1s, cells = [], [], [], []
+    for d in rgb:
+        grids.append(ot.rgb_grid(d["n1"], d["n2"], d["P"]))
+        a, b = synth.rgb_pair(d["n1"], d["n2"], 16, d["s"])
+        f0s.append(torch.from_numpy(a).cuda())
+        f1s.append(torch.from_numpy(b).cuda())
+        cells.append(d["n1"] * d["n2"] * 3 * d["P"])
+    for d in hue:
+        grids.append(ot.hue_grid(d["n"], d["P"]))
+        a, b = synth.hue_pair(d["n"], d["s"])
+        f0s.append(torch.from_numpy(a).cuda())
+        f1s.append(torch.from_numpy(b).cuda())
+        cells.append(d["n"] * d["P"])
+    # one plan per problem, solved one after another
+    plans = [ot.Plan(g) for g in grids]
+    for pl, a, b in zip(plans, f0s, f1s):     # warm-up (graph capture, clocks)
+        pl.solve(a, b, 20, check_every=10)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    seq_iters = []
+    for pl, a, b in zip(plans, f0s, f1s):
+        st = pl.solve(a, b, 20000, tol=tol, check_every=check_every)
+        seq_iters.append(st.iterations)
+    torch.cuda.synchronize()
+    seq_ms = 1e3 * (time.perf_counter() - t)
+    for pl in plans:
+        pl.close()
+    # the batch
+    bt = ot.Batch(grids)
+    bt.solve(f0s, f1s, 20, check_every=10)   # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    stats = bt.solve(f0s, f1s, 20000, tol=tol, check_every=check_every)
+    torch.cuda.synchronize()
+    bat_ms = 1e3 * (time.perf_counter() - t)
+    line = {"metric": "time to residual %g of a mixed batch (16 RGB + 64 hue pairs)" % tol, "unit": "ms",
+            "sequential_ms": seq_ms, "batched_ms": bat_ms, "speedup": seq_ms / bat_ms,
+            "groups": bt.groups, "problems": len(grids), "batched_iterations": stats[0].iterations,
+            "sequential_iterations": {"min": min(seq_iters), "max": max(seq_iters), "sum": sum(seq_iters)},
+            "cell_iterations": {"sequential": int(sum(c * i for c, i in zip(cells, seq_iters))),
+                                "batched": int(sum(cells) * stats[0].iterations)},
+            "max_residual": max(s.residual for s in stats), "max_mass_drift": max(s.mass_drift for s in stats),
+            "config": {"rgb": [(d["n1"], d["n2"], d["P"]) for d in rgb], "hue": [(d["n"], d["P"]) for d in hue],
+                       "blobs": 16, "check_every": check_every}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.batch:
+        batch_bench()
+        return
     if args.precision_study:
         precision_study(args.iters if args.iters != 1000 else 2000)
     elif args.impl == "reference":

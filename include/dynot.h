@@ -192,6 +192,31 @@ ot_status ot_profile(ot_plan_t p, int iters, double ms[5], const char** names);
 ot_status ot_hue_project_noalloc(int bins, int P, int batch, double axis_scale, const float* f0, const float* f1,
                                  const float* a_packed, float* x_packed, float* phi, void* cuda_stream);
 
+/*
+ * Mixed-size batches (many problems of different shapes solved together).
+ * Problems whose grids are identical share one batched plan; every such group
+ * runs on its own stream and whole iterations of all groups are captured into
+ * one CUDA graph, so that small problems fill the GPU side by side.  Each
+ * problem follows Algorithm 1 exactly as ot_solve would.
+ *
+ * ot_batch_create: `count` grids (sizes and parameters per problem), ordered on
+ *   cuda_stream (NULL => own stream).  Allocates one workspace per group.
+ * ot_batch_solve: f0[i], f1[i] are problem i's densities (host or device,
+ *   layout of ot_solve, same validation and mass rescaling).  All problems run
+ *   in lockstep for up to `iters` iterations; every `check_every` iterations
+ *   (0 => 10) the residuals are read and the batch stops once every problem's
+ *   residual is <= tol (OT_ENOTCONV with valid results otherwise, when tol > 0).
+ *   stats (may be NULL) receives `count` entries; elapsed_ms is the whole batch.
+ * ot_batch_path: problem i's path, as ot_path.
+ */
+typedef struct ot_batch_s* ot_batch_t;
+ot_status ot_batch_create(const ot_grid* grids, int count, void* cuda_stream, ot_batch_t* out);
+ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* const* f1, int iters, double tol,
+                         int check_every, ot_solve_stats* stats);
+ot_status ot_batch_path(ot_batch_t b, int i, float* f, float* m0, float* m1, float* m2);
+int ot_batch_groups(ot_batch_t b);
+void ot_batch_destroy(ot_batch_t b);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* ot_last_error(void);
 

@@ -78,8 +78,16 @@ def load_library() -> ctypes.CDLL:
     lib.ot_last_error.argtypes = []
     lib.ot_last_error.restype = c_char_p
     lib.ot_abi_version.restype = c_int
+    lib.ot_batch_create.argtypes = [POINTER(Grid), c_int, c_void_p, POINTER(c_void_p)]
+    lib.ot_batch_solve.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_int, c_double, c_int,
+                                   POINTER(Stats)]
+    lib.ot_batch_path.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.ot_batch_groups.argtypes = [c_void_p]
+    lib.ot_batch_groups.restype = c_int
+    lib.ot_batch_destroy.argtypes = [c_void_p]
+    lib.ot_batch_destroy.restype = None
     for name in ("ot_plan", "ot_solve", "ot_path", "ot_state_set", "ot_state_get", "ot_iterate", "ot_project",
-                 "ot_prox", "ot_profile"):
+                 "ot_prox", "ot_profile", "ot_batch_create", "ot_batch_solve", "ot_batch_path"):
         getattr(lib, name).restype = c_int
     del fp
     _lib = lib
@@ -254,6 +262,60 @@ class Plan:
         names = c_char_p()
         _check(self.lib.ot_profile(self.h, iters, ms, ctypes.byref(names)))
         return dict(zip(names.value.decode().split(","), list(ms)))
+
+
+class Batch:
+    """Problems of mixed sizes solved together (C ABI ot_batch_*)."""
+
+    def __init__(self, grids, stream: Optional[int] = None):
+        self.lib = load_library()
+        self.grids = list(grids)
+        arr = (Grid * len(self.grids))(*self.grids)
+        h = c_void_p()
+        _check(self.lib.ot_batch_create(arr, len(self.grids), c_void_p(stream) if stream else None, ctypes.byref(h)))
+        self.h = h
+        self.shapes = []
+        for g in self.grids:
+            probe = Plan.__new__(Plan)
+            probe.grid = g
+            probe.n = [g.n[k] if k < g.ndim else 1 for k in range(3)]
+            probe.P = g.P
+            self.shapes.append(probe)
+
+    @property
+    def groups(self) -> int:
+        return self.lib.ot_batch_groups(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ot_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, f0s, f1s, iters: int, tol: float = 0.0, check_every: int = 0):
+        n = len(self.grids)
+        p0 = (c_void_p * n)(*[_ptr(a) for a in f0s])
+        p1 = (c_void_p * n)(*[_ptr(a) for a in f1s])
+        stats = (Stats * n)()
+        s = self.lib.ot_batch_solve(self.h, p0, p1, iters, tol, check_every, stats)
+        _check(s, allow=(OT_ENOTCONV,))
+        out = list(stats)
+        for st in out:
+            st.converged = s == OT_OK
+        return out
+
+    def path(self, i: int):
+        sh = self.shapes[i]
+        f = np.empty(sh.f_shape(), np.float32)
+        ms = [np.empty(sh.m_shape(k), np.float32) for k in range(sh.grid.ndim)]
+        ptrs = [_ptr(m) for m in ms] + [None] * (3 - len(ms))
+        _check(self.lib.ot_batch_path(self.h, i, _ptr(f), ptrs[0], ptrs[1], ptrs[2]))
+        return {"f": f, "m": ms}
 
 
 def prox(a_m, a_f, sigma: float):

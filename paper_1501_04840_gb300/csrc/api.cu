@@ -107,6 +107,67 @@ struct ot_plan_s {
   std::unique_ptr<PlanBase> impl;
 };
 
+// A mixed-size batch: problems of equal shape share one batched plan (a group),
+// each group runs on its own stream, and whole iterations of every group are
+// captured into one CUDA graph (fork/join across the group streams).
+struct ot_batch_s {
+  std::vector<std::unique_ptr<PlanBase>> groups;
+  std::vector<int> grp, idx;           // problem -> (group, index inside the group)
+  cudaStream_t main = nullptr;
+  bool own_main = false;
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  ~ot_batch_s() {
+    if (main) cudaStreamSynchronize(main);
+    for (auto& g : groups)
+      if (g && g->st) cudaStreamSynchronize(g->st);
+    for (auto& e : gexec)
+      if (e) cudaGraphExecDestroy(e);
+    for (cudaEvent_t e : {fork, t0, t1})
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : join)
+      if (e) cudaEventDestroy(e);
+    groups.clear();
+    if (own_main && main) cudaStreamDestroy(main);
+  }
+};
+
+namespace {
+
+bool same_shape(const ot_grid& a, const ot_grid& b) {
+  if (a.ndim != b.ndim || a.P != b.P || a.precision != b.precision) return false;
+  if (a.sigma != b.sigma || a.tau != b.tau || a.lam_fp64 != b.lam_fp64) return false;
+  for (int k = 0; k < 3; ++k)
+    if (a.n[k] != b.n[k] || a.bc[k] != b.bc[k] || a.axis_scale[k] != b.axis_scale[k]) return false;
+  return true;
+}
+
+ot_status make_plan(const ot_grid& g, int batch, void* stream, std::unique_ptr<PlanBase>& out);
+
+// fork from the main stream to every group stream and join back
+ot_status batch_capture(ot_batch_s& b, int parity) {
+  if (b.gexec[parity]) return OT_OK;
+  cudaGraph_t gr = nullptr;
+  CUDA_OK(cudaStreamBeginCapture(b.main, cudaStreamCaptureModeThreadLocal));
+  CUDA_OK(cudaEventRecord(b.fork, b.main));
+  for (size_t i = 0; i < b.groups.size(); ++i) {
+    PlanBase& P = *b.groups[i];
+    CUDA_OK(cudaStreamWaitEvent(P.st, b.fork, 0));
+    OT_TRY(P.enqueue_pair());
+    CUDA_OK(cudaEventRecord(b.join[i], P.st));
+    CUDA_OK(cudaStreamWaitEvent(b.main, b.join[i], 0));
+  }
+  cudaError_t e = cudaStreamEndCapture(b.main, &gr);
+  if (e != cudaSuccess) return seterr(OT_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b.gexec[parity], gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return seterr(OT_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+  return OT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void ot_grid_rgb(ot_grid* g, int n1, int n2, int P) {
@@ -137,6 +198,17 @@ ot_status ot_plan(const ot_grid* gi, int batch, void* cuda_stream, ot_plan_t* ou
   ot_grid g;
   OT_TRY(validate(gi, batch, g));
   std::unique_ptr<PlanBase> impl;
+  OT_TRY(make_plan(g, batch, cuda_stream, impl));
+  ot_plan_s* h = new ot_plan_s;
+  h->impl = std::move(impl);
+  *out = h;
+  return OT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+ot_status make_plan(const ot_grid& g, int batch, void* cuda_stream, std::unique_ptr<PlanBase>& impl) {
   if (g.precision == OT_PREC_FP64) impl.reset(new_plan_f64());
   else impl.reset(new_plan_f32());
   PlanBase& P = *impl;
@@ -157,10 +229,122 @@ ot_status ot_plan(const ot_grid* gi, int batch, void* cuda_stream, ot_plan_t* ou
   OT_TRY(make_compact(P));
   OT_TRY(P.init());
   CUDA_OK(cudaStreamSynchronize(P.st));
-  ot_plan_s* h = new ot_plan_s;
-  h->impl = std::move(impl);
-  *out = h;
   return OT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ot_status ot_batch_create(const ot_grid* grids, int count, void* cuda_stream, ot_batch_t* out) {
+  if (!out || !grids || count < 1) return seterr(OT_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  std::unique_ptr<ot_batch_s> b(new ot_batch_s);
+  std::vector<ot_grid> keys;
+  std::vector<int> counts;
+  b->grp.resize(count);
+  b->idx.resize(count);
+  for (int i = 0; i < count; ++i) {
+    ot_grid g;
+    OT_TRY(validate(&grids[i], 1, g));
+    int k = -1;
+    for (size_t j = 0; j < keys.size(); ++j)
+      if (same_shape(keys[j], g)) { k = (int)j; break; }
+    if (k < 0) {
+      k = (int)keys.size();
+      keys.push_back(g);
+      counts.push_back(0);
+    }
+    b->grp[i] = k;
+    b->idx[i] = counts[k]++;
+  }
+  for (size_t j = 0; j < keys.size(); ++j) {
+    std::unique_ptr<PlanBase> p;
+    OT_TRY(make_plan(keys[j], counts[j], nullptr, p));   // each group on a stream of its own
+    b->groups.push_back(std::move(p));
+  }
+  if (cuda_stream) {
+    b->main = (cudaStream_t)cuda_stream;
+  } else {
+    CUDA_OK(cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking));
+    b->own_main = true;
+  }
+  CUDA_OK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  CUDA_OK(cudaEventCreate(&b->t0));
+  CUDA_OK(cudaEventCreate(&b->t1));
+  b->join.resize(b->groups.size());
+  for (auto& e : b->join) CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  *out = b.release();
+  return OT_OK;
+}
+
+int ot_batch_groups(ot_batch_t b) { return b ? (int)b->groups.size() : 0; }
+
+void ot_batch_destroy(ot_batch_t b) { delete b; }
+
+ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* const* f1, int iters, double tol,
+                         int check_every, ot_solve_stats* stats) {
+  if (!b || !f0 || !f1 || iters < 1) return seterr(OT_EINVAL, "bad batch solve arguments");
+  const int count = (int)b->grp.size();
+  for (int i = 0; i < count; ++i) OT_TRY(b->groups[b->grp[i]]->stage_problem(b->idx[i], f0[i], f1[i]));
+  for (auto& g : b->groups) OT_TRY(g->prepare_staged());   // validation, rescaling, cold start
+  for (size_t i = 0; i < b->groups.size(); ++i) {
+    CUDA_OK(cudaEventRecord(b->join[i], b->groups[i]->st));
+    CUDA_OK(cudaStreamWaitEvent(b->main, b->join[i], 0));
+  }
+  CUDA_OK(cudaEventRecord(b->t0, b->main));
+  const int K = check_every > 0 ? check_every : iters;
+  int done = 0;
+  bool converged = false;
+  std::vector<std::vector<ProblemCheck>> per(b->groups.size());
+  while (done < iters) {
+    const int chunk = std::min(K, iters - done);
+    const int plain = chunk - 1;
+    const int par = b->groups[0]->parity();
+    if (plain >= 2) OT_TRY(batch_capture(*b, par));
+    for (int r = 0; r < plain / 2; ++r) CUDA_OK(cudaGraphLaunch(b->gexec[par], b->main));
+    // the remaining single iteration and the checked one, per group after the graph
+    CUDA_OK(cudaEventRecord(b->fork, b->main));
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+      PlanBase& P = *b->groups[i];
+      CUDA_OK(cudaStreamWaitEvent(P.st, b->fork, 0));
+      if (plain % 2) OT_TRY(P.enqueue_single());
+      OT_TRY(P.enqueue_check_async());
+      CUDA_OK(cudaEventRecord(b->join[i], P.st));
+      CUDA_OK(cudaStreamWaitEvent(b->main, b->join[i], 0));
+    }
+    CUDA_OK(cudaStreamSynchronize(b->main));
+    done += chunk;
+    double worst = 0;
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+      OT_TRY(b->groups[i]->collect(per[i]));
+      for (const ProblemCheck& c : per[i]) worst = std::max(worst, c.residual);
+    }
+    if (tol > 0 && worst <= tol) {
+      converged = true;
+      break;
+    }
+  }
+  CUDA_OK(cudaEventRecord(b->t1, b->main));
+  CUDA_OK(cudaEventSynchronize(b->t1));
+  float ms = 0;
+  CUDA_OK(cudaEventElapsedTime(&ms, b->t0, b->t1));
+  if (stats) {
+    for (int i = 0; i < count; ++i) {
+      const ProblemCheck& c = per[b->grp[i]][b->idx[i]];
+      stats[i].iterations = done;
+      stats[i].residual = c.residual;
+      stats[i].energy = c.energy;
+      stats[i].mass_drift = c.drift;
+      stats[i].elapsed_ms = ms;
+    }
+  }
+  if (tol > 0 && !converged) return seterr(OT_ENOTCONV, "batch: tolerance not reached after %d iterations", done);
+  return OT_OK;
+}
+
+ot_status ot_batch_path(ot_batch_t b, int i, float* f, float* m0, float* m1, float* m2) {
+  if (!b || i < 0 || i >= (int)b->grp.size()) return seterr(OT_EINVAL, "bad batch problem index");
+  return b->groups[b->grp[i]]->path_one(b->idx[i], f, m0, m1, m2);
 }
 
 void ot_destroy(ot_plan_t p) {

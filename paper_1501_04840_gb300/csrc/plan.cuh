@@ -112,6 +112,8 @@ struct Plan final : PlanBase {
   double* chk = nullptr;    // [B][kChk]
   double* scl = nullptr;    // [B][2]
   double* part = nullptr;   // per-block partial sums of the residual check
+  double* h_acc = nullptr;  // pinned host copies of acc and mass
+  double* h_mass = nullptr;
   // transform tables
   DevMem tabmem;
   XtTables xt{};
@@ -136,6 +138,8 @@ struct Plan final : PlanBase {
       if (e) cudaGraphExecDestroy(e);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
+    if (h_acc) cudaFreeHost(h_acc);
+    if (h_mass) cudaFreeHost(h_mass);
   }
 
   size_t xt_smem() const { return xt_layout<T>(nullptr, nullptr, P, n1, pmax, scrA, !fft_len(n1)); }
@@ -191,6 +195,8 @@ struct Plan final : PlanBase {
 
     OT_TRY(build_tables());
     for (auto& e : ev) CUDA_OK(cudaEventCreate(&e));
+    CUDA_OK(cudaMallocHost(&h_acc, sizeof(double) * B * kAcc));
+    CUDA_OK(cudaMallocHost(&h_mass, sizeof(double) * (size_t)B * P));
     out_scale.assign(B, 1.0);
     tiled = !hue && !g.per1 && !g.per2 && C <= 4;
     if (tiled) OT_TRY(tune_update());
@@ -398,9 +404,11 @@ struct Plan final : PlanBase {
       if ((int)smA > maxsm || (int)smB > maxsm)
         return seterr(OT_EUNSUPPORTED, "grid needs %zu / %zu bytes of shared memory per block (max %d)", smA, smB,
                       maxsm);
-      CUDA_OK(cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
-      CUDA_OK(cudaFuncSetAttribute((const void*)kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
-      CUDA_OK(cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB));
+      // The limit is a property of the kernel, shared by every plan that uses it:
+      // raise it to the device maximum instead of this plan's size.
+      CUDA_OK(cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+      CUDA_OK(cudaFuncSetAttribute((const void*)kc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+      CUDA_OK(cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     } else {
       ht.cs = base + o_cs; ht.lam = base + o_hl; ht.lamd = (const double*)(base + o_hld);
       ht.lamt = base + o_lt; ht.lamtd = (const double*)(base + o_ltd);
@@ -409,9 +417,14 @@ struct Plan final : PlanBase {
       kh = pick_kh<T>(pmax);
       smH = rnd16(sizeof(T) * n1) + rnd16(sizeof(c2<T>) * n1);
       smHt = 2 * sizeof(T) * (size_t)pmax * pmax;
-      CUDA_OK(cudaFuncSetAttribute((const void*)k_hue_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smH));
-      CUDA_OK(cudaFuncSetAttribute((const void*)k_hue_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smH));
-      CUDA_OK(cudaFuncSetAttribute((const void*)kh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smHt));
+      int maxsm = 0;
+      CUDA_OK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+      if ((int)smH > maxsm || (int)smHt > maxsm)
+        return seterr(OT_EUNSUPPORTED, "hue grid needs %zu / %zu bytes of shared memory per block (max %d)", smH,
+                      smHt, maxsm);
+      CUDA_OK(cudaFuncSetAttribute((const void*)k_hue_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+      CUDA_OK(cudaFuncSetAttribute((const void*)k_hue_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+      CUDA_OK(cudaFuncSetAttribute((const void*)kh, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     }
     return OT_OK;
   }
@@ -496,7 +509,12 @@ struct Plan final : PlanBase {
     CUDA_OK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     enqueue_iteration(p, false, false);
     enqueue_iteration(1 - p, false, false);
+    const cudaError_t le = cudaGetLastError();
     cudaError_t e = cudaStreamEndCapture(st, &gr);
+    if (le != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return seterr(OT_ECUDA, "kernel launch during graph capture: %s", cudaGetErrorString(le));
+    }
     if (e != cudaSuccess) return seterr(OT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&gexec[p], gr, 0);
     cudaGraphDestroy(gr);
@@ -523,31 +541,45 @@ struct Plan final : PlanBase {
     double residual = 0, energy = 0, drift = 0;
   };
 
-  // one iteration with residuals (and x output), read back on the host
-  ot_status run_check(bool wx, Check& out) {
+  // one iteration with residuals (and x output); results land in pinned host memory
+  ot_status enqueue_check(bool wx) {
     CUDA_OK(cudaMemsetAsync(acc, 0, sizeof(double) * B * kAcc, st));
     CUDA_OK(cudaMemsetAsync(mass, 0, sizeof(double) * (size_t)B * P, st));
     enqueue_iteration(par, true, wx);
     CUDA_OK(cudaGetLastError());
     par ^= 1;
     if (wx) have_x = true;
-    std::vector<double> hacc((size_t)B * kAcc), hm((size_t)B * P);
-    CUDA_OK(cudaMemcpyAsync(hacc.data(), acc, hacc.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_OK(cudaMemcpyAsync(hm.data(), mass, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_OK(cudaStreamSynchronize(st));
+    CUDA_OK(cudaMemcpyAsync(h_acc, acc, sizeof(double) * B * kAcc, cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaMemcpyAsync(h_mass, mass, sizeof(double) * (size_t)B * P, cudaMemcpyDeviceToHost, st));
+    return OT_OK;
+  }
+
+  // per-problem residual, energy (caller units) and mass drift of the last check (after a sync)
+  ot_status collect_check(std::vector<ProblemCheck>& per, Check& out) {
+    per.assign(B, ProblemCheck{});
     out = Check{};
     for (int bi = 0; bi < B; ++bi) {
-      const double* q = &hacc[(size_t)bi * kAcc];
+      const double* q = &h_acc[(size_t)bi * kAcc];
       const double res = std::sqrt(q[0]) / std::max(std::sqrt(q[1]), 1e-300);
       if (!std::isfinite(res) || !std::isfinite(q[2]))
         return seterr(OT_ENUMERIC, "non-finite residual in problem %d", bi);
-      out.residual = std::max(out.residual, res);
-      out.energy += q[2] / (double)N * out_scale[bi] / B;
       double M = 0;
-      for (int t = 0; t + 1 < P; ++t) M = std::max(M, std::fabs(hm[(size_t)bi * P + t] - (double)S));
-      out.drift = std::max(out.drift, M / (double)S);
+      for (int t = 0; t + 1 < P; ++t) M = std::max(M, std::fabs(h_mass[(size_t)bi * P + t] - (double)S));
+      per[bi].residual = res;
+      per[bi].energy = q[2] / (double)N * out_scale[bi];
+      per[bi].drift = M / (double)S;
+      out.residual = std::max(out.residual, res);
+      out.energy += per[bi].energy / B;
+      out.drift = std::max(out.drift, per[bi].drift);
     }
     return OT_OK;
+  }
+
+  ot_status run_check(bool wx, Check& out) {
+    OT_TRY(enqueue_check(wx));
+    CUDA_OK(cudaStreamSynchronize(st));
+    std::vector<ProblemCheck> per;
+    return collect_check(per, out);
   }
 
   ot_status drive(int iters, double tol, int check_every, ot_solve_stats* stats) {
@@ -590,6 +622,26 @@ struct Plan final : PlanBase {
     const size_t n = (size_t)B * S;
     CUDA_OK(cudaMemcpyAsync(stage, f0, n * sizeof(float), cudaMemcpyDefault, st));
     CUDA_OK(cudaMemcpyAsync(stage + n, f1, n * sizeof(float), cudaMemcpyDefault, st));
+    return validate_scale(normalise);
+  }
+
+  // problem bi's densities into the staging area (batches assembled from separate arrays)
+  ot_status stage_problem(int bi, const float* f0, const float* f1) override {
+    if (bi < 0 || bi >= B || !f0 || !f1) return seterr(OT_EINVAL, "bad problem index or NULL density");
+    const size_t n = (size_t)B * S;
+    CUDA_OK(cudaMemcpyAsync(stage + (size_t)bi * S, f0, S * sizeof(float), cudaMemcpyDefault, st));
+    CUDA_OK(cudaMemcpyAsync(stage + n + (size_t)bi * S, f1, S * sizeof(float), cudaMemcpyDefault, st));
+    return OT_OK;
+  }
+
+  ot_status prepare_staged() override {
+    OT_TRY(validate_scale(true));
+    return cold_start();
+  }
+
+  // validate the staged densities (section 2: f >= 0, equal masses) and rescale (reading of section 4)
+  ot_status validate_scale(bool normalise) {
+    const size_t n = (size_t)B * S;
     std::vector<double> sc(2 * B, 1.0);
     if (normalise) {
       CUDA_OK(cudaMemsetAsync(chk, 0, sizeof(double) * B * kChk, st));
@@ -666,6 +718,46 @@ struct Plan final : PlanBase {
       }
     }
     return drive(iters, tol, grid.check_every, stats);
+  }
+
+  // ---- hooks for mixed-size batches (several plans captured into one graph)
+  ot_status enqueue_pair() override {
+    enqueue_iteration(par, false, false);
+    enqueue_iteration(1 - par, false, false);
+    CUDA_OK(cudaGetLastError());
+    return OT_OK;
+  }
+  ot_status enqueue_single() override {
+    enqueue_iteration(par, false, false);
+    CUDA_OK(cudaGetLastError());
+    par ^= 1;
+    return OT_OK;
+  }
+  ot_status enqueue_check_async() override { return enqueue_check(true); }
+  ot_status collect(std::vector<ProblemCheck>& per) override {
+    Check ck;
+    return collect_check(per, ck);
+  }
+  int parity() const override { return par; }
+
+  ot_status path_one(int bi, float* f, float* m0, float* m1, float* m2) override {
+    if (!have_x) return seterr(OT_EINVAL, "no path: run a solve first");
+    if (bi < 0 || bi >= B) return seterr(OT_EINVAL, "problem index out of range");
+    float* ds[4] = {m0, d >= 2 ? m1 : nullptr, d >= 3 ? m2 : nullptr, f};
+    Geo<T> g1 = g;
+    g1.B = 1;
+    const size_t off = (size_t)bi * N;
+    for (int k = 0; k < 4; ++k) {
+      if (!ds[k]) continue;
+      float* dd[4] = {nullptr, nullptr, nullptr, nullptr};
+      dd[k] = stage;
+      k_pack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, x[0] + off, x[1] + off, x[2] + off, x[3] + off,
+                                                out_scale[bi], nullptr, dd[0], dd[1], dd[2], dd[3]);
+      CUDA_OK(cudaGetLastError());
+      CUDA_OK(cudaMemcpyAsync(ds[k], stage, (size_t)cp.len[k] * sizeof(float), cudaMemcpyDefault, st));
+      CUDA_OK(cudaStreamSynchronize(st));
+    }
+    return OT_OK;
   }
 
   ot_status path(float* f, float* m0, float* m1, float* m2) override {

@@ -43,6 +43,11 @@ struct DevMem {
 // --------------------------------------------------------------------------
 // plans
 // --------------------------------------------------------------------------
+// residual, energy (caller units) and mass drift of one problem at a check
+struct ProblemCheck {
+  double residual = 0, energy = 0, drift = 0;
+};
+
 struct PlanBase {
   ot_grid grid{};
   int B = 1, d = 3;
@@ -67,6 +72,15 @@ struct PlanBase {
   virtual ot_status iterate(int iters, ot_solve_stats* stats) = 0;
   virtual ot_status project(const float* f0, const float* f1, const float* a, float* x, float* phi) = 0;
   virtual ot_status profile(int iters, double ms[5]) = 0;
+  // mixed-size batches: staging, one plain pair / single iteration, asynchronous checks
+  virtual ot_status stage_problem(int bi, const float* f0, const float* f1) = 0;
+  virtual ot_status prepare_staged() = 0;
+  virtual ot_status enqueue_pair() = 0;
+  virtual ot_status enqueue_single() = 0;
+  virtual ot_status enqueue_check_async() = 0;
+  virtual ot_status collect(std::vector<ProblemCheck>& per) = 0;
+  virtual int parity() const = 0;
+  virtual ot_status path_one(int bi, float* f, float* m0, float* m1, float* m2) = 0;
 };
 
 PlanBase* new_plan_f32();
