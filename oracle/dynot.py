@@ -456,6 +456,30 @@ def pdhg_step(g: Grid, st: State, f0: np.ndarray, f1: np.ndarray, sigma: float, 
     return new, info
 
 
+def warm_state(g: Grid, m: Sequence[np.ndarray], f: np.ndarray, f0: np.ndarray, f1: np.ndarray,
+               sigma: float, dual: bool = True, vmin: float = 1e-3) -> State:
+    """Initial state of Algorithm 1 from a given path x0 = (m, f) (no counterpart in the paper).
+
+    Without ``dual`` the dual starts at zero as in Algorithm 1.  With it,
+    b = bbar = grad J(y) / sigma at y = K x0 + (0, f_b^+): step 2 has the
+    optimality condition 0 = grad J(y) + sigma (y - K x - (0, f_b^+) - b), and
+    step 3 leaves b unchanged exactly when y = K x + (0, f_b^+).  grad J(u, v)
+    = (u / v, -|u|^2 / (2 v^2)) for J = |u|^2 / (2 v); v is clamped below by vmin.
+    """
+    st = State.zeros(g)
+    st.m = [np.asarray(a, float).copy() for a in m]
+    st.f = np.asarray(f, float).copy()
+    if dual:
+        sm, sf = K(g, st.m, st.f)
+        v = np.maximum(sf + f_b_plus(g, f0, f1), vmin)
+        s2 = sum(a * a for a in sm)
+        st.bm = [a / (sigma * v) for a in sm]
+        st.bf = -s2 / (2.0 * sigma * v * v)
+        st.bbm = [a.copy() for a in st.bm]
+        st.bbf = st.bf.copy()
+    return st
+
+
 def normalise_pair(g: Grid, f0: np.ndarray, f1: np.ndarray, rel_tol: float = 1e-6):
     """Mass rescaling of section 4 (||f0||_1 = ||f1||_1) to mean density 1.
 

@@ -148,3 +148,26 @@ def test_translation_energy_and_centroid():
     for k in range(1, P):
         cx = (st.f[k - 1] * xx).sum() / st.f[k - 1].sum()
         assert abs(cx - (cx0 + s * k / P)) < 0.1
+
+
+def test_warm_state_dual_is_the_converged_dual():
+    """At a fixed point of Algorithm 1 the dual equals grad J(K x + (0, f_b^+)) / sigma
+    (optimality of step 2 with y = K x + (0, f_b^+)); a warm state built from the
+    converged path therefore reproduces the converged dual and is itself a fixed point."""
+    g = o.rgb_grid(6, 5, 4)
+    f0, f1 = _pair(g, 11, floor=0.5)
+    g0, g1, _ = o.normalise_pair(g, f0, f1)
+    st, infos, _ = o.solve(g, f0, f1, 3000, SIG, 0.99 / SIG)
+    assert infos[-1].residual < 1e-9
+    w = o.warm_state(g, st.m, st.f, g0, g1, SIG)
+    ref = st.bm + [st.bf]
+    got = w.bm + [w.bf]
+    for a, b in zip(got, ref):
+        np.testing.assert_allclose(a, b, atol=1e-7 * max(1.0, np.abs(b).max()))
+    _, info = o.pdhg_step(g, w, g0, g1, SIG, 0.99 / SIG)
+    assert info.residual < 1e-7
+    # without the dual the first step moves b by O(1)
+    _, info0 = o.pdhg_step(g, o.warm_state(g, st.m, st.f, g0, g1, SIG, dual=False), g0, g1, SIG, 0.99 / SIG)
+    assert info0.residual > 1e-3
+    z = o.warm_state(g, st.m, st.f, g0, g1, SIG, dual=False)
+    assert all(not a.any() for a in z.bm + [z.bf] + z.bbm + [z.bbf])

@@ -1,0 +1,63 @@
+"""Pins of the network reference (oracle/unet.py): the forward convolution
+against scipy.signal.correlate, the data and weight gradients and the pooling
+pair against finite differences / adjointness."""
+import numpy as np
+import pytest
+import scipy.signal
+
+from oracle import unet
+
+
+def test_conv3d_matches_scipy_correlate():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((1, 4, 5, 6, 2))
+    w = rng.standard_normal((3, 27, 2))
+    y = unet.conv3d(x, w)
+    for o in range(3):
+        ref = np.zeros((4, 5, 6))
+        for c in range(2):
+            k = w[o, :, c].reshape(3, 3, 3)       # tap order (dt, dy, dx)
+            ref += scipy.signal.correlate(x[0, :, :, :, c], k, mode="same")
+        np.testing.assert_allclose(y[0, :, :, :, o], ref, atol=1e-12)
+
+
+def _num_grad(f, a, eps=1e-6):
+    g = np.zeros_like(a)
+    it = np.nditer(a, flags=["multi_index"])
+    for _ in it:
+        i = it.multi_index
+        a[i] += eps
+        fp = f()
+        a[i] -= 2 * eps
+        fm = f()
+        a[i] += eps
+        g[i] = (fp - fm) / (2 * eps)
+    return g
+
+
+def test_conv3d_gradients_by_finite_differences():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 3, 3, 4, 2))
+    w = rng.standard_normal((2, 27, 2))
+    gy = rng.standard_normal((1, 3, 3, 4, 2))
+    f = lambda: float(np.sum(unet.conv3d(x, w) * gy))
+    np.testing.assert_allclose(unet.conv3d_dgrad(gy, w), _num_grad(f, x), atol=1e-6)
+    np.testing.assert_allclose(unet.conv3d_wgrad(x, gy), _num_grad(f, w), atol=1e-6)
+
+
+def test_pool_upsample_adjoint_pairs():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((2, 3, 4, 6, 3))
+    g = rng.standard_normal((2, 3, 2, 3, 3))
+    # <pool(x), g> = <x, pool_backward(g)>,  <upsample(g), x> = <g, upsample_backward(x)>
+    assert np.sum(unet.pool(x) * g) == pytest.approx(np.sum(x * unet.pool_backward(g)), abs=1e-12)
+    assert np.sum(unet.upsample(g) * x) == pytest.approx(np.sum(g * unet.upsample_backward(x)), abs=1e-12)
+    np.testing.assert_allclose(unet.pool(unet.upsample(g)), g, atol=1e-15)
+
+
+def test_mse_gradient():
+    rng = np.random.default_rng(3)
+    out = rng.standard_normal((2, 5))
+    tgt = rng.standard_normal((2, 5))
+    loss, g = unet.mse(out, tgt)
+    np.testing.assert_allclose(g, _num_grad(lambda: unet.mse(out, tgt)[0], out), atol=1e-8)
