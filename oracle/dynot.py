@@ -457,24 +457,38 @@ def pdhg_step(g: Grid, st: State, f0: np.ndarray, f1: np.ndarray, sigma: float, 
 
 
 def warm_state(g: Grid, m: Sequence[np.ndarray], f: np.ndarray, f0: np.ndarray, f1: np.ndarray,
-               sigma: float, dual: bool = True, vmin: float = 1e-3) -> State:
+               sigma: float, dual: bool = True, vmin: float = 1e-3, wmax: Optional[float] = None,
+               support: float = 0.0) -> State:
     """Initial state of Algorithm 1 from a given path x0 = (m, f) (no counterpart in the paper).
 
     Without ``dual`` the dual starts at zero as in Algorithm 1.  With it,
     b = bbar = grad J(y) / sigma at y = K x0 + (0, f_b^+): step 2 has the
     optimality condition 0 = grad J(y) + sigma (y - K x - (0, f_b^+) - b), and
     step 3 leaves b unchanged exactly when y = K x + (0, f_b^+).  grad J(u, v)
-    = (u / v, -|u|^2 / (2 v^2)) for J = |u|^2 / (2 v); v is clamped below by vmin.
+    = (w, -|w|^2 / 2) with the velocity w = u / v, for J = |u|^2 / (2 v); v is
+    clamped below by vmin and |w| above by wmax, by default the diameter of the
+    domain (each axis spans n / scale, half of that when periodic): an optimal
+    path moves no mass faster than that per unit time.  Cells whose density is
+    below ``support`` keep b = 0: where the density vanishes, the dual of an
+    optimal path may be any point of the subdifferential of J at 0.
     """
     st = State.zeros(g)
     st.m = [np.asarray(a, float).copy() for a in m]
     st.f = np.asarray(f, float).copy()
     if dual:
+        if wmax is None:
+            wmax = float(np.sqrt(sum((g.n[k] / g.scale[k] * (0.5 if g.bc[k] == PERIODIC else 1.0)) ** 2
+                                     for k in range(g.d))))
         sm, sf = K(g, st.m, st.f)
-        v = np.maximum(sf + f_b_plus(g, f0, f1), vmin)
-        s2 = sum(a * a for a in sm)
-        st.bm = [a / (sigma * v) for a in sm]
-        st.bf = -s2 / (2.0 * sigma * v * v)
+        vraw = sf + f_b_plus(g, f0, f1)
+        v = np.maximum(vraw, vmin)
+        on = (vraw >= support).astype(float)
+        w = [on * a / v for a in sm]
+        speed = np.sqrt(sum(a * a for a in w))
+        lim = np.where(speed > wmax, wmax / np.maximum(speed, 1e-300), 1.0)
+        w = [a * lim for a in w]
+        st.bm = [a / sigma for a in w]
+        st.bf = -sum(a * a for a in w) / (2.0 * sigma)
         st.bbm = [a.copy() for a in st.bm]
         st.bbf = st.bf.copy()
     return st

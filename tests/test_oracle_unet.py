@@ -61,3 +61,47 @@ def test_mse_gradient():
     tgt = rng.standard_normal((2, 5))
     loss, g = unet.mse(out, tgt)
     np.testing.assert_allclose(g, _num_grad(lambda: unet.mse(out, tgt)[0], out), atol=1e-8)
+
+
+def _net(widths, cin, cout, seed):
+    rng = np.random.default_rng(seed)
+    params = {}
+    for name, ci, co in unet.unet_layers(widths, cin, cout):
+        params[name] = (rng.standard_normal((co, 27, ci)) * np.sqrt(2.0 / (27 * ci)), 0.1 * rng.standard_normal(co))
+    return params
+
+
+def test_round_bf16_against_the_format():
+    # representable values stay, halfway cases go to the even neighbour, 1 + 2^-9 is below halfway
+    assert unet.round_bf16(1.0) == 1.0
+    assert unet.round_bf16(1.0 + 2.0 ** -8) == 1.0          # halfway between 1 and 1 + 2^-7, even is 1
+    assert unet.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6   # halfway, even neighbour above
+    assert unet.round_bf16(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7
+    assert unet.round_bf16(-3.0) == -3.0
+    x = np.random.default_rng(5).standard_normal(1000)
+    r = unet.round_bf16(x)
+    assert np.all(np.abs(r - x) <= 2.0 ** -8 * np.abs(x))
+
+
+def test_unet_gradients_by_finite_differences():
+    widths = (2, 3)
+    params = _net(widths, 2, 2, 0)
+    rng = np.random.default_rng(1)
+    inp = rng.standard_normal((1, 2, 4, 4, 2))
+    target = rng.standard_normal((1, 2, 4, 4, 1))
+    loss, out, grads = unet.unet_forward_backward(params, widths, inp, target, 1)
+    assert set(grads) == {n for n, _, _ in unet.unet_layers(widths, 2, 2)}
+    eps = 1e-6
+    for name, (w, b) in params.items():
+        for arr, gidx in ((w, 0), (b, 1)):
+            flat = arr.reshape(-1)
+            for j in rng.choice(flat.size, size=min(4, flat.size), replace=False):
+                old = flat[j]
+                flat[j] = old + eps
+                lp = unet.unet_forward_backward(params, widths, inp, target, 1)[0]
+                flat[j] = old - eps
+                lm = unet.unet_forward_backward(params, widths, inp, target, 1)[0]
+                flat[j] = old
+                num = (lp - lm) / (2 * eps)
+                ana = grads[name][gidx].reshape(-1)[j]
+                assert abs(num - ana) <= 1e-6 + 1e-5 * abs(num), (name, gidx, j, num, ana)
