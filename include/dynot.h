@@ -124,6 +124,28 @@ ot_status ot_solve(ot_plan_t p, const float* f0, const float* f1, const ot_grid*
                    const float* init_path, ot_solve_stats* stats);
 
 /*
+ * ot_solve from a warm start x0 = init_path (required; packed path in the
+ * caller's units, host or device).  The first step of Algorithm 1 projects
+ * x0 - tau sigma K^T bbar0 onto the continuity constraint, so x0 need not
+ * satisfy it.  dual_init = 0 starts from b = bbar = 0 (as ot_solve does);
+ * dual_init = 1 starts from the dual of a fixed point of step 2 for x0:
+ * b = bbar = grad J(y) / sigma at y = K x0 + (0, f_b^+), where
+ * grad J(u, v) = (w, -|w|^2 / 2) with the velocity w = u / v (J of section 2;
+ * v is clamped below at 1e-3 of the mean density and |w| above at the
+ * domain's diameter, which no optimal path exceeds), in cells whose density
+ * (in units of the mean density) is at least dual_support, and b = 0 in the
+ * others, where the dual of an optimal path is not determined by the path.
+ * fallback_residual > 0: when the
+ * residual at the first check exceeds it, the call restarts from the cold
+ * start of Algorithm 1 and sets *used_cold = 1 (may be NULL); the iterations
+ * already spent count towards `iters` and stats->iterations.  The paper has
+ * no warm start; this is a convenience for learned or reused initial paths.
+ */
+ot_status ot_solve_warm(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
+                        const float* init_path, int dual_init, double dual_support, double fallback_residual,
+                        ot_solve_stats* stats, int* used_cold);
+
+/*
  * Copy the primal path x of the last iteration into caller buffers (any of
  * them may be NULL): f, and m along axes 0, 1, 2 (in the layout above, caller
  * units).  For ndim < 3 the unused m pointers are ignored.
@@ -216,6 +238,61 @@ ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* cons
 ot_status ot_batch_path(ot_batch_t b, int i, float* f, float* m0, float* m1, float* m2);
 int ot_batch_groups(ot_batch_t b);
 void ot_batch_destroy(ot_batch_t b);
+
+/*
+ * Warm-start network kernels (SURVEY / north_star "learned warm start"; the
+ * paper has no network).  A 3D U-Net over (t, y, x) maps the boundary densities
+ * of an RGB pair to an initial path x0 for Algorithm 1 (ot_solve's init_path).
+ * All pointers are DEVICE memory; work is ordered on `stream` (cudaStream_t,
+ * NULL = legacy default stream) and the calls return without synchronising.
+ * Activations are channels-last [N][T][Y][X][channels] in bf16; a tensor is
+ * addressed by its channel stride (xs, ys) and first channel (xo, yo), so that
+ * concatenations are channel slices.  Weights are [cout][27][cin] bf16 (tap =
+ * 9 (dt+1) + 3 (dy+1) + (dx+1)), bias fp32.
+ *
+ * ot_nn_conv3d: y = relu?(conv3x3x3(x, w) + bias), zero padding; cin % 16 == 0,
+ *   cout % 8 == 0; out_f32 selects an fp32 output.  Tensor cores (bf16, fp32 accumulate).
+ * ot_nn_conv3d_wgrad: dw (fp32 [cout][27][cin]) += sum_v dy[v] x[v + tap]; db (fp32,
+ *   may be NULL) += sum_v dy[v]; cin, cout % 16 == 0.  The data gradient is
+ *   ot_nn_conv3d with ot_nn_rotate_weights(w) (wr[ci][tap][co] = w[co][26-tap][ci]).
+ * ot_nn_relu_grad: g *= (y > 0).  ot_nn_pool / ot_nn_upsample: 2x2 average pooling
+ *   and nearest upsampling over (y, x) (Yc, Xc = coarse sizes), forward or backward.
+ * ot_nn_add_slice: y[:, yo:yo+C] += x[:, xo:xo+C].
+ * ot_nn_mse: loss (fp32, accumulated) += mean over M voxels x Cv channels of
+ *   (out - target)^2; g (bf16, gs channels) = its gradient.
+ * ot_nn_adamw: AdamW step `step` (1-based) on fp32 master weights p with fp32 grads g;
+ *   pb (bf16 copy, may be NULL) is refreshed.  ot_nn_to_bf16: fp32 -> bf16.
+ * ot_nn_make_input: network input [N][P][Y][X][Cp] (Cp >= 10) from densities f0, f1
+ *   ([N][3][Y][X] fp32) times scale[n] (device, NULL = 1): channels f0 (3), f1 (3),
+ *   (1 - tau) f0 + tau f1 at tau = (t + 1)/P (3), (t + 1/2)/P, zeros.
+ * ot_nn_path_channels: packed path (the ABI layout of ot_path / init_path, N problems)
+ *   <-> 12 cell-aligned fp32 channels [N][P][Y][X][cs] (cs >= 12; faces to the right of
+ *   each cell for m_x, m_y, m_c, then f; zero where the model has no variable; channels
+ *   12..cs-1 are not touched).
+ *   to_channels: ch = scale[n] (packed - L); otherwise packed = ch / scale[n] + L,
+ *   where L is zero for m and, when f0/f1 (same units as packed) are given, the
+ *   linear interpolation (1 - tau) f0 + tau f1 of the densities for f.
+ */
+ot_status ot_nn_conv3d(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo, const void* w,
+                       const float* bias, void* y, int ys, int yo, int relu, int out_f32, void* stream);
+ot_status ot_nn_conv3d_wgrad(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo,
+                             const void* dy, int dys, int dyo, float* dw, float* db, void* stream);
+ot_status ot_nn_rotate_weights(int Cin, int Cout, const void* w, void* wr, void* stream);
+ot_status ot_nn_relu_grad(long long M, int C, void* g, int gs, int go, const void* y, int ys, int yo, void* stream);
+ot_status ot_nn_pool(int N, int T, int Yc, int Xc, int C, const void* x, int xs, int xo, void* y, int ys, int yo,
+                     int backward, void* stream);
+ot_status ot_nn_upsample(int N, int T, int Yc, int Xc, int C, const void* x, int xs, int xo, void* y, int ys, int yo,
+                         int backward, void* stream);
+ot_status ot_nn_add_slice(long long M, int C, const void* x, int xs, int xo, void* y, int ys, int yo, void* stream);
+ot_status ot_nn_mse(long long M, int Cv, const float* out, int os, const float* target, void* g, int gs, float* loss,
+                    void* stream);
+ot_status ot_nn_adamw(long long n, float* p, const float* g, float* m, float* v, void* pb, float lr, float b1,
+                      float b2, float eps, float wd, int step, void* stream);
+ot_status ot_nn_to_bf16(long long n, const float* x, void* y, void* stream);
+ot_status ot_nn_make_input(int N, int P, int Y, int X, int Cp, const float* f0, const float* f1, const float* scale,
+                           void* out, void* stream);
+ot_status ot_nn_path_channels(int N, int Y, int X, int P, int to_channels, const float* scale, const float* f0,
+                              const float* f1, float* packed, float* ch, int cs, void* stream);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* ot_last_error(void);

@@ -64,6 +64,8 @@ def load_library() -> ctypes.CDLL:
     lib.ot_destroy.argtypes = [c_void_p]
     lib.ot_destroy.restype = None
     lib.ot_solve.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(Grid), c_int, c_double, c_void_p, POINTER(Stats)]
+    lib.ot_solve_warm.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(Grid), c_int, c_double, c_void_p, c_int,
+                                  c_double, c_double, POINTER(Stats), POINTER(c_int)]
     lib.ot_path.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.ot_path_size.argtypes = [c_void_p]
     lib.ot_path_size.restype = c_size_t
@@ -86,7 +88,7 @@ def load_library() -> ctypes.CDLL:
     lib.ot_batch_groups.restype = c_int
     lib.ot_batch_destroy.argtypes = [c_void_p]
     lib.ot_batch_destroy.restype = None
-    for name in ("ot_plan", "ot_solve", "ot_path", "ot_state_set", "ot_state_get", "ot_iterate", "ot_project",
+    for name in ("ot_plan", "ot_solve", "ot_solve_warm", "ot_path", "ot_state_set", "ot_state_get", "ot_iterate", "ot_project",
                  "ot_prox", "ot_profile", "ot_batch_create", "ot_batch_solve", "ot_batch_path"):
         getattr(lib, name).restype = c_int
     del fp
@@ -215,6 +217,23 @@ class Plan:
         st.converged = s == OT_OK
         return st
 
+    def solve_warm(self, f0, f1, init, iters: int, tol: float = 0.0, dual_init: bool = True,
+                   dual_support: float = 0.0, fallback_residual: float = 0.0, check_every: int = 0) -> Stats:
+        """ot_solve_warm: start from the packed path `init`; st.used_cold tells whether it fell back."""
+        st = Stats()
+        g = None
+        if check_every:
+            g = Grid.from_buffer_copy(self.grid)
+            g.check_every = check_every
+        used = c_int(0)
+        s = self.lib.ot_solve_warm(self.h, _ptr(f0), _ptr(f1), ctypes.byref(g) if g is not None else None, iters,
+                                   tol, _ptr(init), int(dual_init), dual_support, fallback_residual, ctypes.byref(st),
+                                   ctypes.byref(used))
+        _check(s, allow=(OT_ENOTCONV,))
+        st.converged = s == OT_OK
+        st.used_cold = bool(used.value)
+        return st
+
     def path(self, out: str = "numpy", device=None):
         """Returns {'f': ..., 'm': [m_0, ..., m_{d-1}]} for all problems (leading batch axis)."""
         nd = self.grid.ndim
@@ -245,6 +264,10 @@ class Plan:
         bb = np.empty(self.dual_size, np.float32)
         _check(self.lib.ot_state_get(self.h, _ptr(x), _ptr(b), _ptr(bb)))
         return x, b, bb
+
+    def x_into(self, x_packed):
+        """The primal x of the last check, packed, in solver units (mean density 1), into a caller buffer."""
+        _check(self.lib.ot_state_get(self.h, _ptr(x_packed), None, None))
 
     def iterate(self, iters: int) -> Stats:
         st = Stats()

@@ -353,23 +353,39 @@ void ot_destroy(ot_plan_t p) {
   delete p;
 }
 
+// the per-call grid of ot_solve / ot_solve_warm: sizes must match the plan; check_every applies
+static ot_status call_grid(PlanBase& P, const ot_grid* g) {
+  if (!g) return OT_OK;
+  if (g->ndim != P.grid.ndim || g->P != P.grid.P) return seterr(OT_EINVAL, "grid does not match the plan");
+  for (int k = 0; k < g->ndim; ++k)
+    if (g->n[k] != P.grid.n[k] || g->bc[k] != P.grid.bc[k]) return seterr(OT_EINVAL, "grid does not match the plan");
+  const double sg = g->sigma > 0 ? g->sigma : P.grid.sigma;
+  const double ta = g->tau > 0 ? g->tau : 0.99 / sg;
+  if (!(sg * ta < 1)) return seterr(OT_EINVAL, "need tau*sigma < 1");
+  if (sg != P.grid.sigma || ta != P.grid.tau)
+    return seterr(OT_EINVAL, "sigma/tau differ from the plan's; create a plan with them");
+  if (g->check_every > 0) P.grid.check_every = g->check_every;
+  return OT_OK;
+}
+
 ot_status ot_solve(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
                    const float* init_path, ot_solve_stats* stats) {
   if (!p) return seterr(OT_EINVAL, "plan is NULL");
   PlanBase& P = *p->impl;
-  if (g) {
-    if (g->ndim != P.grid.ndim || g->P != P.grid.P)
-      return seterr(OT_EINVAL, "grid does not match the plan");
-    for (int k = 0; k < g->ndim; ++k)
-      if (g->n[k] != P.grid.n[k] || g->bc[k] != P.grid.bc[k]) return seterr(OT_EINVAL, "grid does not match the plan");
-    const double sg = g->sigma > 0 ? g->sigma : P.grid.sigma;
-    const double ta = g->tau > 0 ? g->tau : 0.99 / sg;
-    if (!(sg * ta < 1)) return seterr(OT_EINVAL, "need tau*sigma < 1");
-    if (sg != P.grid.sigma || ta != P.grid.tau)
-      return seterr(OT_EINVAL, "sigma/tau differ from the plan's; create a plan with them");
-    if (g->check_every > 0) P.grid.check_every = g->check_every;
-  }
-  return P.solve(f0, f1, iters, tol, init_path, stats);
+  OT_TRY(call_grid(P, g));
+  return P.solve(f0, f1, iters, tol, init_path, 0, 0.0, 0.0, stats, nullptr);
+}
+
+ot_status ot_solve_warm(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
+                        const float* init_path, int dual_init, double dual_support, double fallback_residual,
+                        ot_solve_stats* stats, int* used_cold) {
+  if (!p) return seterr(OT_EINVAL, "plan is NULL");
+  if (!init_path) return seterr(OT_EINVAL, "init_path is required");
+  if (!(fallback_residual >= 0) || !(dual_support >= 0))
+    return seterr(OT_EINVAL, "fallback_residual and dual_support must be >= 0");
+  PlanBase& P = *p->impl;
+  OT_TRY(call_grid(P, g));
+  return P.solve(f0, f1, iters, tol, init_path, dual_init, dual_support, fallback_residual, stats, used_cold);
 }
 
 ot_status ot_path(ot_plan_t p, float* f, float* m0, float* m1, float* m2) {

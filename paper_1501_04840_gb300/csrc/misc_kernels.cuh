@@ -187,6 +187,50 @@ __global__ void k_make_a(Geo<T> g, CPtr4<T> x, CPtr4<T> bb, T* a0, T* a1, T* a2,
   }
 }
 
+// Dual of a fixed point of step 2 of Algorithm 1 for a given path x: there
+// y = K x + (0, f_b^+) and 0 = grad J(y) + sigma (y - K x - (0, f_b^+) - b), so
+// b = grad J(y) / sigma.  For J(u, v) = |u|^2 / (2 v) (section 2) the gradient
+// depends on the velocity w = u / v alone: grad J = (w, -|w|^2 / 2).  v is
+// clamped below by vmin and |w| above by wmax (an optimal path on the domain
+// moves no mass faster than the domain's diameter per unit time).  Cells with
+// v < vsup start from b = 0 (where the density vanishes the dual of an optimal
+// path lies anywhere in the subdifferential of J at 0, which this formula does
+// not predict).
+template <typename T>
+__global__ void k_dual_init(Geo<T> g, CPtr4<T> x, const T* __restrict__ f0, const T* __restrict__ f1, T inv_sigma,
+                            T vmin, T wmax, T vsup, T* b0, T* b1, T* b2, T* b3) {
+  const long long tot = (long long)g.B * g.N;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    const int ix = r % g.n1; r /= g.n1;
+    const int iy = r % g.n2; r /= g.n2;
+    const int ic = r % g.C; r /= g.C;
+    const int t = r % g.P;
+    const int b = (int)(r / g.P);
+    // left faces: the right face of the previous cell (wrapping on periodic axes, zero on Neumann ones)
+    T left[3];
+    left[0] = ix > 0 ? x.p[0][cidx(g, b, t, ix - 1, iy, ic)] : (g.per1 ? x.p[0][cidx(g, b, t, g.n1 - 1, iy, ic)] : T(0));
+    left[1] = iy > 0 ? x.p[1][cidx(g, b, t, ix, iy - 1, ic)] : (g.per2 ? x.p[1][cidx(g, b, t, ix, g.n2 - 1, ic)] : T(0));
+    left[2] = ic > 0 ? x.p[2][cidx(g, b, t, ix, iy, ic - 1)] : (g.perc ? x.p[2][cidx(g, b, t, ix, iy, g.C - 1)] : T(0));
+    T u[3];
+    for (int k = 0; k < 3; ++k) u[k] = T(0.5) * (left[k] + x.p[k][id]);   // right faces are zero where absent
+    const size_t s = (size_t)b * g.S + ix + (size_t)g.n1 * (iy + (size_t)g.n2 * ic);
+    const T fl = t == 0 ? f0[s] : x.p[3][cidx(g, b, t - 1, ix, iy, ic)];
+    const T fr = t == g.P - 1 ? f1[s] : x.p[3][id];
+    const T vraw = T(0.5) * (fl + fr);
+    const T v = max(vraw, vmin);
+    const T on = vraw >= vsup ? T(1) : T(0);
+    T w[3] = {on * u[0] / v, on * u[1] / v, on * u[2] / v};
+    const T w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const T lim = w2 > wmax * wmax ? wmax / sqrt(w2) : T(1);
+    for (int k = 0; k < 3; ++k) w[k] *= lim;
+    b0[id] = w[0] * inv_sigma;
+    b1[id] = w[1] * inv_sigma;
+    b2[id] = w[2] * inv_sigma;
+    b3[id] = -T(0.5) * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]) * inv_sigma;
+  }
+}
+
 // x = a - A^T phi at the right faces (the correction of the projection).
 template <typename T>
 __global__ void k_correct(Geo<T> g, Arrays<T> A) {

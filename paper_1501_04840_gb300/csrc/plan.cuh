@@ -582,7 +582,8 @@ struct Plan final : PlanBase {
     return collect_check(per, out);
   }
 
-  ot_status drive(int iters, double tol, int check_every, ot_solve_stats* stats) {
+  ot_status drive(int iters, double tol, int check_every, ot_solve_stats* stats, double fallback = 0.0,
+                  int* used_cold = nullptr) {
     if (iters < 1) return seterr(OT_EINVAL, "iters must be >= 1");
     CUDA_OK(cudaEventRecord(ev[10], st));
     int done = 0;
@@ -594,7 +595,14 @@ struct Plan final : PlanBase {
       OT_TRY(run_plain(chunk - 1));
       const bool last = (done + chunk == iters);
       OT_TRY(run_check(true, ck));
+      const bool first = (done == 0);
       done += chunk;
+      if (first && fallback > 0 && ck.residual > fallback) {
+        // the warm start is worse than the threshold: restart from x = 0, b = bbar = 0
+        OT_TRY(cold_start());
+        if (used_cold) *used_cold = 1;
+        continue;
+      }
       if (tol > 0 && ck.residual <= tol) {
         converged = true;
         break;
@@ -698,26 +706,46 @@ struct Plan final : PlanBase {
     return OT_OK;
   }
 
-  ot_status solve(const float* f0, const float* f1, int iters, double tol, const float* init,
-                  ot_solve_stats* stats) override {
+  ot_status solve(const float* f0, const float* f1, int iters, double tol, const float* init, int dual_init,
+                  double dual_support, double fallback, ot_solve_stats* stats, int* used_cold) override {
     if (!f0 || !f1) return seterr(OT_EINVAL, "f0 and f1 are required");
+    if (used_cold) *used_cold = 0;
     OT_TRY(load_boundary(f0, f1, true));
     OT_TRY(cold_start());
     if (init) {
-      // x0 = init (scaled to solver units per problem), b = bbar = 0 -> a = x0
+      // x0 = init (scaled to solver units per problem) into x, then b = bbar = 0 or the fixed-point dual
       const size_t n = (size_t)B * cp.total;
       CUDA_OK(cudaMemcpyAsync(stage, init, n * sizeof(float), cudaMemcpyDefault, st));
-      // one scale per batch entry: unpack problem by problem
-      for (int bi = 0; bi < B; ++bi) {
+      for (int bi = 0; bi < B; ++bi) {   // one scale per problem
         Geo<T> g1 = g;
         g1.B = 1;
         const size_t off = (size_t)bi * N;
         k_unpack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, stage + (size_t)bi * cp.total, 1.0 / out_scale[bi],
-                                                    a[0][0] + off, a[0][1] + off, a[0][2] + off, a[0][3] + off);
+                                                    x[0] + off, x[1] + off, x[2] + off, x[3] + off);
         CUDA_OK(cudaGetLastError());
       }
+      const long long cells = (long long)B * N;
+      if (dual_init) {
+        // the domain's diameter: extent n_k / scale_k per axis, half of it on periodic axes
+        double diam2 = 0;
+        for (int k = 0; k < grid.ndim; ++k) {
+          const double e = grid.n[k] / grid.axis_scale[k] * (grid.bc[k] == OT_BC_PERIODIC ? 0.5 : 1.0);
+          diam2 += e * e;
+        }
+        k_dual_init<T><<<grid1d(cells), 256, 0, st>>>(g, CPtr4<T>{{x[0], x[1], x[2], x[3]}}, f0n, f1n,
+                                                      T(1.0 / grid.sigma), T(1e-3), T(std::sqrt(diam2)),
+                                                      T(dual_support), b[0][0], b[0][1], b[0][2], b[0][3]);
+        CUDA_OK(cudaGetLastError());
+        for (int k = 0; k < 4; ++k)
+          CUDA_OK(cudaMemcpyAsync(b[1][k], b[0][k], cells * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      }
+      // a = x0 - tau sigma K^T bbar0 (bbar0 = b0)
+      k_make_a<T><<<grid1d(cells), 256, 0, st>>>(g, CPtr4<T>{{x[0], x[1], x[2], x[3]}},
+                                                CPtr4<T>{{b[0][0], b[0][1], b[0][2], b[0][3]}}, a[0][0], a[0][1],
+                                                a[0][2], a[0][3]);
+      CUDA_OK(cudaGetLastError());
     }
-    return drive(iters, tol, grid.check_every, stats);
+    return drive(iters, tol, grid.check_every, stats, init ? fallback : 0.0, used_cold);
   }
 
   // ---- hooks for mixed-size batches (several plans captured into one graph)
