@@ -59,6 +59,14 @@ def parse():
                     help="mixed-size batch: one-by-one solves against one batched graph, time to residual 1e-4")
     ap.add_argument("--precision-study", action="store_true",
                     help="errors of the FP32 / mixed plans against the FP64 plan and the oracle (2000 iterations)")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="learned warm start at 128x128x3x32: train the U-Net on solver-generated pairs, then cold "
+                         "vs warm time to residual 1e-4 on held-out pairs")
+    ap.add_argument("--ws-train-pairs", type=int, default=256)
+    ap.add_argument("--ws-steps", type=int, default=1000)
+    ap.add_argument("--ws-eval-pairs", type=int, default=16)
+    ap.add_argument("--ws-load", type=str, default="default",
+                    help="U-Net weights to evaluate ('default': the package's trained weights; '' trains new ones)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the kernel profile, time-to-tolerance and end-to-end legs (for profiler runs)")
     return ap.parse_args()
@@ -480,10 +488,58 @@ def batch_bench(tol: float = 1e-4, check_every: int = 10):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# learned warm start (not part of the default run)
+# ---------------------------------------------------------------------------
+
+def warmstart_bench(args, side: int = 128, P: int = 32, blobs: int = 16, tol: float = 1e-4):
+    import torch
+    from paper_1501_04840_gb300 import _build, warmstart as W
+    _build.build()
+    t_data = t_train = 0.0
+    with W.side_stream():
+        if args.ws_load:
+            path = W.DEFAULT_WEIGHTS if args.ws_load == "default" else args.ws_load
+            net, meta = W.UNet.load(path)
+            ntrain, steps = meta.get("train_pairs", 0), meta.get("steps", 0)
+        else:
+            ntrain, steps = args.ws_train_pairs, args.ws_steps
+            t = time.perf_counter()
+            data = W.solve_targets(range(ntrain), side, P, blobs, tol=1e-5)
+            t_data = time.perf_counter() - t
+            net = W.UNet()
+            t = time.perf_counter()
+            W.train(net, data, P, steps)
+            t_train = time.perf_counter() - t
+            del data
+            torch.cuda.empty_cache()
+        fallback = W.cold_first_residual(range(8), side, P, blobs)
+        ev = W.evaluate(net, list(range(1_000_000, 1_000_000 + args.ws_eval_pairs)), side, P, blobs, tol=tol,
+                        fallback=fallback, variants=(("net", "net", 0.0), ("zero", "zero", 0.0)))
+    line = {"metric": "time to residual %g at %dx%dx3x%d, learned warm start vs cold start" % (tol, side, side, P),
+            "unit": "ms", "higher_is_better": False,
+            "cold_ms": ev["cold"]["ms"]["mean"], "warm_ms": ev["net"]["ms"]["mean"],
+            "speedup": ev["cold"]["ms"]["mean"] / ev["net"]["ms"]["mean"],
+            "cold_iters": ev["cold"]["iters"], "warm_iters": ev["net"]["iters"],
+            "warm_zero_dual_iters": ev["zero"]["iters"], "infer_ms": ev["net"]["infer_ms"]["mean"],
+            "err_vs_converged": {"cold": ev["cold"]["err"]["mean"], "warm": ev["net"]["err"]["mean"]},
+            "fallbacks": ev["net"]["fallbacks"], "fallback_residual": fallback,
+            "config": {"workload": "rgb %dx%dx3, P=%d, %d blobs/channel" % (side, side, P, blobs),
+                       "params": net.n_params, "widths": list(net.widths), "train_pairs": ntrain, "steps": steps,
+                       "eval_pairs": ev["pairs"], "data_s": t_data, "train_s": t_train,
+                       "weights": ("package weights" if args.ws_load == "default" else args.ws_load)
+                       if args.ws_load else "trained in this run"},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.batch:
         batch_bench()
+        return
+    if args.warmstart:
+        warmstart_bench(args)
         return
     if args.precision_study:
         precision_study(args.iters if args.iters != 1000 else 2000)

@@ -127,23 +127,26 @@ ot_status ot_solve(ot_plan_t p, const float* f0, const float* f1, const ot_grid*
  * ot_solve from a warm start x0 = init_path (required; packed path in the
  * caller's units, host or device).  The first step of Algorithm 1 projects
  * x0 - tau sigma K^T bbar0 onto the continuity constraint, so x0 need not
- * satisfy it.  dual_init = 0 starts from b = bbar = 0 (as ot_solve does);
- * dual_init = 1 starts from the dual of a fixed point of step 2 for x0:
- * b = bbar = grad J(y) / sigma at y = K x0 + (0, f_b^+), where
- * grad J(u, v) = (w, -|w|^2 / 2) with the velocity w = u / v (J of section 2;
- * v is clamped below at 1e-3 of the mean density and |w| above at the
- * domain's diameter, which no optimal path exceeds), in cells whose density
- * (in units of the mean density) is at least dual_support, and b = 0 in the
- * others, where the dual of an optimal path is not determined by the path.
- * fallback_residual > 0: when the
- * residual at the first check exceeds it, the call restarts from the cold
- * start of Algorithm 1 and sets *used_cold = 1 (may be NULL); the iterations
- * already spent count towards `iters` and stats->iterations.  The paper has
- * no warm start; this is a convenience for learned or reused initial paths.
+ * satisfy it.  The dual starts from
+ *   - init_dual != NULL: b = bbar = init_dual (the packed dual layout of
+ *     ot_state_get; the dual is a velocity and has no density units);
+ *   - otherwise dual_init = 0: b = bbar = 0 (as ot_solve does);
+ *   - otherwise dual_init = 1: the dual of a fixed point of step 2 for x0,
+ *     b = bbar = grad J(y) / sigma at y = K x0 + (0, f_b^+), where
+ *     grad J(u, v) = (w, -|w|^2 / 2) with the velocity w = u / v (J of
+ *     section 2; v is clamped below at 1e-3 of the mean density and |w| above
+ *     at the domain's diameter, which no optimal path exceeds), in cells whose
+ *     density (in units of the mean density) is at least dual_support, and
+ *     b = 0 in the others, where an optimal path does not determine its dual.
+ * fallback_residual > 0: when the residual at the first check exceeds it, the
+ * call restarts from the cold start of Algorithm 1 and sets *used_cold = 1
+ * (used_cold may be NULL); the iterations already spent count towards `iters`
+ * and stats->iterations.  The paper has no warm start; this serves learned or
+ * reused initial paths.
  */
 ot_status ot_solve_warm(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
-                        const float* init_path, int dual_init, double dual_support, double fallback_residual,
-                        ot_solve_stats* stats, int* used_cold);
+                        const float* init_path, const float* init_dual, int dual_init, double dual_support,
+                        double fallback_residual, ot_solve_stats* stats, int* used_cold);
 
 /*
  * Copy the primal path x of the last iteration into caller buffers (any of
@@ -259,7 +262,8 @@ void ot_batch_destroy(ot_batch_t b);
  *   and nearest upsampling over (y, x) (Yc, Xc = coarse sizes), forward or backward.
  * ot_nn_add_slice: y[:, yo:yo+C] += x[:, xo:xo+C].
  * ot_nn_mse: loss (fp32, accumulated) += mean over M voxels x Cv channels of
- *   (out - target)^2; g (bf16, gs channels) = its gradient.
+ *   (out - target)^2 (out fp32 with channel stride os, target bf16 [M][Cv]);
+ *   g (bf16, gs channels) = its gradient, zero in channels Cv..gs-1.
  * ot_nn_adamw: AdamW step `step` (1-based) on fp32 master weights p with fp32 grads g;
  *   pb (bf16 copy, may be NULL) is refreshed.  ot_nn_to_bf16: fp32 -> bf16.
  * ot_nn_make_input: network input [N][P][Y][X][Cp] (Cp >= 10) from densities f0, f1
@@ -272,6 +276,9 @@ void ot_batch_destroy(ot_batch_t b);
  *   to_channels: ch = scale[n] (packed - L); otherwise packed = ch / scale[n] + L,
  *   where L is zero for m and, when f0/f1 (same units as packed) are given, the
  *   linear interpolation (1 - tau) f0 + tau f1 of the densities for f.
+ * ot_nn_dual_channels: packed dual (the layout of ot_state_get's b: per problem
+ *   b_mx, b_my, b_mc, b_f, each [P][3][Y][X]) <-> channels co + 3k + c of
+ *   [N][P][Y][X][cs].
  */
 ot_status ot_nn_conv3d(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo, const void* w,
                        const float* bias, void* y, int ys, int yo, int relu, int out_f32, void* stream);
@@ -284,7 +291,7 @@ ot_status ot_nn_pool(int N, int T, int Yc, int Xc, int C, const void* x, int xs,
 ot_status ot_nn_upsample(int N, int T, int Yc, int Xc, int C, const void* x, int xs, int xo, void* y, int ys, int yo,
                          int backward, void* stream);
 ot_status ot_nn_add_slice(long long M, int C, const void* x, int xs, int xo, void* y, int ys, int yo, void* stream);
-ot_status ot_nn_mse(long long M, int Cv, const float* out, int os, const float* target, void* g, int gs, float* loss,
+ot_status ot_nn_mse(long long M, int Cv, const float* out, int os, const void* target, void* g, int gs, float* loss,
                     void* stream);
 ot_status ot_nn_adamw(long long n, float* p, const float* g, float* m, float* v, void* pb, float lr, float b1,
                       float b2, float eps, float wd, int step, void* stream);
@@ -293,6 +300,8 @@ ot_status ot_nn_make_input(int N, int P, int Y, int X, int Cp, const float* f0, 
                            void* out, void* stream);
 ot_status ot_nn_path_channels(int N, int Y, int X, int P, int to_channels, const float* scale, const float* f0,
                               const float* f1, float* packed, float* ch, int cs, void* stream);
+ot_status ot_nn_dual_channels(int N, int Y, int X, int P, int to_channels, float* packed, float* ch, int cs, int co,
+                              void* stream);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* ot_last_error(void);

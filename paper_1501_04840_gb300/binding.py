@@ -64,8 +64,8 @@ def load_library() -> ctypes.CDLL:
     lib.ot_destroy.argtypes = [c_void_p]
     lib.ot_destroy.restype = None
     lib.ot_solve.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(Grid), c_int, c_double, c_void_p, POINTER(Stats)]
-    lib.ot_solve_warm.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(Grid), c_int, c_double, c_void_p, c_int,
-                                  c_double, c_double, POINTER(Stats), POINTER(c_int)]
+    lib.ot_solve_warm.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(Grid), c_int, c_double, c_void_p, c_void_p,
+                                  c_int, c_double, c_double, POINTER(Stats), POINTER(c_int)]
     lib.ot_path.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.ot_path_size.argtypes = [c_void_p]
     lib.ot_path_size.restype = c_size_t
@@ -218,8 +218,10 @@ class Plan:
         return st
 
     def solve_warm(self, f0, f1, init, iters: int, tol: float = 0.0, dual_init: bool = True,
-                   dual_support: float = 0.0, fallback_residual: float = 0.0, check_every: int = 0) -> Stats:
-        """ot_solve_warm: start from the packed path `init`; st.used_cold tells whether it fell back."""
+                   dual_support: float = 0.0, fallback_residual: float = 0.0, check_every: int = 0,
+                   init_dual=None) -> Stats:
+        """ot_solve_warm: start from the packed path `init` (and the packed dual `init_dual`, if given);
+        st.used_cold tells whether it fell back to the cold start."""
         st = Stats()
         g = None
         if check_every:
@@ -227,7 +229,8 @@ class Plan:
             g.check_every = check_every
         used = c_int(0)
         s = self.lib.ot_solve_warm(self.h, _ptr(f0), _ptr(f1), ctypes.byref(g) if g is not None else None, iters,
-                                   tol, _ptr(init), int(dual_init), dual_support, fallback_residual, ctypes.byref(st),
+                                   tol, _ptr(init), _ptr(init_dual), int(dual_init), dual_support, fallback_residual,
+                                   ctypes.byref(st),
                                    ctypes.byref(used))
         _check(s, allow=(OT_ENOTCONV,))
         st.converged = s == OT_OK
@@ -268,6 +271,10 @@ class Plan:
     def x_into(self, x_packed):
         """The primal x of the last check, packed, in solver units (mean density 1), into a caller buffer."""
         _check(self.lib.ot_state_get(self.h, _ptr(x_packed), None, None))
+
+    def dual_into(self, b_packed):
+        """The dual b of the last iteration, packed, into a caller buffer."""
+        _check(self.lib.ot_state_get(self.h, None, _ptr(b_packed), None))
 
     def iterate(self, iters: int) -> Stats:
         st = Stats()

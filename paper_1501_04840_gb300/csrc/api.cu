@@ -373,19 +373,20 @@ ot_status ot_solve(ot_plan_t p, const float* f0, const float* f1, const ot_grid*
   if (!p) return seterr(OT_EINVAL, "plan is NULL");
   PlanBase& P = *p->impl;
   OT_TRY(call_grid(P, g));
-  return P.solve(f0, f1, iters, tol, init_path, 0, 0.0, 0.0, stats, nullptr);
+  return P.solve(f0, f1, iters, tol, init_path, nullptr, 0, 0.0, 0.0, stats, nullptr);
 }
 
 ot_status ot_solve_warm(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
-                        const float* init_path, int dual_init, double dual_support, double fallback_residual,
-                        ot_solve_stats* stats, int* used_cold) {
+                        const float* init_path, const float* init_dual, int dual_init, double dual_support,
+                        double fallback_residual, ot_solve_stats* stats, int* used_cold) {
   if (!p) return seterr(OT_EINVAL, "plan is NULL");
   if (!init_path) return seterr(OT_EINVAL, "init_path is required");
   if (!(fallback_residual >= 0) || !(dual_support >= 0))
     return seterr(OT_EINVAL, "fallback_residual and dual_support must be >= 0");
   PlanBase& P = *p->impl;
   OT_TRY(call_grid(P, g));
-  return P.solve(f0, f1, iters, tol, init_path, dual_init, dual_support, fallback_residual, stats, used_cold);
+  return P.solve(f0, f1, iters, tol, init_path, init_dual, dual_init, dual_support, fallback_residual, stats,
+                 used_cold);
 }
 
 ot_status ot_path(ot_plan_t p, float* f, float* m0, float* m1, float* m2) {

@@ -275,7 +275,7 @@ static __global__ void k_prox_cells(int count, int ncomp, float sigma, const flo
     const float a1 = ncomp > 1 ? am[(size_t)count + i] : 0.f;
     const float a2 = ncomp > 2 ? am[2 * (size_t)count + i] : 0.f;
     float u0, u1, u2, vv;
-    prox_J<float>(a0, a1, a2, af[i], sigma, u0, u1, u2, vv);
+    prox_J<float>(a0, a1, a2, af[i], sigma, 1.f / sigma, u0, u1, u2, vv);
     u[i] = u0;
     if (ncomp > 1) u[(size_t)count + i] = u1;
     if (ncomp > 2) u[2 * (size_t)count + i] = u2;

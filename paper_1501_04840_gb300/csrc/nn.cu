@@ -296,15 +296,16 @@ __global__ void k_add_slice(long long M, int C, const bf16* __restrict__ x, int 
   }
 }
 
-// loss += sum over v, c < Cv of (out - target)^2 / count; g = 2 (out - target) / count (bf16, Cg channels)
-__global__ void k_mse(long long M, int Cv, const float* __restrict__ out, int os, const float* __restrict__ target,
+// loss += sum over v, c < Cv of (out - target)^2 / count; g = 2 (out - target) / count (bf16, gs channels);
+// target is bf16 [M][Cv]
+__global__ void k_mse(long long M, int Cv, const float* __restrict__ out, int os, const bf16* __restrict__ target,
                       bf16* __restrict__ g, int gs, float inv_count, float* __restrict__ loss) {
   float s = 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M * gs; i += (long long)gridDim.x * blockDim.x) {
     const long long vv = i / gs;
     const int c = (int)(i % gs);
     float d = 0.f;
-    if (c < Cv) d = out[vv * os + c] - target[vv * Cv + c];
+    if (c < Cv) d = out[vv * os + c] - __bfloat162float(target[vv * Cv + c]);
     s += d * d;
     g[i] = __float2bfloat16(2.f * d * inv_count);
   }
@@ -409,6 +410,27 @@ __global__ void k_path_channels(int Y, int X, int P, int to_channels, const floa
   }
 }
 
+// Packed dual (the ABI's layout of ot_state_get: per problem the cell arrays b_mx | b_my | b_mc | b_f,
+// each [t][c][y][x]) <-> channels co + k*3 + c of [N][P][Y][X][cs].
+__global__ void k_dual_channels(int Y, int X, int P, int to_channels, float* __restrict__ packed,
+                                float* __restrict__ ch, int cs, int co, int Nb) {
+  const long long cells = (long long)P * 3 * Y * X;
+  const long long n = (long long)Nb * P * Y * X * 12;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int ch12 = (int)(i % 12);
+    long long q = i / 12;
+    const int x = (int)(q % X); q /= X;
+    const int y = (int)(q % Y); q /= Y;
+    const int t = (int)(q % P);
+    const int b = (int)(q / P);
+    const int k = ch12 / 3, c = ch12 % 3;
+    const long long idx = ((long long)b * 4 + k) * cells + (((long long)t * 3 + c) * Y + y) * X + x;
+    const long long e = (i / 12) * cs + co + ch12;
+    if (to_channels) ch[e] = packed[idx];
+    else packed[idx] = ch[e];
+  }
+}
+
 inline int blocks_for(long long n) { return (int)((n + 255) / 256 < 152 * 32 ? (n + 255) / 256 : 152 * 32); }
 
 }  // namespace
@@ -501,10 +523,10 @@ ot_status ot_nn_add_slice(long long M, int C, const void* x, int xs, int xo, voi
   return OT_OK;
 }
 
-ot_status ot_nn_mse(long long M, int Cv, const float* out, int os, const float* target, void* g, int gs, float* loss,
+ot_status ot_nn_mse(long long M, int Cv, const float* out, int os, const void* target, void* g, int gs, float* loss,
                     void* stream) {
   if (Cv < 1 || Cv > os || Cv > gs) return seterr(OT_EINVAL, "mse: need 1 <= Cv <= os, gs");
-  k_mse<<<blocks_for(M * gs), 256, 0, (cudaStream_t)stream>>>(M, Cv, out, os, target, (bf16*)g, gs,
+  k_mse<<<blocks_for(M * gs), 256, 0, (cudaStream_t)stream>>>(M, Cv, out, os, (const bf16*)target, (bf16*)g, gs,
                                                                1.f / (float)(M * Cv), loss);
   NN_LAUNCH_CHECK();
   return OT_OK;
@@ -539,6 +561,15 @@ ot_status ot_nn_path_channels(int N, int Y, int X, int P, int to_channels, const
   if (cs < 12) return seterr(OT_EINVAL, "path_channels: channel stride must be >= 12");
   k_path_channels<<<blocks_for((long long)N * P * Y * X * 12), 256, 0, (cudaStream_t)stream>>>(
       Y, X, P, to_channels, scale, f0, f1, packed, ch, cs, N);
+  NN_LAUNCH_CHECK();
+  return OT_OK;
+}
+
+ot_status ot_nn_dual_channels(int N, int Y, int X, int P, int to_channels, float* packed, float* ch, int cs, int co,
+                              void* stream) {
+  if (co < 0 || co + 12 > cs) return seterr(OT_EINVAL, "dual_channels: channels co..co+11 must fit the stride");
+  k_dual_channels<<<blocks_for((long long)N * P * Y * X * 12), 256, 0, (cudaStream_t)stream>>>(
+      Y, X, P, to_channels, packed, ch, cs, co, N);
   NN_LAUNCH_CHECK();
   return OT_OK;
 }

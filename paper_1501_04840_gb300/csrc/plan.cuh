@@ -18,7 +18,10 @@ namespace dynot {
 
 constexpr int kThreadsXt = 256;
 constexpr int kThreadsUpd = 128;
-constexpr int kW = 8;   // x-strip width of the y/colour pass
+#ifndef DYNOT_YC_W
+#define DYNOT_YC_W 8
+#endif
+constexpr int kW = DYNOT_YC_W;   // x-strip width of the y/colour pass
 
 inline int pmax_for(int P) { return P <= 16 ? 16 : (P <= 32 ? 32 : 64); }
 inline bool fft_len(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
@@ -706,8 +709,9 @@ struct Plan final : PlanBase {
     return OT_OK;
   }
 
-  ot_status solve(const float* f0, const float* f1, int iters, double tol, const float* init, int dual_init,
-                  double dual_support, double fallback, ot_solve_stats* stats, int* used_cold) override {
+  ot_status solve(const float* f0, const float* f1, int iters, double tol, const float* init,
+                  const float* init_dual, int dual_init, double dual_support, double fallback, ot_solve_stats* stats,
+                  int* used_cold) override {
     if (!f0 || !f1) return seterr(OT_EINVAL, "f0 and f1 are required");
     if (used_cold) *used_cold = 0;
     OT_TRY(load_boundary(f0, f1, true));
@@ -725,7 +729,11 @@ struct Plan final : PlanBase {
         CUDA_OK(cudaGetLastError());
       }
       const long long cells = (long long)B * N;
-      if (dual_init) {
+      if (init_dual) {
+        OT_TRY(load_dual(init_dual, b[0]));
+        for (int k = 0; k < 4; ++k)
+          CUDA_OK(cudaMemcpyAsync(b[1][k], b[0][k], cells * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      } else if (dual_init) {
         // the domain's diameter: extent n_k / scale_k per axis, half of it on periodic axes
         double diam2 = 0;
         for (int k = 0; k < grid.ndim; ++k) {

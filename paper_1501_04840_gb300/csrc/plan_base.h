@@ -66,9 +66,10 @@ struct PlanBase {
   // init: packed path (caller units) or NULL; dual_init: b = bbar = grad J(K x0 + (0, f_b^+)) / sigma
   // where the density is >= dual_support (solver units), zero elsewhere;
   // fallback > 0: restart cold when the residual of the first check exceeds it (*used_cold = 1).
+  // init_dual (packed dual, or NULL) replaces the formula.
   virtual ot_status solve(const float* f0, const float* f1, int iters, double tol, const float* init,
-                          int dual_init, double dual_support, double fallback, ot_solve_stats* stats,
-                          int* used_cold) = 0;
+                          const float* init_dual, int dual_init, double dual_support, double fallback,
+                          ot_solve_stats* stats, int* used_cold) = 0;
   virtual ot_status path(float* f, float* m0, float* m1, float* m2) = 0;
   virtual ot_status state_set(const float* f0, const float* f1, const float* x, const float* b,
                               const float* bb) = 0;

@@ -31,6 +31,10 @@ __device__ __forceinline__ size_t cidx(const Geo<T>& g, int b, int t, int ix, in
 
 __device__ __forceinline__ float fdiv_fast(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv_fast(double a, double b) { return a / b; }
+// d^(1/3) for Newton's starting point: in FP32 the fast power intrinsic (a few ulp off,
+// which Newton corrects), in FP64 the library cube root.
+__device__ __forceinline__ float cbrt_start(float d) { return d > 0.f ? __powf(d, 1.f / 3.f) : 0.f; }
+__device__ __forceinline__ double cbrt_start(double d) { return cbrt(d); }
 
 // Per-cell proximal map of J (section 3, step 2):
 //   argmin_{u,v} |u|^2/(2v) + sigma/2 |u - a_m|^2 + sigma/2 (v - a_f)^2.
@@ -43,7 +47,7 @@ __device__ __forceinline__ double fdiv_fast(double a, double b) { return a / b; 
 // for c <= 0.  q is increasing and convex for z >= max(e, 0), so Newton's
 // method from that bound decreases monotonically to the root.
 template <typename T>
-__device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T& u0, T& u1, T& u2, T& v) {
+__device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T inv_sigma, T& u0, T& u1, T& u2, T& v) {
   const T s2 = am0 * am0 + am1 * am1 + am2 * am2;
   const T e = sigma * af;
   const T d = T(0.5) * sigma * sigma * s2;
@@ -52,12 +56,13 @@ __device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T& u0
     return;
   }
   const T c = T(1) + e;
+  const T cbd = cbrt_start(d);
   T z;
   if (c > T(0)) {
-    const T del = min(cbrt(d), fdiv_fast(d, c * c));
+    const T del = min(cbd, fdiv_fast(d, c * c));
     z = e + del;
   } else {
-    z = min(cbrt(d), sqrt(fdiv_fast(d, -c))) - T(1);
+    z = min(cbd, sqrt(fdiv_fast(d, -c))) - T(1);
   }
   z = max(z, T(0));
   // Stop when the step is below a few units in the last place of the data
@@ -78,11 +83,11 @@ __device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T& u0
     if (!(fabs(step) > eps * z + tol)) break;
   }
   z = max(z, T(0));
-  const T r = z / (T(1) + z);
+  const T r = fdiv_fast(z, T(1) + z);
   u0 = r * am0;
   u1 = r * am1;
   u2 = r * am2;
-  v = z / sigma;
+  v = z * inv_sigma;
 }
 
 // ---------------------------------------------------------------------------
@@ -154,7 +159,7 @@ struct CellCtx {
 #pragma unroll
     for (int k = 0; k < 4; ++k) bo[k] = A.b[k][i0];
     const T am0 = kx[0] + bo[0], am1 = kx[1] + bo[1], am2 = kx[2] + bo[2], af = kx[3] + bo[3];
-    prox_J<T>(am0, am1, am2, af, g.sigma, U0, U1, U2, V);
+    prox_J<T>(am0, am1, am2, af, g.sigma, T(1) / g.sigma, U0, U1, U2, V);
     bn[0] = am0 - U0;
     bn[1] = am1 - U1;
     bn[2] = am2 - U2;
@@ -302,7 +307,10 @@ struct XtTables {
 #define DYNOT_TFFT 1
 #endif
 #ifndef DYNOT_XT_MINB
-#define DYNOT_XT_MINB 2   // blocks per SM the x/t kernels are compiled for
+#define DYNOT_XT_MINB 2   // blocks per SM the forward x/t kernel is compiled for
+#endif
+#ifndef DYNOT_XTC_MINB
+#define DYNOT_XTC_MINB 3  // blocks per SM the inverse x/t kernel is compiled for (measured faster at 3)
 #endif
 template <int PMAX, int N1>
 __device__ __forceinline__ bool t_by_fft(int P) { return DYNOT_TFFT && N1 > 0 && PMAX <= 32 && P == PMAX; }
@@ -407,7 +415,7 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
 
 // K_C: inverse DCT along t and x -> phi
 template <typename T, int N1, int N2, int PMAX>
-__global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_inv_xt(Geo<T> g, const T* __restrict__ phihat, T* __restrict__ phi,
+__global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const T* __restrict__ phihat, T* __restrict__ phi,
                                                 XtTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int y = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
@@ -569,7 +577,7 @@ __global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ h
           const double ld = tb.lam1d[x0 + w] + tb.lam2d[ky] + tb.lamtd[kt] + tb.lamcd[j];
           co[j] = ld > 0.0 ? (T)((double)s / ld) : T(0);
         } else {
-          co[j] = s / lam;
+          co[j] = fdiv_fast(s, lam);   // a few ulp; the low modes above take the exact FP64 path
         }
       }
 #pragma unroll
@@ -667,6 +675,7 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
   T* __restrict__ qb2 = A.bn[2] + col;
   T* __restrict__ qb3 = A.bn[3] + col;
   const T s1 = g.s1, s2 = g.s2, scl = g.sc, sp = g.sp, ts = g.ts, half = T(0.5);
+  const T isg = T(1) / g.sigma;
   const bool perc = g.perc;
   if (CHECK) {
     for (int i = threadIdx.x + kTX * threadIdx.y; i < 64; i += kTX * kTY) smass[i] = 0.0;
@@ -740,7 +749,7 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
       const T k3 = half * (xfp[c] + xr[c][3]);
       const T am0 = k0 + lb[c][0], am1 = k1 + lb[c][1], am2 = k2 + lb[c][2], af = k3 + lb[c][3];
       T U0, U1, U2, V;
-      prox_J<T>(am0, am1, am2, af, g.sigma, U0, U1, U2, V);
+      prox_J<T>(am0, am1, am2, af, g.sigma, isg, U0, U1, U2, V);
       bn[c][0] = am0 - U0;
       bn[c][1] = am1 - U1;
       bn[c][2] = am2 - U2;
@@ -757,7 +766,7 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
         }
         r_db += (double)db2;
         r_kx += (double)(k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3);
-        if (V > T(0)) r_J += (double)((U0 * U0 + U1 * U1 + U2 * U2) / (T(2) * V));
+        if (V > T(0)) r_J += (double)fdiv_fast(U0 * U0 + U1 * U1 + U2 * U2, T(2) * V);
       }
     }
     // neighbours' bbar: x+1 by shuffle, y+1 through shared memory

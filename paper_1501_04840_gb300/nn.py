@@ -36,6 +36,7 @@ def lib():
         "ot_nn_to_bf16": [ll, vp, vp, vp],
         "ot_nn_make_input": [i, i, i, i, i, vp, vp, vp, vp, vp],
         "ot_nn_path_channels": [i, i, i, i, i, vp, vp, vp, vp, vp, i, vp],
+        "ot_nn_dual_channels": [i, i, i, i, i, vp, vp, i, i, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -116,7 +117,7 @@ def add_slice(x: Slice, y: Slice, stream=None):
 
 
 def mse(out, cv: int, target, g, loss, stream=None):
-    """out: fp32 [M][os]; target fp32 [M][cv]; g bf16 [M][gs]; loss fp32 [1] (accumulated)."""
+    """out: fp32 [M][os]; target bf16 [M][cv]; g bf16 [M][gs]; loss fp32 [1] (accumulated)."""
     M = target.numel() // cv
     _check(lib().ot_nn_mse(M, cv, _p(out), out.shape[-1], _p(target), _p(g), g.shape[-1], _p(loss), _s(stream)))
 
@@ -137,3 +138,8 @@ def make_input(N, P, Y, X, f0, f1, out, scale=None, stream=None):
 def path_channels(N, Y, X, P, to_channels: bool, packed, ch, f0=None, f1=None, scale=None, stream=None):
     _check(lib().ot_nn_path_channels(N, Y, X, P, int(to_channels), _p(scale), _p(f0), _p(f1), _p(packed), _p(ch),
                                      ch.shape[-1], _s(stream)))
+
+
+def dual_channels(N, Y, X, P, to_channels: bool, packed, ch, co: int, stream=None):
+    _check(lib().ot_nn_dual_channels(N, Y, X, P, int(to_channels), _p(packed), _p(ch), ch.shape[-1], co,
+                                     _s(stream)))

@@ -1,12 +1,13 @@
 """Learned warm start for Algorithm 1.
 
 A 3D U-Net over (t, y, x) maps the boundary densities (f0, f1) of an RGB
-pair to an initial path x0 = (m_x, m_y, m_c, f) on the P-step staggered grid;
-ot_solve_warm then starts Algorithm 1 from it (its first step projects x0 onto
-the continuity constraint, and the dual starts from the fixed-point dual
-grad J(K x0 + (0, f_b^+)) / sigma).  The network predicts f as a deviation
-from the linear interpolation (1 - t) f0 + t f1.  The plain cold start remains
-the fallback when the warm start's first residual is worse than a cold start's.
+pair to an initial path x0 = (m_x, m_y, m_c, f) on the P-step staggered grid
+and an initial dual b0 (the scaled dual of Algorithm 1 at the cells);
+ot_solve_warm then starts Algorithm 1 from them (its first step projects
+x0 - tau sigma K^T b0 onto the continuity constraint).  The network predicts f
+as a deviation from the linear interpolation (1 - t) f0 + t f1.  The plain
+cold start remains the fallback when the warm start's first residual is worse
+than a cold start's.
 
 Every numerical step runs in libdynot.so (convolutions on the tensor cores with
 bf16 operands and fp32 accumulation, pooling, losses, AdamW, the solver);
@@ -36,9 +37,12 @@ from .binding import Plan, rgb_grid
 from .synth import rgb_pair
 
 WIDTHS = (16, 32, 48, 64)
+# weights trained by `python -m paper_1501_04840_gb300.warmstart` (2000 pairs at 128x128x3, P = 32, 6000 steps)
+DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_rgb128x128x3x32.npz")
 CIN = 16    # input channels: f0 (3), f1 (3), interpolation (3), half time (1), zero padding
-COUT = 16   # output channels: the 12 path channels (m_x, m_y, m_c, f deviation; 3 colours each) + 4 unused
-CV = 12
+COUT = 32   # output channels: 12 path channels (m_x, m_y, m_c, f deviation; 3 colours each),
+CV = 24     # then 12 dual channels (b_mx, b_my, b_mc, b_f), then 8 unused
+DUAL0 = 12
 
 
 @contextlib.contextmanager
@@ -247,7 +251,7 @@ class UNet:
             K.rotate_weights(ci, co, self._w(name), self._wr(name), stream=stream)
 
     def backward(self, B: _Buffers, target: torch.Tensor, stream=None):
-        """MSE of the 12 path channels against target [N][P][Y][X][12]; loss accumulates in B.loss."""
+        """MSE of the CV output channels against the bf16 target [N][P][Y][X][CV]; loss accumulates in B.loss."""
         W, w = self.widths, K.whole
         self.rotate(stream)
         K.mse(B.out, CV, target, B.g_out, B.loss, stream=stream)
@@ -272,13 +276,15 @@ class UNet:
         self.step += 1
         K.adamw(self.p32, self.g32, self.m, self.v, self.pb, lr, b1, b2, eps, wd, self.step, stream=stream)
 
-    # ---- inference: the packed initial path (solver units) of N pairs
-    def predict(self, f0: torch.Tensor, f1: torch.Tensor, P: int, init: torch.Tensor, stream=None):
+    # ---- inference: the packed initial path (solver units) and packed dual of N pairs
+    def predict(self, f0: torch.Tensor, f1: torch.Tensor, P: int, init: torch.Tensor, dual=None, stream=None):
         N, _, Y, X = f0.shape
         B = self.buffers(N, P, Y, X, False)
         K.make_input(N, P, Y, X, f0, f1, B.inp, stream=stream)
         self.forward(B, stream)
         K.path_channels(N, Y, X, P, False, init, B.out, f0=f0, f1=f1, stream=stream)
+        if dual is not None:
+            K.dual_channels(N, Y, X, P, False, dual, B.out, DUAL0, stream=stream)
         return init
 
     def save(self, path: str, **meta):
@@ -300,7 +306,7 @@ class UNet:
 class PairSet:
     f0: torch.Tensor       # [n][3][Y][X] solver units (device)
     f1: torch.Tensor
-    target: Optional[torch.Tensor]   # [n][P][Y][X][12] fp32 path channels (device) or None
+    target: Optional[torch.Tensor]   # [n][P][Y][X][CV] bf16 path and dual channels (device) or None
     seeds: List[int]
     iterations: List[int]
 
@@ -316,25 +322,29 @@ def make_pairs(seeds, side: int, nblobs: int, device="cuda") -> Tuple[torch.Tens
 
 
 def _solve_targets(seeds, side: int, P: int, nblobs: int, batch: int = 16, tol: float = 1e-5,
-                  max_iters: int = 6000, device="cuda", log=None) -> PairSet:
-    """Solve every pair with the cold-started GPU solver and keep the path as 12 channels."""
+                   max_iters: int = 6000, device="cuda", log=None) -> PairSet:
+    """Solve every pair with the cold-started GPU solver; keep its path and dual as CV bf16 channels."""
     f0, f1 = make_pairs(seeds, side, nblobs, device)
     n = len(seeds)
-    target = torch.empty((n, P, side, side, CV), dtype=torch.float32, device=device)
+    target = torch.empty((n, P, side, side, CV), dtype=torch.bfloat16, device=device)
+    tmp = torch.empty((min(batch, n), P, side, side, CV), dtype=torch.float32, device=device)
     iters = []
     stream = torch.cuda.current_stream()
-    plans = {}
-    xbuf = {}
+    plans, xbuf = {}, {}
     for i0 in range(0, n, batch):
         nb = min(batch, n - i0)
         if nb not in plans:
             plans[nb] = Plan(rgb_grid(side, side, P), batch=nb, stream=stream.cuda_stream)
-            xbuf[nb] = torch.empty(plans[nb].path_size, dtype=torch.float32, device=device)
-        plan, x = plans[nb], xbuf[nb]
+            xbuf[nb] = (torch.empty(plans[nb].path_size, dtype=torch.float32, device=device),
+                        torch.empty(plans[nb].dual_size, dtype=torch.float32, device=device))
+        plan, (x, b) = plans[nb], xbuf[nb]
         st = plan.solve(f0[i0:i0 + nb], f1[i0:i0 + nb], max_iters, tol)
         plan.x_into(x)
-        K.path_channels(nb, side, side, P, True, x, target[i0:i0 + nb], f0=f0[i0:i0 + nb], f1=f1[i0:i0 + nb],
-                        stream=stream)
+        plan.dual_into(b)
+        t = tmp[:nb]
+        K.path_channels(nb, side, side, P, True, x, t, f0=f0[i0:i0 + nb], f1=f1[i0:i0 + nb], stream=stream)
+        K.dual_channels(nb, side, side, P, True, b, t, DUAL0, stream=stream)
+        K.to_bf16(t, target[i0:i0 + nb], stream=stream)
         iters += [st.iterations] * nb
         if log:
             log("targets %d/%d: %d iterations, residual %.2e" % (i0 + nb, n, st.iterations, st.residual))
@@ -391,7 +401,8 @@ def _cold_first_residual(seeds, side, P, nblobs, check_every=10, device="cuda") 
     return r
 
 
-VARIANTS = (("nodual", False, 0.0), ("dual", True, 0.0), ("dual_s0.3", True, 0.3))
+# (name, dual source, dual_support): "net" = the network's dual, "formula" = the fixed-point dual, "zero"
+VARIANTS = (("net", "net", 0.0), ("zero", "zero", 0.0), ("formula", "formula", 0.3))
 
 
 def _evaluate(net: UNet, seeds, side: int, P: int, nblobs: int, tol: float = 1e-4, max_iters: int = 10000,
@@ -403,12 +414,13 @@ def _evaluate(net: UNet, seeds, side: int, P: int, nblobs: int, tol: float = 1e-
     stream = torch.cuda.current_stream()
     plan = Plan(rgb_grid(side, side, P), batch=1, stream=stream.cuda_stream)
     init = torch.empty(plan.path_size, dtype=torch.float32, device=device)
+    dual = torch.empty(plan.dual_size, dtype=torch.float32, device=device)
     f_run = torch.empty((P - 1, 3, side, side), dtype=torch.float32, device=device)
     f_ref = torch.empty_like(f_run)
     rows = []
     # warm up the kernels, graphs and the network buffers once
     f0, f1 = make_pairs([seeds[0]], side, nblobs, device)
-    net.predict(f0, f1, P, init, stream)
+    net.predict(f0, f1, P, init, dual, stream)
     plan.solve(f0, f1, 2 * check_every, 0.0, check_every=check_every)
     plan.solve_warm(f0, f1, init, 2 * check_every, 0.0, check_every=check_every)
     torch.cuda.synchronize()
@@ -427,14 +439,15 @@ def _evaluate(net: UNet, seeds, side: int, P: int, nblobs: int, tol: float = 1e-
         torch.cuda.synchronize()
         row = dict(seed=s, ref_iters=ref.iterations, ref_residual=ref.residual, cold_iters=cold.iterations,
                    cold_ms=(time.perf_counter() - t0) * 1e3, cold_converged=cold.converged, cold_err=err())
-        for name, dual, support in variants:
+        for name, src, support in variants:
             t0 = time.perf_counter()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            net.predict(f0, f1, P, init, stream)
+            net.predict(f0, f1, P, init, dual if src == "net" else None, stream)
             ev1.record(stream)
-            w = plan.solve_warm(f0, f1, init, max_iters, tol, dual_init=dual, dual_support=support,
-                                fallback_residual=fallback, check_every=check_every)
+            w = plan.solve_warm(f0, f1, init, max_iters, tol, dual_init=src == "formula", dual_support=support,
+                                fallback_residual=fallback, check_every=check_every,
+                                init_dual=dual if src == "net" else None)
             torch.cuda.synchronize()
             row.update({name + "_iters": w.iterations, name + "_ms": (time.perf_counter() - t0) * 1e3,
                         name + "_infer_ms": ev0.elapsed_time(ev1), name + "_used_cold": w.used_cold,
@@ -454,8 +467,8 @@ def _evaluate(net: UNet, seeds, side: int, P: int, nblobs: int, tol: float = 1e-
     out = {"pairs": len(rows), "tol": tol, "ref_tol": ref_tol,
            "cold": {"iters": stat("cold_iters"), "ms": stat("cold_ms"), "err": stat("cold_err"),
                     "all_converged": bool(all(r["cold_converged"] for r in rows))}}
-    for n, dual, support in variants:
-        out[n] = {"dual_init": dual, "dual_support": support, "iters": stat(n + "_iters"), "ms": stat(n + "_ms"),
+    for n, src, support in variants:
+        out[n] = {"dual": src, "dual_support": support, "iters": stat(n + "_iters"), "ms": stat(n + "_ms"),
                   "infer_ms": stat(n + "_infer_ms"), "err": stat(n + "_err"),
                   "fallbacks": int(sum(r[n + "_used_cold"] for r in rows)),
                   "all_converged": bool(all(r[n + "_converged"] for r in rows))}

@@ -148,12 +148,12 @@ def test_mse_and_adamw(K):
     import torch
     rng = np.random.default_rng(17)
     out = torch.from_numpy(rng.standard_normal((300, 16)).astype(np.float32)).cuda()
-    tgt = torch.from_numpy(rng.standard_normal((300, 12)).astype(np.float32)).cuda()
+    tgt = torch.from_numpy(rng.standard_normal((300, 12)).astype(np.float32)).to(torch.bfloat16).cuda()
     g = torch.empty((300, 16), dtype=torch.bfloat16, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     K.mse(out, 12, tgt, g, loss)
     torch.cuda.synchronize()
-    lref, gref = unet.mse(out.cpu().double().numpy()[:, :12], tgt.cpu().double().numpy())
+    lref, gref = unet.mse(out.cpu().double().numpy()[:, :12], _np(tgt))
     assert abs(loss.item() - lref) <= 1e-5 * lref
     gg = _np(g)
     assert np.all(np.abs(gg[:, :12] - gref) <= BF_REL * np.abs(gref) + 1e-12)
@@ -226,4 +226,22 @@ def test_make_input_and_path_channels(K):
     K.path_channels(N, Y, X, P, True, pk, ch)
     back.zero_()
     K.path_channels(N, Y, X, P, False, back, ch)
+    assert np.array_equal(back.cpu().numpy(), packed)
+
+
+def test_dual_channels(K):
+    """Packed dual [n][k][t][c][y][x] <-> channels co + 3k + c: a permutation, exact both ways."""
+    import torch
+    N, P, Y, X = 2, 3, 5, 4
+    rng = np.random.default_rng(19)
+    packed = rng.standard_normal(N * 4 * P * 3 * Y * X).astype(np.float32)
+    ch = torch.full((N, P, Y, X, 32), -3.0, device="cuda")
+    pk = torch.from_numpy(packed).cuda()
+    K.dual_channels(N, Y, X, P, True, pk, ch, 12)
+    c = ch.cpu().numpy()
+    ref = packed.reshape(N, 4, P, 3, Y, X).transpose(0, 2, 4, 5, 1, 3).reshape(N, P, Y, X, 12)
+    assert np.array_equal(c[..., 12:24], ref)
+    assert np.all(c[..., :12] == -3.0) and np.all(c[..., 24:] == -3.0)
+    back = torch.zeros_like(pk)
+    K.dual_channels(N, Y, X, P, False, back, ch, 12)
     assert np.array_equal(back.cpu().numpy(), packed)

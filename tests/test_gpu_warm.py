@@ -56,6 +56,27 @@ def test_warm_start_matches_oracle(ot, dual, support):
     assert abs(stats.residual - infos[-1].residual) <= 1e-2 * infos[-1].residual + 1e-6
 
 
+def test_warm_start_with_given_dual_matches_oracle(ot):
+    """x0 and b0 = bbar0 from an unfinished oracle run, passed through init_path / init_dual."""
+    from _helpers import pack_dual
+    plan, g = _plan(ot)
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(32, 32, 8, 3)
+    f0d, f1d = f0.astype(np.float64), f1.astype(np.float64)
+    st0, _, scale = o.solve(g, f0d, f1d, 60, SIG, TAU)
+    init = pack_path(g, [a * scale for a in st0.m], st0.f * scale).astype(np.float32)
+    b0 = pack_dual(g, st0.bm, st0.bf).astype(np.float32)
+    stats = plan.solve_warm(f32(f0), f32(f1), init, 40, init_dual=b0, dual_init=True)
+    path = plan.path()
+    start = o.State([a.copy() for a in st0.m], st0.f.copy(), [a.copy() for a in st0.bm], st0.bf.copy(),
+                    [a.copy() for a in st0.bm], st0.bf.copy())
+    st, infos, _ = o.solve(g, f0d, f1d, 40, SIG, TAU, state=start)
+    assert rel(path["f"][0], st.f * scale) <= 1e-3
+    for k in range(3):
+        assert rel(path["m"][k][0], st.m[k] * scale) <= 1e-3
+    assert abs(stats.residual - infos[-1].residual) <= 1e-2 * infos[-1].residual + 1e-6
+
+
 def test_warm_without_dual_equals_init_path(ot):
     """ot_solve_warm with dual_init = 0 is ot_solve with init_path (same launches, same bits)."""
     plan, g = _plan(ot)
@@ -127,7 +148,8 @@ def test_unet_gradients_match_oracle(ot):
     f1 = torch.from_numpy(np.stack(f1s)).cuda()
     B = net.buffers(N, P, Y, X, True)
     K.make_input(N, P, Y, X, f0, f1, B.inp)
-    target = torch.from_numpy(np.random.default_rng(5).standard_normal((N, P, Y, X, 12)).astype(np.float32)).cuda()
+    target = torch.from_numpy(np.random.default_rng(5).standard_normal((N, P, Y, X, W.CV)).astype(np.float32))
+    target = target.to(torch.bfloat16).cuda()
     net.forward(B)
     net.g32.zero_()
     B.loss.zero_()
@@ -135,10 +157,30 @@ def test_unet_gradients_match_oracle(ot):
     torch.cuda.synchronize()
     inp = B.inp.cpu().double().numpy()
     loss, out, grads = unet.unet_forward_backward(net.params_numpy(), widths, inp, target.cpu().double().numpy(),
-                                                  12, rnd=unet.round_bf16)
+                                                  W.CV, rnd=unet.round_bf16)
     assert abs(B.loss.item() - loss) <= 1e-3 * loss
     assert rel(B.out.cpu().double().numpy(), out) <= 5e-3
     got = net.grads_numpy()
     for name in grads:
         assert rel(got[name][0], grads[name][0]) <= 5e-3, name
         assert rel(got[name][1], grads[name][1]) <= 5e-3, name
+
+
+def test_trained_network_beats_cold_start(ot):
+    """The packaged U-Net (trained on 2000 solver-generated pairs at 128x128x3, P = 32) against the
+    cold start on held-out pairs: fewer iterations and less wall time (inference included) to residual
+    1e-4, and the same accuracy against a solve to 1e-6."""
+    import os
+    from paper_1501_04840_gb300 import warmstart as W
+    if not os.path.exists(W.DEFAULT_WEIGHTS):
+        pytest.skip("no trained weights in the package")
+    net, meta = W.UNet.load(W.DEFAULT_WEIGHTS)
+    ev = W.evaluate(net, list(range(1_000_000, 1_000_006)), 128, 32, 16, variants=(("net", "net", 0.0),))
+    cold, warm = ev["cold"], ev["net"]
+    print("cold %.1f it %.1f ms err %.3f | warm %.1f it %.1f ms err %.3f" % (
+        cold["iters"]["mean"], cold["ms"]["mean"], cold["err"]["mean"], warm["iters"]["mean"], warm["ms"]["mean"],
+        warm["err"]["mean"]))
+    assert cold["all_converged"] and warm["all_converged"]
+    assert warm["iters"]["mean"] <= 0.92 * cold["iters"]["mean"]
+    assert warm["ms"]["mean"] < cold["ms"]["mean"]
+    assert warm["err"]["mean"] <= cold["err"]["mean"] + 0.01
