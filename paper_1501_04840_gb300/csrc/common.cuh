@@ -14,6 +14,43 @@
 
 namespace dynot {
 
+// Asynchronous global -> shared copies (cp.async): the loads of a whole tile are in flight at
+// once and need no registers; cp_async_wait_all() waits for this thread's copies (a
+// __syncthreads() must follow before other threads read them).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8, "element copies of 4 or 8 bytes");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy nrows rows of len elements from src (row stride src_ld) to shared dst (row stride dst_ld),
+// in 16-byte pieces when every row start is 16-byte aligned, element by element otherwise.
+template <typename T>
+__device__ __forceinline__ void async_rows(T* dst, int dst_ld, const T* src, long long src_ld, int nrows, int len) {
+  constexpr int V = 16 / (int)sizeof(T);
+  const bool vec = len % V == 0 && dst_ld % V == 0 && src_ld % V == 0 && ((uintptr_t)src & 15) == 0 &&
+                   ((uintptr_t)dst & 15) == 0;
+  if (vec) {
+    const int per = len / V;
+    for (int i = threadIdx.x; i < nrows * per; i += blockDim.x) {
+      const int r = i / per, k = i - r * per;
+      cp_async16(dst + (size_t)r * dst_ld + k * V, src + r * src_ld + k * V);
+    }
+  } else {
+    for (int i = threadIdx.x; i < nrows * len; i += blockDim.x) {
+      const int r = i / len, k = i - r * len;
+      cp_async_small<sizeof(T)>(dst + (size_t)r * dst_ld + k, src + r * src_ld + k);
+    }
+  }
+}
+
+
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
 template <typename T> struct vec2;

@@ -26,6 +26,8 @@ constexpr int kW = DYNOT_YC_W;   // x-strip width of the y/colour pass
 inline int pmax_for(int P) { return P <= 16 ? 16 : (P <= 32 ? 32 : 64); }
 inline bool fft_len(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
 inline int fft_n1(int n) { return n == 64 ? 8 : (n == 128 ? 8 : 16); }
+// threads per block of the y/colour pass (matches pick_kb)
+inline int yc_threads(int n2) { return fft_len(n2) ? 12 * fft_n1(n2) : 256; }
 
 inline size_t rnd16(size_t b) { return (b + 15) & ~size_t(15); }
 
@@ -68,11 +70,11 @@ KC<T> pick_kc(int n, int pm) {
 template <typename T>
 KB<T> pick_kb(int n) {
   switch (n) {
-    case 64: return k_solve_yc<T, 8, 8, kW>;
-    case 128: return k_solve_yc<T, 8, 16, kW>;
-    case 256: return k_solve_yc<T, 16, 16, kW>;
-    case 512: return k_solve_yc<T, 16, 32, kW>;
-    default: return k_solve_yc<T, 0, 0, kW>;
+    case 64: return k_solve_yc<T, 8, 8, kW, 12 * 8>;
+    case 128: return k_solve_yc<T, 8, 16, kW, 12 * 8>;
+    case 256: return k_solve_yc<T, 16, 16, kW, 12 * 16>;
+    case 512: return k_solve_yc<T, 16, 32, kW, 12 * 16>;
+    default: return k_solve_yc<T, 0, 0, kW, 256>;
   }
 }
 template <typename T> using KD = void (*)(Geo<T>, Arrays<T>, int, double*);
@@ -396,7 +398,7 @@ struct Plan final : PlanBase {
       yc.Qc = base + o_Q; yc.lamc = base + o_lc; yc.lamcd = (const double*)(base + o_lcd);
       yc.lam_fp64 = thr;
       scrA = fft_len(n1) ? (kThreadsXt / fft_n1(n1)) * n1 : 4 * n1;
-      scrB = fft_len(n2) ? (kThreadsXt / fft_n1(n2)) * n2 : 4 * n2;
+      scrB = fft_len(n2) ? (yc_threads(n2) / fft_n1(n2)) * n2 : 4 * n2;
       ka = pick_ka<T>(n1, pmax);
       kc = pick_kc<T>(n1, pmax);
       kb = pick_kb<T>(n2);
@@ -454,7 +456,7 @@ struct Plan final : PlanBase {
       if (evs) cudaEventRecord(evs[0], st);
       ka<<<dim3(n2, C, B), kThreadsXt, smA, st>>>(g, aptr(p), f0n, f1n, hat, xt, scrA);
       if (evs) cudaEventRecord(evs[1], st);
-      kb<<<dim3((n1 + kW - 1) / kW, P, B), kThreadsXt, smB, st>>>(g, hat, yc, scrB);
+      kb<<<dim3((n1 + kW - 1) / kW, P, B), yc_threads(n2), smB, st>>>(g, hat, yc, scrB);
       if (evs) cudaEventRecord(evs[2], st);
       kc<<<dim3(n2, C, B), kThreadsXt, smA, st>>>(g, hat, phi, xt, scrA);
       if (evs) cudaEventRecord(evs[3], st);

@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
     const T* pxm = px + (xm - x);   // dereferenced only when the face exists
     const T* pym = py + dy;
     const T* pcm = pc + dc;
-#pragma unroll 4
+#pragma unroll 8
     for (int t = 0; t < P; ++t) {
       const size_t o = (size_t)t * S;
       T r = g.s1 * (px[o] - (xm >= 0 ? pxm[o] : T(0)));
@@ -422,6 +422,8 @@ __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const 
   const int n1 = g.n1, P = g.P;
   XtSmem<T> s;
   xt_layout<T>(&s, smraw, P, n1, PMAX, scr_elems, N1 == 0);
+  // the (t, x) plane of this (y, c), all rows in flight at once
+  async_rows<T>(s.tile, n1, phihat + cidx(g, b, 0, 0, y, c), (long long)g.S, P, n1);
   if (N1) load_tables<T>(s.tw, s.hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
   else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) s.cos4[j] = ((const T*)tb.cos4)[j];
   const bool tfft = t_by_fft<PMAX, N1>(P);
@@ -434,8 +436,7 @@ __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const 
   } else {
     for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_i)[j];
   }
-  for (int t = 0; t < P; ++t)
-    for (int x = threadIdx.x; x < n1; x += blockDim.x) s.tile[t * n1 + x] = phihat[cidx(g, b, t, x, y, c)];
+  cp_async_wait_all();
   __syncthreads();
   if constexpr (PMAX <= 32 && N1 > 0) {
     if (tfft) dct_cols_fft<T, PMAX, true, N1 * N2>(s.tile, n1, (const c2<T>*)s.Mt, (const c2<T>*)s.Mt + P);
@@ -506,8 +507,10 @@ struct YcTables {
   double lam_fp64;     // eigenvalues below this are divided in FP64
 };
 
-template <typename T, int M1, int M2, int W>
-__global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ hat, YcTables tb, int scr_elems) {
+// NT threads per block: 12 row pairs of length M1 * M2 per FFT chunk (NT = 12 M1) fill every
+// thread for the 3 x 8 = 24 rows of an RGB strip; the dense path uses 256.
+template <typename T, int M1, int M2, int W, int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restrict__ hat, YcTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int x0 = blockIdx.x * W, kt = blockIdx.y, b = blockIdx.z;
   const int n1 = g.n1, n2 = g.n2, C = g.C;
@@ -519,6 +522,27 @@ __global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ h
   T* Qs = tabs;                      // [4][4], zero outside C x C
   T* lcs = tabs + kMaxC * kMaxC;     // [4]
   T* l1s = lcs + kMaxC;              // [W]
+  // load [c][y][w] (zero beyond the last column so pairs stay well defined); the rows (c, y) of the
+  // strip are n1 apart in hat, W wide in the tile: whole-strip asynchronous copies when aligned
+  const size_t plane = ((size_t)b * g.P + kt) * g.S + x0;
+  constexpr int V = 16 / (int)sizeof(T);
+  if (w_act == W && W % V == 0 && n1 % V == 0 && x0 % V == 0 && cst % V == 0 && ((uintptr_t)hat & 15) == 0) {
+    constexpr int PER = W / V;
+    for (int i = threadIdx.x; i < C * n2 * PER; i += blockDim.x) {
+      const int r = i / PER, k = i - r * PER;   // r = c * n2 + y
+      const int c = r / n2, yy = r - c * n2;
+      cp_async16(tile + c * cst + yy * W + k * V, hat + plane + (size_t)r * n1 + k * V);
+    }
+  } else {
+    for (int c = 0; c < C; ++c) {
+      const T* src = hat + plane + (size_t)c * n1 * n2;
+      T* dst = tile + c * cst;
+      for (int j = threadIdx.x; j < n2 * W; j += blockDim.x) {
+        const int w = j % W, y = j / W;
+        dst[j] = (w < w_act) ? src[(size_t)y * n1 + w] : T(0);
+      }
+    }
+  }
   if (M1) load_tables<T>(tw, hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n2);
   else for (int j = threadIdx.x; j < 4 * n2; j += blockDim.x) cos4[j] = ((const T*)tb.cos4)[j];
   for (int j = threadIdx.x; j < n2; j += blockDim.x) l2[j] = ((const T*)tb.lam2)[j];
@@ -528,21 +552,12 @@ __global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ h
   }
   if (threadIdx.x < kMaxC) lcs[threadIdx.x] = threadIdx.x < C ? ((const T*)tb.lamc)[threadIdx.x] : T(0);
   if (threadIdx.x < W) l1s[threadIdx.x] = threadIdx.x < w_act ? ((const T*)tb.lam1)[x0 + threadIdx.x] : T(0);
-  // load [c][y][w] (zero beyond the last column so pairs stay well defined)
-  const size_t plane = ((size_t)b * g.P + kt) * g.S + x0;
-  for (int c = 0; c < C; ++c) {
-    const T* src = hat + plane + (size_t)c * n1 * n2;
-    T* dst = tile + c * cst;
-    for (int j = threadIdx.x; j < n2 * W; j += blockDim.x) {
-      const int w = j % W, y = j / W;
-      dst[j] = (w < w_act) ? src[(size_t)y * n1 + w] : T(0);
-    }
-  }
+  cp_async_wait_all();
   __syncthreads();
   Rows<T, W, W> rows{tile, cst, 1};
   const int nrows = C * W;
   if constexpr (M1 > 0) {
-    DctPow2<T, M1, M2, true, 256>::forward(rows, nrows, scr, tw, hw);
+    DctPow2<T, M1, M2, true, NT>::forward(rows, nrows, scr, tw, hw);
   } else {
     dct_dense_rows<T, true>(rows, nrows, n2, false, (T*)scr, 2 * scr_elems, cos4);
   }
@@ -592,7 +607,7 @@ __global__ void __launch_bounds__(256, 3) k_solve_yc(Geo<T> g, T* __restrict__ h
   }
   __syncthreads();
   if constexpr (M1 > 0) {
-    DctPow2<T, M1, M2, true, 256>::inverse(rows, nrows, scr, tw, hw);
+    DctPow2<T, M1, M2, true, NT>::inverse(rows, nrows, scr, tw, hw);
   } else {
     dct_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, cos4);
   }
