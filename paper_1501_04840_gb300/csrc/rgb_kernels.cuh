@@ -309,6 +309,10 @@ struct XtTables {
 #ifndef DYNOT_XT_MINB
 #define DYNOT_XT_MINB 2   // blocks per SM the forward x/t kernel is compiled for
 #endif
+#ifndef DYNOT_RHS_UNROLL
+#define DYNOT_RHS_UNROLL 8   // time planes of right-hand-side loads in flight per thread
+#endif
+constexpr int kRhsUnroll = DYNOT_RHS_UNROLL;
 #ifndef DYNOT_XTC_MINB
 #define DYNOT_XTC_MINB 3  // blocks per SM the inverse x/t kernel is compiled for (measured faster at 3)
 #endif
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
     const T* pxm = px + (xm - x);   // dereferenced only when the face exists
     const T* pym = py + dy;
     const T* pcm = pc + dc;
-#pragma unroll 8
+#pragma unroll kRhsUnroll
     for (int t = 0; t < P; ++t) {
       const size_t o = (size_t)t * S;
       T r = g.s1 * (px[o] - (xm >= 0 ? pxm[o] : T(0)));
