@@ -651,11 +651,12 @@ constexpr int kTX = 32, kTY = 8;
 // 0: |b+ - b|^2, 1: |K x + (0, f_b^+)|^2, 2: J(u, v), 3 + t: mass of the time slice t.
 constexpr int kPart = 68;
 
-template <typename T, int C, bool CHECK, bool WRITE_X>
-__global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<T> g, Arrays<T> A, int TC,
-                                                                double* __restrict__ part) {
-  __shared__ T sbb[2][kTY][kTX][C];   // bbar_y exchange, double-buffered by plane parity
-  __shared__ double smass[64];
+// The body of the tiled update.  INTERIOR: every thread of the block has both x and y neighbours
+// inside the grid, so the boundary tests fold away (about three quarters of the blocks at 256^2).
+template <typename T, int C, bool CHECK, bool WRITE_X, bool INTERIOR>
+__device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<T>& A, int TC,
+                                                  double* __restrict__ part, T (&sbb)[2][kTY][kTX][C],
+                                                  double (&smass)[64]) {
   const int lane = threadIdx.x, row = threadIdx.y;
   const int x = blockIdx.x * (kTX - 1) + lane;
   const int y = blockIdx.y * (kTY - 1) + row;
@@ -664,12 +665,13 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
   const int t0 = (blockIdx.z % nch) * TC;
   const int tend = min(t0 + TC, g.P);           // planes [t0, tend) are written
   const int tlast = min(tend, g.P - 1);          // planes [t0, tlast] are computed
-  const bool vx = x < g.n1, vy = y < g.n2;
+  const bool vx = INTERIOR || x < g.n1, vy = INTERIOR || y < g.n2;
   const bool live = vx && vy;
   const int xs = vx ? x : g.n1 - 1, ys = vy ? y : g.n2 - 1;   // clamped for safe loads
-  const bool out = live && (lane < kTX - 1 || x == g.n1 - 1) && (row < kTY - 1 || y == g.n2 - 1);
-  const bool hasR = xs < g.n1 - 1, hasL = xs > 0;
-  const bool hasU = ys < g.n2 - 1, hasD = ys > 0;
+  const bool out = live && (lane < kTX - 1 || (!INTERIOR && x == g.n1 - 1)) &&
+                   (row < kTY - 1 || (!INTERIOR && y == g.n2 - 1));
+  const bool hasR = INTERIOR || xs < g.n1 - 1, hasL = INTERIOR || xs > 0;
+  const bool hasU = INTERIOR || ys < g.n2 - 1, hasD = INTERIOR || ys > 0;
   // 32-bit offsets from per-thread column bases (problem sizes stay below 2^31 cells)
   const int S = g.S, sy = g.n1, sc = g.n1 * g.n2;
   const size_t col = (size_t)b * g.P * S + xs + (size_t)sy * ys;
@@ -867,6 +869,18 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
     for (int t = tid; t < 64; t += kTX * kTY) pp[3 + t] = (t >= t0 && t < tend && t < g.P - 1) ? smass[t] : 0.0;
   }
 }
+
+template <typename T, int C, bool CHECK, bool WRITE_X>
+__global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<T> g, Arrays<T> A, int TC,
+                                                                double* __restrict__ part) {
+  __shared__ T sbb[2][kTY][kTX][C];   // bbar_y exchange, double-buffered by plane parity
+  __shared__ double smass[64];
+  const int x0 = blockIdx.x * (kTX - 1), y0 = blockIdx.y * (kTY - 1);
+  const bool interior = x0 >= 1 && x0 + kTX < g.n1 && y0 >= 1 && y0 + kTY < g.n2;
+  if (interior) update_tiled_body<T, C, CHECK, WRITE_X, true>(g, A, TC, part, sbb, smass);
+  else update_tiled_body<T, C, CHECK, WRITE_X, false>(g, A, TC, part, sbb, smass);
+}
+
 
 // Sum the per-block partials of each problem (one block per problem) into acc and mass.
 static __global__ void k_reduce_check(const double* __restrict__ part, int nblk, int P, double* __restrict__ acc,
