@@ -61,42 +61,76 @@ __global__ void __launch_bounds__(256) k_hue_fwd(Geo<T> g, CPtr4<T> ap, const T*
   }
   __syncthreads();
   for (int slot = threadIdx.x; slot < n; slot += blockDim.x) {
-    // four interleaved partial sums: shorter rounding chains and independent FMAs
+    // four interleaved partial sums: shorter rounding chains and independent FMAs.  The basis
+    // index (i j) mod n of the cos / sin slots advances by 4 j per step instead of a modulo per term.
     T acc[4] = {0, 0, 0, 0};
     int i = 0;
-    for (; i + 3 < n; i += 4) {
+    if (slot == 0 || ((n & 1) == 0 && slot == n - 1)) {
+      // the constant slot and, for even n, the alternating Nyquist slot
+      const bool alt = slot != 0;
+      for (; i + 3 < n; i += 4) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fma(row[i + q], hue_basis<T>(cs, n, slot, i + q), acc[q]);
+        for (int q = 0; q < 4; ++q) acc[q] = fma(row[i + q], (alt && ((i + q) & 1)) ? T(-1) : T(1), acc[q]);
+      }
+    } else {
+      const bool use_cos = slot & 1;
+      const int j = (slot + 1) >> 1;
+      int idx[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) idx[q] = (int)(((long long)q * j) % n);
+      const int step = (int)((4LL * j) % n);
+      for (; i + 3 < n; i += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const c2<T> w = cs[idx[q]];
+          acc[q] = fma(row[i + q], use_cos ? w.x : w.y, acc[q]);
+          idx[q] += step;
+          if (idx[q] >= n) idx[q] -= n;
+        }
+      }
     }
     for (; i < n; ++i) acc[0] = fma(row[i], hue_basis<T>(cs, n, slot, i), acc[0]);
     hat[(size_t)(b * P + t) * n + slot] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   }
 }
 
+// Shared memory of k_hue_t: the two DCT matrices with padded rows, and one column per slot of the
+// input and of the divided spectrum.
 template <typename T, int PMAX>
-__global__ void __launch_bounds__(128) k_hue_t(Geo<T> g, T* __restrict__ hat, HueTables tb) {
+__host__ __device__ constexpr size_t hue_t_smem() {
+  return sizeof(T) * (2 * (size_t)PMAX * (PMAX + 1) + 2 * (size_t)(256 / PMAX) * PMAX);
+}
+template <typename T>
+__host__ __device__ inline size_t hue_t_smem_for(int pmax) {
+  return pmax == 16 ? hue_t_smem<T, 16>() : (pmax == 32 ? hue_t_smem<T, 32>() : hue_t_smem<T, 64>());
+}
+
+// 256 threads = 256 / PMAX slot columns x PMAX time indices: thread (slot, k) forms the k-th DCT
+// coefficient of its column and divides it, then (after a barrier) the k-th time sample of the inverse.
+template <typename T, int PMAX>
+__global__ void __launch_bounds__(256) k_hue_t(Geo<T> g, T* __restrict__ hat, HueTables tb) {
   extern __shared__ __align__(16) char smraw[];
+  constexpr int SL = 256 / PMAX, LD = PMAX + 1;
   const int P = g.P, n = g.n1, b = blockIdx.y;
-  T* Mf = (T*)smraw;
-  T* Mi = Mf + PMAX * PMAX;
+  T* Mf = (T*)smraw;            // [k][t], row stride LD
+  T* Mi = Mf + PMAX * LD;       // [t][k]
+  T* v = Mi + PMAX * LD;        // [SL][PMAX] input columns
+  T* w = v + SL * PMAX;         // [SL][PMAX] divided spectra
   for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) {
-    Mf[j] = ((const T*)tb.Mt_f)[j];
-    Mi[j] = ((const T*)tb.Mt_i)[j];
+    const int r = j / PMAX, c = j - r * PMAX;
+    Mf[r * LD + c] = ((const T*)tb.Mt_f)[j];
+    Mi[r * LD + c] = ((const T*)tb.Mt_i)[j];
   }
+  const int sl = threadIdx.x / PMAX, k = threadIdx.x - sl * PMAX;
+  const int slot = blockIdx.x * SL + sl;
+  const bool act = slot < n && k < P;
+  v[sl * PMAX + k] = act ? hat[(size_t)(b * P + k) * n + slot] : T(0);
   __syncthreads();
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= n) return;
-  T v[PMAX], w[PMAX];
-#pragma unroll
-  for (int t = 0; t < PMAX; ++t) v[t] = t < P ? hat[(size_t)(b * P + t) * n + slot] : T(0);
-  const T ls = ((const T*)tb.lam)[slot];
-#pragma unroll
-  for (int k = 0; k < PMAX; ++k) {
-    if (k >= P) { w[k] = T(0); continue; }
-    T acc = 0;
-#pragma unroll
-    for (int t = 0; t < PMAX; ++t) acc = fma(Mf[k * PMAX + t], v[t], acc);
-    const T lam = ls + ((const T*)tb.lamt)[k];
+  T acc = 0;
+  if (act) {
+#pragma unroll 16
+    for (int t = 0; t < PMAX; ++t) acc = fma(Mf[k * LD + t], v[sl * PMAX + t], acc);
+    const T lam = ((const T*)tb.lam)[slot] + ((const T*)tb.lamt)[k];
     if (!(lam > T(0))) {
       acc = T(0);
     } else if ((double)lam < tb.lam_fp64) {
@@ -104,13 +138,14 @@ __global__ void __launch_bounds__(128) k_hue_t(Geo<T> g, T* __restrict__ hat, Hu
     } else {
       acc = acc / lam;
     }
-    w[k] = acc;
   }
-  for (int t = 0; t < P; ++t) {
-    T acc = 0;
-#pragma unroll
-    for (int k = 0; k < PMAX; ++k) acc = fma(Mi[t * PMAX + k], w[k], acc);
-    hat[(size_t)(b * P + t) * n + slot] = acc;
+  w[sl * PMAX + k] = act ? acc : T(0);
+  __syncthreads();
+  if (act) {
+    T y = 0;
+#pragma unroll 16
+    for (int kk = 0; kk < PMAX; ++kk) y = fma(Mi[k * LD + kk], w[sl * PMAX + kk], y);
+    hat[(size_t)(b * P + k) * n + slot] = y;
   }
 }
 
@@ -131,9 +166,20 @@ __global__ void __launch_bounds__(256) k_hue_inv(Geo<T> g, const T* __restrict__
     T acc[4] = {0, 0, 0, 0};
     const int last = (n & 1) ? n : n - 1;
     int slot = 1;
+    // slots s, s+1 (cos, sin of frequency j) and s+2, s+3 (frequency j+1) for odd s: the basis
+    // indices i j and i (j+1) mod n advance by 2 i per step of 4 slots
+    int ia = i % n, ib = (int)((2LL * i) % n);
+    const int step = (int)((2LL * i) % n);
     for (; slot + 3 < last; slot += 4) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fma(row[slot + q], hue_basis<T>(cs, n, slot + q, i), acc[q]);
+      const c2<T> wa = cs[ia], wb = cs[ib];
+      acc[0] = fma(row[slot], wa.x, acc[0]);
+      acc[1] = fma(row[slot + 1], wa.y, acc[1]);
+      acc[2] = fma(row[slot + 2], wb.x, acc[2]);
+      acc[3] = fma(row[slot + 3], wb.y, acc[3]);
+      ia += step;
+      if (ia >= n) ia -= n;
+      ib += step;
+      if (ib >= n) ib -= n;
     }
     for (; slot < last; ++slot) acc[0] = fma(row[slot], hue_basis<T>(cs, n, slot, i), acc[0]);
     T sum = T(2) * ((acc[0] + acc[1]) + (acc[2] + acc[3])) + row[0];

@@ -421,7 +421,7 @@ struct Plan final : PlanBase {
       ht.lam_fp64 = thr;
       kh = pick_kh<T>(pmax);
       smH = rnd16(sizeof(T) * n1) + rnd16(sizeof(c2<T>) * n1);
-      smHt = 2 * sizeof(T) * (size_t)pmax * pmax;
+      smHt = hue_t_smem_for<T>(pmax);
       int maxsm = 0;
       CUDA_OK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
       if ((int)smH > maxsm || (int)smHt > maxsm)
@@ -464,7 +464,7 @@ struct Plan final : PlanBase {
       if (evs) cudaEventRecord(evs[0], st);
       k_hue_fwd<T><<<dim3(P, B), 256, smH, st>>>(g, aptr(p), f0n, f1n, hat, ht);
       if (evs) cudaEventRecord(evs[1], st);
-      kh<<<dim3((n1 + 127) / 128, B), 128, smHt, st>>>(g, hat, ht);
+      kh<<<dim3((n1 + 256 / pmax - 1) / (256 / pmax), B), 256, smHt, st>>>(g, hat, ht);
       if (evs) cudaEventRecord(evs[2], st);
       k_hue_inv<T><<<dim3(P, B), 256, smH, st>>>(g, hat, phi, ht);
       if (evs) cudaEventRecord(evs[3], st);
