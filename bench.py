@@ -256,6 +256,22 @@ def hue_leg(ot, synth, dev, bins: int = 360, Ph: int = 64, batch: int = 64):
     return out
 
 
+def bc_leg(ot, synth, dev, f0, f1, iters: int = 200):
+    """Other boundary conditions on the bench's 256x256x3x32 pair (section 2: kappa per axis): Neumann colour,
+    and periodic x, y and colour.  Per-iteration device time of `iters` iterations after a warm-up."""
+    import torch
+    out = {}
+    for name, bc in (("neumann_colour", (1, 1, 1)), ("periodic_xyc", (0, 0, 0))):
+        g = ot.grid((N1, N2, 3), bc, P)
+        plan = ot.Plan(g)
+        plan.solve(f0, f1, 20, check_every=20)
+        st = plan.solve(f0, f1, iters, check_every=iters)
+        out[name] = {"iteration_ms": st.elapsed_ms / iters,
+                     "cell_iterations_per_s": CELLS / (st.elapsed_ms / iters / 1e3)}
+        plan.close()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, local, world = dist_env()
@@ -326,6 +342,7 @@ def run_ours(args):
         h2d = 2 * f0.nbytes
         d2h = pin["f"].numel() * 4 + sum(m.numel() * 4 for m in pin["m"])
         hue = hue_leg(ot, synth, dev) if rank == 0 else None
+        bcs = bc_leg(ot, synth, dev, d0, d1) if rank == 0 else None
 
     if rank != 0:
         if world > 1:
@@ -361,6 +378,7 @@ def run_ours(args):
         "e2e": {"value": world * CELLS * iters / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "hue": hue,
+        "other_bc": bcs,
         "gpu_launches": args.steps * (2 + 4 * iters),
         "clocks": clk,
         "final_residual": last.residual if last else None,

@@ -14,7 +14,9 @@
  *   - RGB images: n = {n1, n2, 3}, bc = {NEUMANN, NEUMANN, PERIODIC} (section 1,
  *     Remark 2: the 4D Poisson problem with periodic colour);
  *   - hue histograms: ndim = 1, n = {bins}, bc = {PERIODIC} (section 5);
- *   - grey images / 1D signals: ndim = 2 or 1 with Neumann axes (section 1).
+ *   - grey images / 1D signals: ndim = 2 or 1 with Neumann axes (section 1);
+ *   - any axis of a 2- or 3-axis grid may be periodic (kappa = 0 in section 2):
+ *     periodic x and y axes use the real Fourier basis instead of the DCT.
  *
  * Array conventions (all float32, C order, slowest index first):
  *   densities f0, f1 : [c][y][x]               (S = n1*n2*C values per problem)

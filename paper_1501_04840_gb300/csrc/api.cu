@@ -90,8 +90,6 @@ ot_status validate(const ot_grid* gi, int batch, ot_grid& g) {
   if (g.precision < 0 || g.precision > 2) return seterr(OT_EINVAL, "precision invalid");
   const bool hue = g.ndim == 1 && g.bc[0] == OT_BC_PERIODIC;
   if (!hue) {
-    if (g.ndim >= 1 && g.bc[0] == OT_BC_PERIODIC) return seterr(OT_EUNSUPPORTED, "periodic x axis needs ndim == 1");
-    if (g.ndim >= 2 && g.bc[1] == OT_BC_PERIODIC) return seterr(OT_EUNSUPPORTED, "periodic y axis is not implemented");
     if (g.n[2] > dynot::kMaxC) return seterr(OT_EUNSUPPORTED, "colour axis longer than %d", kMaxC);
     if (g.n[0] < 2) return seterr(OT_EUNSUPPORTED, "n[0] must be >= 2");
     if (g.n[0] > 4096 || g.n[1] > 4096) return seterr(OT_EUNSUPPORTED, "axes longer than 4096");

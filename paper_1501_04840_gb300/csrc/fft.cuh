@@ -280,6 +280,67 @@ struct DctPow2 {
   }
 };
 
+// Dense real DFT of arbitrary length along rows, for periodic axes: cs[m] = (cos, sin)(2 pi m / N).
+// Forward: slot 0 = sum_n x[n]; slots 2j-1, 2j = sum_n x[n] cos, sin (2 pi n j / N); for even N the
+// last slot = sum_n x[n] (-1)^n.  These real Fourier coefficients diagonalise the periodic Laplacian
+// (eigenvalue 4 sin^2(pi j / N) for both slots of frequency j).  Inverse:
+// x[n] = (1/N) (X[0] + 2 sum_j (X[2j-1] cos + X[2j] sin)(2 pi n j / N) + X[N-1] (-1)^n [even N]).
+template <typename T, bool PFAST, class R>
+__device__ void rdft_dense_rows(const R& rows, int nrows, int N, bool inverse, T* __restrict__ scr, int scr_cap,
+                                const c2<T>* __restrict__ cs) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int CR = max(1, scr_cap / N);
+  const bool even = (N & 1) == 0;
+  const int last = even ? N - 1 : N;   // slots 1 .. last-1 come in (cos, sin) pairs
+  for (int r0 = 0; r0 < nrows; r0 += CR) {
+    const int cr = min(CR, nrows - r0);
+    for (int it = tid; it < cr * N; it += nt) {
+      int r, k;
+      if (PFAST) { k = it / cr; r = it - k * cr; } else { r = it / N; k = it - r * N; }
+      const T* x = rows.row(r0 + r);
+      T acc = 0;
+      if (!inverse) {
+        if (k == 0) {
+          for (int n = 0; n < N; ++n) acc += x[n * R::es];
+        } else if (even && k == N - 1) {
+          for (int n = 0; n < N; ++n) acc += (n & 1) ? -x[n * R::es] : x[n * R::es];
+        } else {
+          const int j = (k + 1) >> 1;
+          const bool use_cos = k & 1;
+          int m = 0;   // n j mod N, stepping n
+          for (int n = 0; n < N; ++n) {
+            const c2<T> w = cs[m];
+            acc += x[n * R::es] * (use_cos ? w.x : w.y);
+            m += j;
+            if (m >= N) m -= N;
+          }
+        }
+      } else {
+        const int n = k;   // output sample; sum over the slots
+        T s2 = 0;
+        int m = 0;         // n j mod N, stepping j
+        for (int slot = 1; slot < last; slot += 2) {
+          m += n;
+          if (m >= N) m -= N;
+          const c2<T> w = cs[m];
+          s2 += x[slot * R::es] * w.x + x[(slot + 1) * R::es] * w.y;
+        }
+        acc = x[0] + T(2) * s2;
+        if (even) acc += (n & 1) ? -x[(N - 1) * R::es] : x[(N - 1) * R::es];
+        acc *= T(1) / T(N);
+      }
+      scr[PFAST ? k * cr + r : r * N + k] = acc;
+    }
+    __syncthreads();
+    for (int it = tid; it < cr * N; it += nt) {
+      int r, k;
+      if (PFAST) { k = it / cr; r = it - k * cr; } else { r = it / N; k = it - r * N; }
+      rows.row(r0 + r)[k * R::es] = scr[PFAST ? k * cr + r : r * N + k];
+    }
+    __syncthreads();
+  }
+}
+
 // Dense DCT of arbitrary length along rows: cos4[m] = cos(pi m / (2N)), m < 4N.
 // scr holds one chunk of rows * N values.  Forward X[k] = sum_n x[n] cos4[k(2n+1) mod 4N];
 // inverse x[n] = (1/N) (X[0] + 2 sum_{k>=1} X[k] cos4[k(2n+1) mod 4N]).

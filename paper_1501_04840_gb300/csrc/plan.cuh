@@ -147,11 +147,14 @@ struct Plan final : PlanBase {
     if (h_mass) cudaFreeHost(h_mass);
   }
 
-  size_t xt_smem() const { return xt_layout<T>(nullptr, nullptr, P, n1, pmax, scrA, !fft_len(n1)); }
+  // the FFT paths cover power-of-two Neumann axes; periodic x / y axes take the dense real DFT
+  bool x_fft() const { return fft_len(n1) && !g.per1; }
+  bool y_fft() const { return fft_len(n2) && !g.per2; }
+  size_t xt_smem() const { return xt_layout<T>(nullptr, nullptr, P, n1, pmax, scrA, !x_fft()); }
   size_t yc_smem() const {
     T *t0, *t1, *t2, *t3;
     c2<T> *c0, *c1, *c3;
-    return yc_layout<T>(nullptr, C, n2, kW, scrB, !fft_len(n2), &t0, &c0, &c1, &c3, &t1, &t2, &t3);
+    return yc_layout<T>(nullptr, C, n2, kW, scrB, !y_fft(), &t0, &c0, &c1, &c3, &t1, &t2, &t3);
   }
 
   ot_status init() override {
@@ -283,6 +286,25 @@ struct Plan final : PlanBase {
       }
       return l;
     };
+    // periodic axis: eigenvalue of each real-Fourier slot (rdft_dense_rows), frequency (slot + 1) / 2
+    auto per_lam = [&](int n, double s) {
+      std::vector<double> l(n);
+      for (int slot = 0; slot < n; ++slot) {
+        const int j = (n % 2 == 0 && slot == n - 1) ? n / 2 : (slot + 1) / 2;
+        const double v = std::sin(kPi * j / n);
+        l[slot] = s * s * 4.0 * v * v;
+      }
+      return l;
+    };
+    // (cos, sin)(2 pi m / n) pairs, padded to the 4 n values of the cosine table they replace
+    auto cs_pad = [&](int n) {
+      std::vector<T> c(4 * n, T(0));
+      for (int m = 0; m < n; ++m) {
+        c[2 * m] = (T)std::cos(2 * kPi * m / n);
+        c[2 * m + 1] = (T)std::sin(2 * kPi * m / n);
+      }
+      return c;
+    };
     auto toT = [&](const std::vector<double>& v) {
       std::vector<T> r(v.size());
       for (size_t i = 0; i < v.size(); ++i) r[i] = (T)v[i];
@@ -321,15 +343,16 @@ struct Plan final : PlanBase {
       twid(n1, tw, hw);
       o_tw1 = put(tw.data(), tw.size() * sizeof(T));
       o_hw1 = put(hw.data(), hw.size() * sizeof(T));
-      std::vector<T> c1 = cos4(n1);
+      std::vector<T> c1 = g.per1 ? cs_pad(n1) : cos4(n1);
       o_c41 = put(c1.data(), c1.size() * sizeof(T));
       twid(n2, tw, hw);
       o_tw2 = put(tw.data(), tw.size() * sizeof(T));
       o_hw2 = put(hw.data(), hw.size() * sizeof(T));
-      std::vector<T> c2v = cos4(n2);
+      std::vector<T> c2v = g.per2 ? cs_pad(n2) : cos4(n2);
       o_c42 = put(c2v.data(), c2v.size() * sizeof(T));
-      std::vector<double> l1 = neu_lam(n1, grid.axis_scale[0]);
-      std::vector<double> l2 = neu_lam(n2, d >= 2 ? grid.axis_scale[1] : 1.0);
+      std::vector<double> l1 = g.per1 ? per_lam(n1, grid.axis_scale[0]) : neu_lam(n1, grid.axis_scale[0]);
+      const double s2y = d >= 2 ? grid.axis_scale[1] : 1.0;
+      std::vector<double> l2 = g.per2 ? per_lam(n2, s2y) : neu_lam(n2, s2y);
       std::vector<T> l1T = toT(l1), l2T = toT(l2);
       o_l1 = put(l1T.data(), n1 * sizeof(T));
       o_l1d = put(l1.data(), n1 * sizeof(double));
@@ -397,11 +420,11 @@ struct Plan final : PlanBase {
       yc.lamtd = (const double*)(base + o_ltd);
       yc.Qc = base + o_Q; yc.lamc = base + o_lc; yc.lamcd = (const double*)(base + o_lcd);
       yc.lam_fp64 = thr;
-      scrA = fft_len(n1) ? (kThreadsXt / fft_n1(n1)) * n1 : 4 * n1;
-      scrB = fft_len(n2) ? (yc_threads(n2) / fft_n1(n2)) * n2 : 4 * n2;
-      ka = pick_ka<T>(n1, pmax);
-      kc = pick_kc<T>(n1, pmax);
-      kb = pick_kb<T>(n2);
+      scrA = x_fft() ? (kThreadsXt / fft_n1(n1)) * n1 : 4 * n1;
+      scrB = y_fft() ? (yc_threads(n2) / fft_n1(n2)) * n2 : 4 * n2;
+      ka = pick_ka<T>(x_fft() ? n1 : 0, pmax);
+      kc = pick_kc<T>(x_fft() ? n1 : 0, pmax);
+      kb = pick_kb<T>(y_fft() ? n2 : 0);
       smA = xt_smem();
       smB = yc_smem();
       int maxsm = 0;
@@ -456,7 +479,7 @@ struct Plan final : PlanBase {
       if (evs) cudaEventRecord(evs[0], st);
       ka<<<dim3(n2, C, B), kThreadsXt, smA, st>>>(g, aptr(p), f0n, f1n, hat, xt, scrA);
       if (evs) cudaEventRecord(evs[1], st);
-      kb<<<dim3((n1 + kW - 1) / kW, P, B), yc_threads(n2), smB, st>>>(g, hat, yc, scrB);
+      kb<<<dim3((n1 + kW - 1) / kW, P, B), yc_threads(y_fft() ? n2 : 0), smB, st>>>(g, hat, yc, scrB);
       if (evs) cudaEventRecord(evs[2], st);
       kc<<<dim3(n2, C, B), kThreadsXt, smA, st>>>(g, hat, phi, xt, scrA);
       if (evs) cudaEventRecord(evs[3], st);

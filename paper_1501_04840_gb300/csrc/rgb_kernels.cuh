@@ -296,7 +296,7 @@ struct XtTables {
   const void* hw;    // c2<T>[n1]
   const void* Mt_f;  // forward t-DCT, [P][PMAX]
   const void* Mt_i;  // inverse t-DCT
-  const void* cos4;  // [4 n1]
+  const void* cos4;  // [4 n1]; for a periodic x axis the (cos, sin)(2 pi m / n1) pairs instead
   const void* twt;   // c2<T>[P]: exp(-2 pi i j / P)   (register t-DCT when P == PMAX <= 32)
   const void* hwt;   // c2<T>[P]: exp(-i pi k / (2P))
 };
@@ -403,7 +403,8 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
   if constexpr (N1 > 0) {
     DctPow2<T, N1, N2, false, 256>::forward(rows, Pr, s.scr, s.tw, s.hw);
   } else {
-    dct_dense_rows<T, false>(rows, P, n1, false, (T*)s.scr, 2 * scr_elems, s.cos4);
+    if (g.per1) rdft_dense_rows<T, false>(rows, P, n1, false, (T*)s.scr, 2 * scr_elems, (const c2<T>*)s.cos4);
+    else dct_dense_rows<T, false>(rows, P, n1, false, (T*)s.scr, 2 * scr_elems, s.cos4);
   }
   // (the FFT path leaves a trailing barrier; the dense path too)
   if constexpr (PMAX <= 32 && N1 > 0) {
@@ -457,7 +458,8 @@ __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const 
   if constexpr (N1 > 0) {
     DctPow2<T, N1, N2, false, 256>::inverse(rows, Pr, s.scr, s.tw, s.hw);
   } else {
-    dct_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, s.cos4);
+    if (g.per1) rdft_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, (const c2<T>*)s.cos4);
+    else dct_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, s.cos4);
   }
   for (int t = 0; t < P; ++t)
     for (int x = threadIdx.x; x < n1; x += blockDim.x) phi[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
@@ -498,7 +500,7 @@ __host__ __device__ __forceinline__ size_t yc_layout(char* sm, int C, int n2, in
 struct YcTables {
   const void* tw;      // c2<T>[n2]
   const void* hw;      // c2<T>[n2]
-  const void* cos4;    // [4 n2]
+  const void* cos4;    // [4 n2]; for a periodic y axis the (cos, sin)(2 pi m / n2) pairs instead
   const void* lam1;    // T[n1]   eigenvalues along x
   const void* lam2;    // T[n2]
   const void* lamt;    // T[P]
@@ -563,7 +565,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restri
   if constexpr (M1 > 0) {
     DctPow2<T, M1, M2, true, NT>::forward(rows, nrows, scr, tw, hw);
   } else {
-    dct_dense_rows<T, true>(rows, nrows, n2, false, (T*)scr, 2 * scr_elems, cos4);
+    if (g.per2) rdft_dense_rows<T, true>(rows, nrows, n2, false, (T*)scr, 2 * scr_elems, (const c2<T>*)cos4);
+    else dct_dense_rows<T, true>(rows, nrows, n2, false, (T*)scr, 2 * scr_elems, cos4);
   }
   // colour eigen-solve: phi_c = sum_j Q[c][j] (sum_c' Q[c'][j] r_c') / lambda(kx, ky, j, kt)
   {
@@ -613,7 +616,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restri
   if constexpr (M1 > 0) {
     DctPow2<T, M1, M2, true, NT>::inverse(rows, nrows, scr, tw, hw);
   } else {
-    dct_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, cos4);
+    if (g.per2) rdft_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, (const c2<T>*)cos4);
+    else dct_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, cos4);
   }
   for (int c = 0; c < C; ++c) {
     T* dst = hat + plane + (size_t)c * n1 * n2;

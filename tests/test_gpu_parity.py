@@ -51,6 +51,10 @@ GRIDS = [
     ((360,), ("periodic",), 64),
     ((101,), ("periodic",), 20),
     ((2, 2, 3), RGB, 2),
+    ((24, 20, 3), ("periodic", "periodic", "periodic"), 8),
+    ((32, 16, 3), ("periodic", "neumann", "periodic"), 6),
+    ((16, 24), ("neumann", "periodic"), 5),
+    ((33, 7), ("periodic", "periodic"), 4),
     ((256, 256, 3), RGB, 32),
 ]
 IDS = ["x".join(map(str, n)) + "_" + "".join(b[0] for b in bc) + "_P%d" % P for n, bc, P in GRIDS]
@@ -194,6 +198,19 @@ def test_full_solve_rgb_32x32x3x16_500_iterations(ot):
     assert stats.mass_drift <= 1e-5
 
 
+def test_full_solve_periodic_xy_24x20x3x8(ot):
+    """A torus image (periodic x, y and colour): 300 iterations against the oracle."""
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(24, 20, 4, 5)
+    bc = ("periodic", "periodic", "periodic")
+    plan, g, stats, path, st, infos, scale = _solve_both(ot, (24, 20, 3), bc, 8, 300, f0, f1)
+    assert rel(path["f"][0], st.f * scale) <= 1e-3
+    for k in range(3):
+        assert rel(path["m"][k][0], st.m[k] * scale) <= 1e-3
+    assert abs(stats.energy - infos[-1].energy * scale) <= 1e-3 * infos[-1].energy * scale
+    assert stats.mass_drift <= 1e-5
+
+
 def test_full_solve_hue_360x64(ot):
     from paper_1501_04840_gb300 import synth
     h0, h1 = synth.hue_pair(360, 0)
@@ -331,3 +348,24 @@ def test_profile_reports_every_kernel(ot):
     ms = plan.profile(4)
     assert set(ms) == {"rhs_fwd_xt", "solve_yc", "inv_xt", "update", "iteration"}
     assert all(v > 0 for v in ms.values())
+
+
+@pytest.mark.parametrize("colour_bc", ["periodic", "neumann"])
+def test_fig1_red_to_blue_matches_oracle(ot, colour_bc):
+    """Fig. 1's red -> blue Gaussian on the GPU with periodic and with Neumann colour: the path after
+    600 iterations against the oracle, and the green share at t = 1/2 (small for periodic colour,
+    most of the mass for Neumann colour)."""
+    from test_oracle_solve import _fig1_pair
+    n, P = 12, 8
+    f0, f1 = _fig1_pair(n)
+    bc = ("neumann", "neumann", colour_bc)
+    plan, g = make_plan(ot, (n, n, 3), bc, P)
+    plan.solve(f32(f0), f32(f1), 600)
+    path = plan.path()
+    st, _, sc = o.solve(g, f32(f0).astype(np.float64), f32(f1).astype(np.float64), 600, SIG, TAU)
+    assert rel(path["f"][0], st.f * sc) <= 1e-3
+    mid = path["f"][0][P // 2 - 1].astype(np.float64)
+    green = mid[1].sum() / mid.sum()
+    ref = (st.f[P // 2 - 1] * sc)[1].sum() / (st.f[P // 2 - 1] * sc).sum()
+    assert abs(green - ref) <= 1e-3
+    assert (green < 0.15) if colour_bc == "periodic" else (green > 0.5)

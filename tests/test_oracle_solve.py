@@ -171,3 +171,31 @@ def test_warm_state_dual_is_the_converged_dual():
     assert info0.residual > 1e-3
     z = o.warm_state(g, st.m, st.f, g0, g1, SIG, dual=False)
     assert all(not a.any() for a in z.bm + [z.bf] + z.bbm + [z.bbf])
+
+
+def _fig1_pair(n):
+    """A Gaussian that is red at t = 0 and blue at t = 1 (section 1, Fig. 1), on a small floor."""
+    yy, xx = np.mgrid[0:n, 0:n] + 0.5
+    gauss = np.exp(-((xx - n / 2) ** 2 + (yy - n / 2) ** 2) / (2 * 2.0 ** 2))
+
+    def img(ch):
+        f = np.full((3, n, n), 1e-3)
+        f[ch] += gauss
+        return f / f.sum()
+    return img(0), img(2)
+
+
+def test_fig1_red_to_blue_colour_boundary():
+    """Fig. 1: with periodic colour, red reaches blue directly (red and blue are neighbours on the
+    colour circle), so little mass passes through green at t = 1/2; with Neumann colour the path
+    from red to blue runs through green, which then holds most of the mass."""
+    n, P = 12, 8
+    f0, f1 = _fig1_pair(n)
+    frac = {}
+    for bc in ("periodic", "neumann"):
+        g = o.Grid((n, n, 3), ("neumann", "neumann", bc), P)
+        st, _, sc = o.solve(g, f0, f1, 800, SIG, 0.99 / SIG)
+        mid = st.f[P // 2 - 1] * sc                      # f at time 1/2
+        frac[bc] = mid.sum(axis=(1, 2)) / mid.sum()
+    assert frac["periodic"][1] < 0.15 and abs(frac["periodic"][0] - frac["periodic"][2]) < 1e-6
+    assert frac["neumann"][1] > 0.5
