@@ -59,7 +59,7 @@ def test_invalid_grids_are_rejected_before_any_device_work(lib):
         with pytest.raises(b.OTError) as ei:
             b.Plan(g)
         assert ei.value.status in (b.OT_EINVAL, b.OT_EUNSUPPORTED)
-    g = b.grid([32, 32], ["neumann", "periodic"], 8)
+    g = b.grid([32, 32, 5], ["neumann", "neumann", "periodic"], 8)   # colour axis longer than the kernels' 4
     with pytest.raises(b.OTError) as ei:
         b.Plan(g)
     assert ei.value.status == b.OT_EUNSUPPORTED
