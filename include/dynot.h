@@ -190,6 +190,14 @@ ot_status ot_project(ot_plan_t p, const float* f0, const float* f1, const float*
 ot_status ot_prox(int count, int ncomp, double sigma, const float* a_m, const float* a_f, float* u, float* v);
 
 /*
+ * The same map with the cubic's root in closed form (Cardano's formula, which
+ * section 3 names as the alternative to Newton's method) instead of Newton
+ * iterations; for comparing the two in FP32.  Same arguments as ot_prox.
+ */
+ot_status ot_prox_cardano(int count, int ncomp, double sigma, const float* a_m, const float* a_f, float* u,
+                          float* v);
+
+/*
  * Measurement: run `iters` iterations with CUDA events around every kernel and
  * return the mean device time per launch in ms: ms[0..3] = the four kernels of
  * an iteration (rhs + forward x/t transform, y/colour solve, inverse x/t

@@ -76,6 +76,7 @@ def load_library() -> ctypes.CDLL:
     lib.ot_iterate.argtypes = [c_void_p, c_int, POINTER(Stats)]
     lib.ot_project.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.ot_prox.argtypes = [c_int, c_int, c_double, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.ot_prox_cardano.argtypes = [c_int, c_int, c_double, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.ot_profile.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_char_p)]
     lib.ot_last_error.argtypes = []
     lib.ot_last_error.restype = c_char_p
@@ -89,7 +90,7 @@ def load_library() -> ctypes.CDLL:
     lib.ot_batch_destroy.argtypes = [c_void_p]
     lib.ot_batch_destroy.restype = None
     for name in ("ot_plan", "ot_solve", "ot_solve_warm", "ot_path", "ot_state_set", "ot_state_get", "ot_iterate", "ot_project",
-                 "ot_prox", "ot_profile", "ot_batch_create", "ot_batch_solve", "ot_batch_path"):
+                 "ot_prox", "ot_prox_cardano", "ot_profile", "ot_batch_create", "ot_batch_solve", "ot_batch_path"):
         getattr(lib, name).restype = c_int
     del fp
     _lib = lib
@@ -348,15 +349,16 @@ class Batch:
         return {"f": f, "m": ms}
 
 
-def prox(a_m, a_f, sigma: float):
-    """Per-cell prox of J on the device: a_m of shape (ncomp, count), a_f (count,)."""
+def prox(a_m, a_f, sigma: float, method: str = "newton"):
+    """Per-cell prox of J on the device: a_m of shape (ncomp, count), a_f (count,); method 'newton' or 'cardano'."""
     lib = load_library()
+    fn = lib.ot_prox if method == "newton" else lib.ot_prox_cardano
     a_m = np.ascontiguousarray(a_m, dtype=np.float32)
     a_f = np.ascontiguousarray(a_f, dtype=np.float32)
     ncomp, count = a_m.shape
     u = np.empty_like(a_m)
     v = np.empty_like(a_f)
-    _check(lib.ot_prox(count, ncomp, sigma, _ptr(a_m), _ptr(a_f), _ptr(u), _ptr(v)))
+    _check(fn(count, ncomp, sigma, _ptr(a_m), _ptr(a_f), _ptr(u), _ptr(v)))
     return u, v
 
 

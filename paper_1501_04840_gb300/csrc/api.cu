@@ -418,7 +418,8 @@ ot_status ot_project(ot_plan_t p, const float* f0, const float* f1, const float*
   return p->impl->project(f0, f1, a, x, phi);
 }
 
-ot_status ot_prox(int count, int ncomp, double sigma, const float* am, const float* af, float* u, float* v) {
+static ot_status prox_impl(bool cardano, int count, int ncomp, double sigma, const float* am, const float* af,
+                           float* u, float* v) {
   if (count < 0 || ncomp < 1 || ncomp > 3 || !(sigma > 0)) return seterr(OT_EINVAL, "bad prox arguments");
   if (count == 0) return OT_OK;
   if (!am || !af || !u || !v) return seterr(OT_EINVAL, "NULL prox buffer");
@@ -432,11 +433,20 @@ ot_status ot_prox(int count, int ncomp, double sigma, const float* am, const flo
   CUDA_OK(cudaMemcpy(dam, am, sizeof(float) * n * ncomp, cudaMemcpyDefault));
   CUDA_OK(cudaMemcpy(daf, af, sizeof(float) * n, cudaMemcpyDefault));
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
-  k_prox_cells<<<blocks, 256>>>(count, ncomp, (float)sigma, dam, daf, du, dv);
+  if (cardano) k_prox_cells<true><<<blocks, 256>>>(count, ncomp, (float)sigma, dam, daf, du, dv);
+  else k_prox_cells<false><<<blocks, 256>>>(count, ncomp, (float)sigma, dam, daf, du, dv);
   CUDA_OK(cudaGetLastError());
   CUDA_OK(cudaMemcpy(u, du, sizeof(float) * n * ncomp, cudaMemcpyDefault));
   CUDA_OK(cudaMemcpy(v, dv, sizeof(float) * n, cudaMemcpyDefault));
   return OT_OK;
+}
+
+ot_status ot_prox(int count, int ncomp, double sigma, const float* am, const float* af, float* u, float* v) {
+  return prox_impl(false, count, ncomp, sigma, am, af, u, v);
+}
+
+ot_status ot_prox_cardano(int count, int ncomp, double sigma, const float* am, const float* af, float* u, float* v) {
+  return prox_impl(true, count, ncomp, sigma, am, af, u, v);
 }
 
 ot_status ot_profile(ot_plan_t p, int iters, double ms[5], const char** names) {

@@ -268,14 +268,16 @@ __global__ void k_convert(long long n, const Ti* __restrict__ in, To* __restrict
     out[i] = (To)in[i];
 }
 
+template <bool CARDANO>
 static __global__ void k_prox_cells(int count, int ncomp, float sigma, const float* __restrict__ am,
-                             const float* __restrict__ af, float* __restrict__ u, float* __restrict__ v) {
+                                    const float* __restrict__ af, float* __restrict__ u, float* __restrict__ v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const float a0 = am[i];
     const float a1 = ncomp > 1 ? am[(size_t)count + i] : 0.f;
     const float a2 = ncomp > 2 ? am[2 * (size_t)count + i] : 0.f;
     float u0, u1, u2, vv;
-    prox_J<float>(a0, a1, a2, af[i], sigma, 1.f / sigma, u0, u1, u2, vv);
+    if (CARDANO) prox_J_cardano<float>(a0, a1, a2, af[i], sigma, 1.f / sigma, u0, u1, u2, vv);
+    else prox_J<float>(a0, a1, a2, af[i], sigma, 1.f / sigma, u0, u1, u2, vv);
     u[i] = u0;
     if (ncomp > 1) u[(size_t)count + i] = u1;
     if (ncomp > 2) u[2 * (size_t)count + i] = u2;

@@ -90,6 +90,54 @@ __device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T inv
   v = z * inv_sigma;
 }
 
+// The same prox with the cubic's root in closed form (Cardano, section 3 "Step 2"; no iteration).
+// In w = 1 + z with c = 1 + e the cubic reads w^3 - c w^2 - d = 0; w = t + c/3 gives the depressed
+// cubic t^3 + p t + q = 0 with p = -c^2/3 and -q/2 = A = c^3/27 + d/2, and its discriminant
+// D = A^2 - c^6/729 = d (c^3/27 + d/4).
+// - D >= 0 (always when c > 0): one real root t = r + c^2/(9 r), r = cbrt(A + sqrt D).  The second
+//   term is cbrt(A - sqrt D) rewritten through (A + sqrt D)(A - sqrt D) = (c^2/9)^3, which avoids
+//   the cancellation of the textbook form.
+// - D < 0 (c < 0, small d): three real roots; the largest is t = 2 m cos(acos(A / m^3) / 3), m = |c|/3.
+template <typename T>
+__device__ __forceinline__ void prox_J_cardano(T am0, T am1, T am2, T af, T sigma, T inv_sigma, T& u0, T& u1, T& u2,
+                                               T& v) {
+  const T s2 = am0 * am0 + am1 * am1 + am2 * am2;
+  const T e = sigma * af;
+  const T d = T(0.5) * sigma * sigma * s2;
+  if (!(e + d > T(0))) {
+    u0 = u1 = u2 = v = T(0);
+    return;
+  }
+  const T c = T(1) + e;
+  const T c3_27 = c * c * c * T(1.0 / 27.0);
+  const T A = c3_27 + T(0.5) * d;
+  const T D = d * (c3_27 + T(0.25) * d);
+  T w;
+  if (D >= T(0)) {
+    const T r = cbrt(A + sqrt(D));
+    w = r + fdiv_fast(c * c * T(1.0 / 9.0), r) + c * T(1.0 / 3.0);
+  } else {
+    const T m = fabs(c) * T(1.0 / 3.0);
+    const T arg = fdiv_fast(A, m * m * m);
+    w = T(2) * m * cos(acos(min(max(arg, T(-1)), T(1))) * T(1.0 / 3.0)) + c * T(1.0 / 3.0);
+  }
+  const T z = max(w - T(1), T(0));
+  const T rr = fdiv_fast(z, T(1) + z);
+  u0 = rr * am0;
+  u1 = rr * am1;
+  u2 = rr * am2;
+  v = z * inv_sigma;
+}
+
+#ifndef DYNOT_PROX_CARDANO
+#define DYNOT_PROX_CARDANO 0   // 1: the update kernels use the closed form instead of Newton
+#endif
+template <typename T>
+__device__ __forceinline__ void prox_cell(T am0, T am1, T am2, T af, T sigma, T inv_sigma, T& u0, T& u1, T& u2, T& v) {
+  if (DYNOT_PROX_CARDANO) prox_J_cardano<T>(am0, am1, am2, af, sigma, inv_sigma, u0, u1, u2, v);
+  else prox_J<T>(am0, am1, am2, af, sigma, inv_sigma, u0, u1, u2, v);
+}
+
 // ---------------------------------------------------------------------------
 // K_D: fused projection correction + prox + dual update + next a
 // ---------------------------------------------------------------------------
@@ -159,7 +207,7 @@ struct CellCtx {
 #pragma unroll
     for (int k = 0; k < 4; ++k) bo[k] = A.b[k][i0];
     const T am0 = kx[0] + bo[0], am1 = kx[1] + bo[1], am2 = kx[2] + bo[2], af = kx[3] + bo[3];
-    prox_J<T>(am0, am1, am2, af, g.sigma, T(1) / g.sigma, U0, U1, U2, V);
+    prox_cell<T>(am0, am1, am2, af, g.sigma, T(1) / g.sigma, U0, U1, U2, V);
     bn[0] = am0 - U0;
     bn[1] = am1 - U1;
     bn[2] = am2 - U2;
@@ -774,7 +822,7 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
       const T k3 = half * (xfp[c] + xr[c][3]);
       const T am0 = k0 + lb[c][0], am1 = k1 + lb[c][1], am2 = k2 + lb[c][2], af = k3 + lb[c][3];
       T U0, U1, U2, V;
-      prox_J<T>(am0, am1, am2, af, g.sigma, isg, U0, U1, U2, V);
+      prox_cell<T>(am0, am1, am2, af, g.sigma, isg, U0, U1, U2, V);
       bn[c][0] = am0 - U0;
       bn[c][1] = am1 - U1;
       bn[c][2] = am2 - U2;

@@ -74,6 +74,27 @@ def test_prox_matches_oracle(ot):
     assert np.all(v[zero] == 0) and np.all(u[:, zero] == 0)
 
 
+def test_prox_cardano_against_newton_and_oracle(ot):
+    """The closed-form prox (Cardano) against the FP64 oracle on the same mix of scales as the Newton
+    test: relative L2 within 1e-5 too, and per-cell errors reported for both methods.  The closed form
+    loses relative accuracy where the root sits just above the edge of the feasible set (small d with
+    c < 0: three real roots, arccos near its end), which Newton's scale-aware stop does not."""
+    rng = np.random.default_rng(1)
+    n = 200_000
+    am = (rng.standard_normal((3, n)) * rng.choice([0.01, 1.0, 30.0], size=n)).astype(np.float32)
+    af = (rng.standard_normal(n) * rng.choice([0.01, 1.0, 30.0], size=n)).astype(np.float32)
+    uo, vo = o.prox_J([am[k].astype(np.float64) for k in range(3)], af.astype(np.float64), SIG)
+    errs = {}
+    for method in ("newton", "cardano"):
+        u, v = ot.prox(am, af, SIG, method=method)
+        errs[method] = (rel(v, vo), rel(u, np.stack(uo)))
+        scale = np.abs(vo) + np.abs(af) + 1e-30
+        errs[method] += (float(np.max(np.abs(v - vo) / scale)),)
+    print("prox errors (rel L2 v, rel L2 u, max |dv| / (|v| + |a_f|)):", errs)
+    assert errs["cardano"][0] <= 1e-5 and errs["cardano"][1] <= 1e-5
+    assert errs["newton"][0] <= 1e-5 and errs["newton"][1] <= 1e-5
+
+
 @pytest.mark.parametrize("n,bc,P", GRIDS, ids=IDS)
 def test_projection_matches_oracle(ot, n, bc, P):
     """Smooth operands: phi to 1e-5; x to the FP32 bound of the A^T phi correction."""
