@@ -313,6 +313,33 @@ ot_status ot_nn_path_channels(int N, int Y, int X, int P, int to_channels, const
 ot_status ot_nn_dual_channels(int N, int Y, int X, int P, int to_channels, float* packed, float* ch, int cs, int co,
                               void* stream);
 
+/*
+ * Hue image pipeline (section 5): two images that differ only in hue are
+ * morphed by transporting the hue histogram with the periodic OT of the
+ * paper (ot_solve on an ot_grid_hue grid) and specifying the source hues to
+ * each intermediate histogram, keeping saturation and value.  All pointers
+ * are DEVICE memory; work is ordered on `stream` (cudaStream_t, NULL = legacy
+ * default stream).
+ *
+ * ot_rgb_to_hsv / ot_hsv_to_rgb: rgb is [3][npix] in [0, 1]; hue in [0, 1)
+ *   (hexcone model), saturation, value.  Asynchronous.
+ * ot_hue_histogram: hist[bins] = fraction of the pixels whose hue lies in
+ *   [b / bins, (b + 1) / bins) (mass 1); 1 <= npix < 2^24.  Asynchronous.
+ * ot_hue_specify: h_out = the hues h re-assigned so that their histogram is
+ *   exactly `target` (bins values; negative entries count as 0 and the rest is
+ *   renormalised to mass 1; integer counts by largest remainders).  The paper cites its circular specification method without
+ *   printing it; the reading implemented: pixels ranked by (hue, index), rank
+ *   r gets target rank (r - s) mod npix, where the cyclic shift s has the least
+ *   squared circular distance (searched on the multiples of ceil(npix / 1024),
+ *   then around the best), and target rank q in bin b gets the hue
+ *   (b + (q - C_b + 1/2) / c_b) / bins.  Allocates its workspace and
+ *   synchronises `stream`; 1 <= npix <= 2^26.
+ */
+ot_status ot_rgb_to_hsv(int npix, const float* rgb, float* h, float* s, float* v, void* stream);
+ot_status ot_hsv_to_rgb(int npix, const float* h, const float* s, const float* v, float* rgb, void* stream);
+ot_status ot_hue_histogram(int npix, const float* h, int bins, float* hist, void* stream);
+ot_status ot_hue_specify(int npix, const float* h, int bins, const float* target, float* h_out, void* stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* ot_last_error(void);
 

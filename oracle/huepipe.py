@@ -85,7 +85,8 @@ def hue_histogram(h, bins):
 def exact_counts(target, npix):
     """Integer counts summing to npix from a histogram of mass 1: floors plus the largest remainders
     (ties to the lower bin)."""
-    x = np.asarray(target, np.float64) * npix
+    t = np.maximum(np.asarray(target, np.float64), 0.0)   # negative entries count as empty
+    x = t / t.sum() * npix
     c = np.floor(x).astype(np.int64)
     rem = x - c
     short = npix - int(c.sum())

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdynot.so")
-UNITS = ["api", "plan_f32", "plan_f64", "noalloc", "nn"]
+UNITS = ["api", "plan_f32", "plan_f64", "noalloc", "nn", "huepipe"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC"]
 # extra nvcc flags for tuning experiments (e.g. -DDYNOT_UPD_MINB=2); empty by default

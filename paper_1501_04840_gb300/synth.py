@@ -87,3 +87,31 @@ def mixed_batch(seed: int = 0, n_rgb: int = 16, n_hue: int = 64) -> Tuple[List[d
     for i in range(n_hue):
         hue.append({"n": int(rng.integers(64, 721)), "P": int(rng.integers(16, 65)), "s": 2000 + i})
     return rgb, hue
+
+
+def hue_image_pair(n: int, seed: int = 0, dtype=np.float32) -> Tuple[np.ndarray, np.ndarray]:
+    """Two n x n RGB images ([3][n][n] in [0, 1]) with the same saturation and value that differ only in
+    hue, like the yellow and red flowers of section 5: a flower (a union of Gaussian petals) on a green
+    background.  Every pixel has max channel V and min channel V (1 - S); the third channel sets the hue
+    inside the sector: between red and yellow in the flower (yellow-orange in the first image, red-orange
+    in the second), between green and cyan-green in the background."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:n, 0:n] + 0.5
+    flower = np.zeros((n, n))
+    for _ in range(6):
+        cx, cy = rng.uniform(0.3, 0.7, 2) * n
+        r = rng.uniform(0.06, 0.14) * n
+        flower = np.maximum(flower, np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * r * r)))
+    inside = flower > 0.5
+    V = 0.35 + 0.6 * (0.5 + 0.5 * np.sin(2 * np.pi * (xx / n * rng.uniform(1, 3) + rng.uniform())))
+    S = 0.4 + 0.5 * flower
+    w = np.clip(0.5 + 0.15 * rng.standard_normal((n, n)), 0, 1)       # position inside the sector
+    lo = V * (1 - S)
+    imgs = []
+    for warm in (0.85, 0.12):
+        mid = lo + (V - lo) * np.where(inside, np.clip(warm + 0.1 * (w - 0.5), 0, 1), 0.3 * w)
+        r = np.where(inside, V, lo)
+        g = np.where(inside, mid, V)
+        b = np.where(inside, lo, mid)
+        imgs.append(np.stack([r, g, b]).astype(dtype))
+    return imgs[0], imgs[1]

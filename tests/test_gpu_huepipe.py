@@ -1,0 +1,88 @@
+"""The hue image pipeline of section 5 on the GPU against oracle/huepipe.py."""
+import numpy as np
+import pytest
+
+from oracle import huepipe as hp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_04840_gb300 import _build
+    _build.build()
+    from paper_1501_04840_gb300 import huepipe
+    huepipe.lib()
+    return huepipe
+
+
+def test_hsv_round_trip_matches_oracle(H):
+    import torch
+    rng = np.random.default_rng(0)
+    rgb = rng.random((3, 5000)).astype(np.float32)
+    rgb[:, :8] = np.array([[0, 1, 0, 0, 1, 1, 0.5, 1], [0, 0, 1, 0, 1, 0, 0.5, 1], [0, 0, 0, 1, 0, 1, 0.5, 1]])
+    h, s, v = H.rgb_to_hsv(torch.from_numpy(rgb).cuda())
+    ho, so, vo = hp.rgb_to_hsv(rgb.astype(np.float64))
+    dh = np.abs(h.cpu().numpy() - ho)
+    assert np.all(np.minimum(dh, 1 - dh) <= 1e-6)
+    assert np.abs(s.cpu().numpy() - so).max() <= 1e-6 and np.abs(v.cpu().numpy() - vo).max() == 0
+    back = H.hsv_to_rgb(h, s, v).cpu().numpy()
+    assert np.abs(back - rgb).max() <= 2e-6
+
+
+def test_histogram_and_specification_match_oracle(H):
+    import torch
+    from paper_1501_04840_gb300 import synth
+    rgb0, _ = synth.hue_image_pair(64, 3)
+    h, _, _ = H.rgb_to_hsv(torch.from_numpy(rgb0).cuda())
+    hh = h.cpu().numpy().ravel()
+    bins = 360
+    hist = H.hue_histogram(h, bins).cpu().numpy()
+    np.testing.assert_allclose(hist, hp.hue_histogram(hh, bins), rtol=0, atol=1e-7)
+    rng = np.random.default_rng(4)
+    for target in (rng.random(bins).astype(np.float32), np.roll(hist, 17).astype(np.float32)):
+        target /= target.sum()
+        out = H.specify(h, bins, torch.from_numpy(target).cuda()).cpu().numpy().ravel()
+        ref = hp.specify(hh, bins, target)
+        # same strict order and cut: every pixel gets the same target hue (float rounding of it)
+        assert np.abs(out - ref).max() <= 1e-7
+        assert np.array_equal(np.bincount(hp.hue_bin(out, bins), minlength=bins),
+                              hp.exact_counts(target, hh.size))
+
+
+def test_hue_morph_frames(H):
+    """The whole pipeline on the synthetic flower pair: the transported histograms come from the GPU
+    solver (Algorithm 1 on the hue grid, parity-tested elsewhere); the frames built from them match the
+    oracle's specification of the same histograms, keep saturation and value, start and end on the two
+    images' hue histograms, and move the flower's hue from yellow to red through orange."""
+    import torch
+    from paper_1501_04840_gb300 import synth
+    rgb0, rgb1 = synth.hue_image_pair(64, 1)
+    frames, hists, st = H.hue_morph(rgb0, rgb1, bins=360, P=8, iters=4000, tol=1e-5)
+    frames = frames.cpu().numpy()
+    hists = hists.cpu().numpy()
+    assert st.mass_drift <= 1e-5
+    h0, s0, v0 = hp.rgb_to_hsv(rgb0.reshape(3, -1).astype(np.float64))
+    # the oracle's specification from the GPU's float32 HSV of the source (the strict order of
+    # nearly equal hues depends on their float rounding)
+    hg, sg, vg = (a.cpu().numpy().ravel() for a in H.rgb_to_hsv(torch.from_numpy(rgb0).cuda()))
+    for k in range(len(frames)):
+        ref = hp.hsv_to_rgb(hp.specify(hg, 360, hists[k]), sg, vg)
+        np.testing.assert_allclose(frames[k].reshape(3, -1), ref, atol=2e-6)
+        hk, sk, vk = hp.rgb_to_hsv(frames[k].reshape(3, -1).astype(np.float64))
+        assert np.abs(vk - v0).max() <= 1e-6 and np.abs(sk - s0).max() <= 1e-5
+    h1, _, _ = hp.rgb_to_hsv(rgb1.reshape(3, -1).astype(np.float64))
+    last, _, _ = hp.rgb_to_hsv(frames[-1].reshape(3, -1).astype(np.float64))
+    assert np.array_equal(np.bincount(hp.hue_bin(last, 360), minlength=360),
+                          np.bincount(hp.hue_bin(h1.astype(np.float32), 360), minlength=360))
+    # the flower pixels' mean hue (on the circle) drifts monotonically from yellow towards red
+    flower = (rgb0.reshape(3, -1).argmax(axis=0) == 0)
+    means = []
+    for k in range(len(frames)):
+        hk, _, _ = hp.rgb_to_hsv(frames[k].reshape(3, -1).astype(np.float64))
+        a = 2 * np.pi * hk[flower]
+        means.append(np.angle(np.mean(np.exp(1j * a))) / (2 * np.pi))
+    assert np.all(np.diff(means) < 1e-3) and means[0] - means[-1] > 0.05
