@@ -14,6 +14,14 @@
 
 namespace dynot {
 
+// Programmatic dependent launch: a kernel launched with the programmatic-serialisation attribute may
+// start while its predecessor in the stream finishes.  pdl_trigger() lets the successor launch once
+// every block of this grid has passed it; pdl_wait() blocks until the predecessor grid has completed
+// and its writes are visible.  Without the attribute both are no-ops.  Every kernel here reads or
+// writes global data only after pdl_wait(); only constant tables are read before it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // Asynchronous global -> shared copies (cp.async): the loads of a whole tile are in flight at
 // once and need no registers; cp_async_wait_all() waits for this thread's copies (a
 // __syncthreads() must follow before other threads read them).

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fft.cuh"
@@ -30,6 +31,28 @@ inline int fft_n1(int n) { return n == 64 ? 8 : (n == 128 ? 8 : 16); }
 inline int yc_threads(int n2) { return fft_len(n2) ? 12 * fft_n1(n2) : 256; }
 
 inline size_t rnd16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Launch with programmatic dependent launch allowed (the kernels wait for their predecessor with
+// griddepcontrol.wait before touching its data; see pdl_wait): the next pass's blocks can be
+// scheduled and load their tables while the previous pass drains.  DYNOT_PDL=0 launches plainly.
+#ifndef DYNOT_PDL
+#define DYNOT_PDL 1
+#endif
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = DYNOT_PDL ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // --------------------------------------------------------------------------
 // kernel selection
@@ -477,11 +500,12 @@ struct Plan final : PlanBase {
   void enqueue_poisson(int p, cudaEvent_t* evs) {
     if (!hue) {
       if (evs) cudaEventRecord(evs[0], st);
-      ka<<<dim3(n2, C, B), kThreadsXt, smA, st>>>(g, aptr(p), f0n, f1n, hat, xt, scrA);
+      launch_pdl(ka, dim3(n2, C, B), dim3(kThreadsXt), smA, st, g, aptr(p), (const T*)f0n, (const T*)f1n, hat, xt,
+                 scrA);
       if (evs) cudaEventRecord(evs[1], st);
-      kb<<<dim3((n1 + kW - 1) / kW, P, B), yc_threads(y_fft() ? n2 : 0), smB, st>>>(g, hat, yc, scrB);
+      launch_pdl(kb, dim3((n1 + kW - 1) / kW, P, B), dim3(yc_threads(y_fft() ? n2 : 0)), smB, st, g, hat, yc, scrB);
       if (evs) cudaEventRecord(evs[2], st);
-      kc<<<dim3(n2, C, B), kThreadsXt, smA, st>>>(g, hat, phi, xt, scrA);
+      launch_pdl(kc, dim3(n2, C, B), dim3(kThreadsXt), smA, st, g, (const T*)hat, phi, xt, scrA);
       if (evs) cudaEventRecord(evs[3], st);
     } else {
       if (evs) cudaEventRecord(evs[0], st);
@@ -511,7 +535,7 @@ struct Plan final : PlanBase {
     const Arrays<T> A = arrays(p, wx);
     if (tiled) {
       const dim3 grd = tiled_grid(tc);
-      pick_kd<T>(C, check, wx)<<<grd, dim3(kTX, kTY), 0, st>>>(g, A, tc, part);
+      launch_pdl(pick_kd<T>(C, check, wx), grd, dim3(kTX, kTY), 0, st, g, A, tc, part);
       if (check) k_reduce_check<<<B, 256, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass);
       return;
     }

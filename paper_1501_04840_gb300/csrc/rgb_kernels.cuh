@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
   } else {
     for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_f)[j];
   }
+  pdl_wait();   // a (previous update) is read from here on
   // divergence of a and the time difference with the boundary densities
   const int ym = y > 0 ? y - 1 : (g.per2 ? g.n2 - 1 : -1);
   const int cm = c > 0 ? c - 1 : (g.perc ? g.C - 1 : -1);
@@ -462,6 +463,7 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
     dct_cols<T, PMAX>(s.tile, n1, n1, P, s.Mt);
   }
   __syncthreads();
+  pdl_trigger();
   for (int t = 0; t < P; ++t)
     for (int x = threadIdx.x; x < n1; x += blockDim.x) rhat[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
 }
@@ -475,8 +477,6 @@ __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const 
   const int n1 = g.n1, P = g.P;
   XtSmem<T> s;
   xt_layout<T>(&s, smraw, P, n1, PMAX, scr_elems, N1 == 0);
-  // the (t, x) plane of this (y, c), all rows in flight at once
-  async_rows<T>(s.tile, n1, phihat + cidx(g, b, 0, 0, y, c), (long long)g.S, P, n1);
   if (N1) load_tables<T>(s.tw, s.hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
   else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) s.cos4[j] = ((const T*)tb.cos4)[j];
   const bool tfft = t_by_fft<PMAX, N1>(P);
@@ -489,6 +489,9 @@ __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const 
   } else {
     for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) s.Mt[j] = ((const T*)tb.Mt_i)[j];
   }
+  pdl_wait();   // the spectral array (y/colour pass) is read from here on
+  // the (t, x) plane of this (y, c), all rows in flight at once
+  async_rows<T>(s.tile, n1, phihat + cidx(g, b, 0, 0, y, c), (long long)g.S, P, n1);
   cp_async_wait_all();
   __syncthreads();
   if constexpr (PMAX <= 32 && N1 > 0) {
@@ -509,6 +512,7 @@ __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const 
     if (g.per1) rdft_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, (const c2<T>*)s.cos4);
     else dct_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, s.cos4);
   }
+  pdl_trigger();
   for (int t = 0; t < P; ++t)
     for (int x = threadIdx.x; x < n1; x += blockDim.x) phi[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
 }
@@ -576,6 +580,16 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restri
   T* Qs = tabs;                      // [4][4], zero outside C x C
   T* lcs = tabs + kMaxC * kMaxC;     // [4]
   T* l1s = lcs + kMaxC;              // [W]
+  if (M1) load_tables<T>(tw, hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n2);
+  else for (int j = threadIdx.x; j < 4 * n2; j += blockDim.x) cos4[j] = ((const T*)tb.cos4)[j];
+  for (int j = threadIdx.x; j < n2; j += blockDim.x) l2[j] = ((const T*)tb.lam2)[j];
+  if (threadIdx.x < kMaxC * kMaxC) {
+    const int c = threadIdx.x / kMaxC, j = threadIdx.x % kMaxC;
+    Qs[threadIdx.x] = (c < C && j < C) ? ((const T*)tb.Qc)[c * C + j] : T(0);
+  }
+  if (threadIdx.x < kMaxC) lcs[threadIdx.x] = threadIdx.x < C ? ((const T*)tb.lamc)[threadIdx.x] : T(0);
+  if (threadIdx.x < W) l1s[threadIdx.x] = threadIdx.x < w_act ? ((const T*)tb.lam1)[x0 + threadIdx.x] : T(0);
+  pdl_wait();   // the spectral array (forward x/t pass) is read from here on
   // load [c][y][w] (zero beyond the last column so pairs stay well defined); the rows (c, y) of the
   // strip are n1 apart in hat, W wide in the tile: whole-strip asynchronous copies when aligned
   const size_t plane = ((size_t)b * g.P + kt) * g.S + x0;
@@ -597,15 +611,6 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restri
       }
     }
   }
-  if (M1) load_tables<T>(tw, hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n2);
-  else for (int j = threadIdx.x; j < 4 * n2; j += blockDim.x) cos4[j] = ((const T*)tb.cos4)[j];
-  for (int j = threadIdx.x; j < n2; j += blockDim.x) l2[j] = ((const T*)tb.lam2)[j];
-  if (threadIdx.x < kMaxC * kMaxC) {
-    const int c = threadIdx.x / kMaxC, j = threadIdx.x % kMaxC;
-    Qs[threadIdx.x] = (c < C && j < C) ? ((const T*)tb.Qc)[c * C + j] : T(0);
-  }
-  if (threadIdx.x < kMaxC) lcs[threadIdx.x] = threadIdx.x < C ? ((const T*)tb.lamc)[threadIdx.x] : T(0);
-  if (threadIdx.x < W) l1s[threadIdx.x] = threadIdx.x < w_act ? ((const T*)tb.lam1)[x0 + threadIdx.x] : T(0);
   cp_async_wait_all();
   __syncthreads();
   Rows<T, W, W> rows{tile, cst, 1};
@@ -667,6 +672,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restri
     if (g.per2) rdft_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, (const c2<T>*)cos4);
     else dct_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, cos4);
   }
+  pdl_trigger();
   for (int c = 0; c < C; ++c) {
     T* dst = hat + plane + (size_t)c * n1 * n2;
     const T* src = tile + c * cst;
@@ -754,6 +760,7 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
     for (int i = threadIdx.x + kTX * threadIdx.y; i < 64; i += kTX * kTY) smass[i] = 0.0;
   }
   double r_db = 0, r_kx = 0, r_J = 0;
+  pdl_wait();   // phi (inverse x/t pass) and the state are read from here on
 
   T phic[C], xfp[C], bbfp[C];
   // state entering plane t0: phi(t0), x_f at the face t0 - 1 (or f0)
@@ -895,6 +902,7 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
       phic[c] = phn[c];
     }
   }
+  pdl_trigger();
   if (CHECK) {
     __shared__ double red[kTY][3];
 #pragma unroll
