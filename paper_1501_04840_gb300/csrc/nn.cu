@@ -16,6 +16,7 @@
 
 #include <cstdint>
 
+#include "common.cuh"
 #include "plan_base.h"
 
 namespace dynot {
@@ -121,6 +122,113 @@ __global__ void __launch_bounds__(128) k_conv3d(Vol v, int Cin, int Cout, const 
         *reinterpret_cast<uint32_t*>((bf16*)y + o) = pack2(__float2bfloat16(u0), __float2bfloat16(u1));
       }
     }
+  }
+}
+
+// The same convolution with the input staged in shared memory.  A block computes 4 rows of 32
+// voxels (one warp per row, two m16 tiles) for 8 * NT output channels.  For each 16-channel slice
+// of the input it stages the zero-padded halo [3][6][34] voxels x 16 channels with cp.async, then
+// runs the 27 taps: the A fragments of a tap are ldmatrix loads from the halo rows shifted by the
+// tap (no per-tap address or bounds arithmetic), the B fragments come from the weights as above.
+// Halo rows are 32 bytes (16 channels); the two 16-byte halves of voxel v are swapped when
+// (v >> 2) & 1 so that the eight rows of one ldmatrix hit distinct banks.  Needs the input's
+// channel stride and offset to be multiples of 8 (16-byte pieces).
+constexpr int kCT_TY = 4, kCT_TX = 32, kCT_HY = kCT_TY + 2, kCT_HX = kCT_TX + 2;
+constexpr int kCT_HV = 3 * kCT_HY * kCT_HX;   // halo voxels
+
+__device__ __forceinline__ int ct_half_off(int v, int half) { return v * 32 + ((half ^ ((v >> 2) & 1)) << 4); }
+
+template <int NT>
+__global__ void __launch_bounds__(128) k_conv3d_tiled(Vol v, int Cin, int Cout, const bf16* __restrict__ x, int xs,
+                                                      int xo, const bf16* __restrict__ w,
+                                                      const float* __restrict__ bias, void* __restrict__ y, int ys,
+                                                      int yo, int relu, int out_f32) {
+  __shared__ __align__(128) unsigned char halo[kCT_HV * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int nxb = (v.X + kCT_TX - 1) / kCT_TX;
+  const int x0 = (blockIdx.x % nxb) * kCT_TX, y0 = (blockIdx.x / nxb) * kCT_TY;
+  const int t = blockIdx.y % v.T, n = blockIdx.y / v.T;
+  const int co0 = blockIdx.z * 8 * NT;
+  float acc[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[mt][j][0] = acc[mt][j][1] = acc[mt][j][2] = acc[mt][j][3] = 0.f;
+  const unsigned hbase = (unsigned)__cvta_generic_to_shared(halo);
+  // ldmatrix row of this lane: matrix (lane >> 3) = (m rows 0-7 | 8-15) x (channels 0-7 | 8-15)
+  const int mrow = ((lane >> 3) & 1) * 8 + (lane & 7), mhalf = lane >> 4;
+  for (int ci0 = 0; ci0 < Cin; ci0 += 16) {
+    // stage the halo of this channel slice (zeros outside the volume)
+    for (int i = threadIdx.x; i < kCT_HV * 2; i += blockDim.x) {
+      const int hv = i >> 1, half = i & 1;
+      const int hx = hv % kCT_HX, hy = (hv / kCT_HX) % kCT_HY, ht = hv / (kCT_HX * kCT_HY);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gt = t + ht - 1;
+      unsigned char* dst = halo + ct_half_off(hv, half);
+      if (gx >= 0 && gx < v.X && gy >= 0 && gy < v.Y && gt >= 0 && gt < v.T) {
+        const bf16* src = x + ((((long long)n * v.T + gt) * v.Y + gy) * v.X + gx) * xs + xo + ci0 + half * 8;
+        cp_async16(dst, src);
+      } else {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int tap = 0; tap < 27; ++tap) {
+      const int dt = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;   // offsets + 1 into the halo
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int hv = (dt * kCT_HY + warp + dy) * kCT_HX + mt * 16 + mrow + dx;
+        const unsigned addr = hbase + (unsigned)ct_half_off(hv, mhalf);
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(a[mt][0]), "=r"(a[mt][1]), "=r"(a[mt][2]), "=r"(a[mt][3])
+                     : "r"(addr));
+      }
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int co = co0 + j * 8 + gid;
+        uint32_t b0 = 0u, b1 = 0u;
+        if (co < Cout) {
+          const bf16* wp = w + ((long long)co * 27 + tap) * Cin + ci0 + tig * 2;
+          b0 = ld32(wp);
+          b1 = ld32(wp + 8);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][j], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: bias, ReLU, store (rows gid, gid + 8 of each m16 tile = voxels x0 + 16 mt + gid (+8))
+  const int yy = y0 + warp;
+  if (yy >= v.Y) return;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int co = co0 + j * 8 + tig * 2;
+    if (co >= Cout) continue;
+    const float bb0 = bias ? bias[co] : 0.f, bb1 = bias ? bias[co + 1] : 0.f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int xx = x0 + mt * 16 + gid + r * 8;
+        if (xx >= v.X) continue;
+        float u0 = acc[mt][j][2 * r] + bb0, u1 = acc[mt][j][2 * r + 1] + bb1;
+        if (relu) {
+          u0 = fmaxf(u0, 0.f);
+          u1 = fmaxf(u1, 0.f);
+        }
+        const long long vox = (((long long)n * v.T + t) * v.Y + yy) * v.X + xx;
+        const long long o = vox * ys + yo + co;
+        if (out_f32) {
+          float* yp = (float*)y + o;
+          yp[0] = u0;
+          yp[1] = u1;
+        } else {
+          *reinterpret_cast<uint32_t*>((bf16*)y + o) = pack2(__float2bfloat16(u0), __float2bfloat16(u1));
+        }
+      }
   }
 }
 
@@ -455,6 +563,19 @@ ot_status ot_nn_conv3d(int N, int T, int Y, int X, int Cin, int Cout, const void
   const long long M = (long long)N * T * Y * X;
   const dim3 blk(128);
   cudaStream_t st = (cudaStream_t)stream;
+  if (xs % 8 == 0 && xo % 8 == 0 && ((uintptr_t)x & 15) == 0 && (long long)N * T < 65536) {
+    // shared-memory tiled form (16-byte input pieces)
+    const int nxb = (X + kCT_TX - 1) / kCT_TX, nyb = (Y + kCT_TY - 1) / kCT_TY;
+    if (Cout % 32 == 0) {
+      k_conv3d_tiled<4><<<dim3((unsigned)(nxb * nyb), (unsigned)(N * T), Cout / 32), blk, 0, st>>>(
+          v, Cin, Cout, (const bf16*)x, xs, xo, (const bf16*)w, bias, y, ys, yo, relu, out_f32);
+    } else {
+      k_conv3d_tiled<2><<<dim3((unsigned)(nxb * nyb), (unsigned)(N * T), (Cout + 15) / 16), blk, 0, st>>>(
+          v, Cin, Cout, (const bf16*)x, xs, xo, (const bf16*)w, bias, y, ys, yo, relu, out_f32);
+    }
+    NN_LAUNCH_CHECK();
+    return OT_OK;
+  }
   if (Cout % 32 == 0) {
     k_conv3d<4><<<dim3((unsigned)((M + 63) / 64), Cout / 32), blk, 0, st>>>(
         v, Cin, Cout, (const bf16*)x, xs, xo, (const bf16*)w, bias, y, ys, yo, relu, out_f32);
