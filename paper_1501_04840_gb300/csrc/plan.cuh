@@ -159,11 +159,17 @@ struct Plan final : PlanBase {
   int par = 0;              // buffer holding the current state
   bool have_x = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // [parity][lead]: the check iteration (x written) with its reductions and the copies of the results
+  // to pinned host memory, optionally preceded by one plain iteration
+  cudaGraphExec_t gcheck[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaEvent_t ev[12] = {};
 
   ~Plan() override {
     for (auto& e : gexec)
       if (e) cudaGraphExecDestroy(e);
+    for (auto& row : gcheck)
+      for (auto& e : row)
+        if (e) cudaGraphExecDestroy(e);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     if (h_acc) cudaFreeHost(h_acc);
@@ -627,6 +633,44 @@ struct Plan final : PlanBase {
     return OT_OK;
   }
 
+  // one launch for [plain iteration on p (lead)] + check iteration (x written) + result copies
+  ot_status check_graph_for(int p, bool lead) {
+    if (gcheck[p][lead]) return OT_OK;
+    cudaGraph_t gr = nullptr;
+    CUDA_OK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(acc, 0, sizeof(double) * B * kAcc, st);
+    cudaMemsetAsync(mass, 0, sizeof(double) * (size_t)B * P, st);
+    if (lead) enqueue_iteration(p, false, false);
+    enqueue_iteration(lead ? 1 - p : p, true, true);
+    cudaMemcpyAsync(h_acc, acc, sizeof(double) * B * kAcc, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(h_mass, mass, sizeof(double) * (size_t)B * P, cudaMemcpyDeviceToHost, st);
+    const cudaError_t le = cudaGetLastError();
+    cudaError_t e = cudaStreamEndCapture(st, &gr);
+    if (le != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return seterr(OT_ECUDA, "launch during check-graph capture: %s", cudaGetErrorString(le));
+    }
+    if (e != cudaSuccess) return seterr(OT_ECUDA, "check-graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&gcheck[p][lead], gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return seterr(OT_ECUDA, "check-graph instantiate: %s", cudaGetErrorString(e));
+    return OT_OK;
+  }
+
+  // n iterations, the last one a check (x written), all from graphs; results collected after a sync
+  ot_status run_chunk_with_check(int n, Check& out) {
+    const int plain = n - 1;
+    OT_TRY(run_plain(plain - (plain & 1)));
+    const bool lead = plain & 1;
+    OT_TRY(check_graph_for(par, lead));
+    CUDA_OK(cudaGraphLaunch(gcheck[par][lead], st));
+    if (!lead) par ^= 1;   // with a lead iteration the pair returns to the same buffer
+    have_x = true;
+    CUDA_OK(cudaStreamSynchronize(st));
+    std::vector<ProblemCheck> per;
+    return collect_check(per, out);
+  }
+
   ot_status run_check(bool wx, Check& out) {
     OT_TRY(enqueue_check(wx));
     CUDA_OK(cudaStreamSynchronize(st));
@@ -644,9 +688,8 @@ struct Plan final : PlanBase {
     const int K = check_every > 0 ? check_every : iters;
     while (done < iters) {
       const int chunk = std::min(K, iters - done);
-      OT_TRY(run_plain(chunk - 1));
       const bool last = (done + chunk == iters);
-      OT_TRY(run_check(true, ck));
+      OT_TRY(run_chunk_with_check(chunk, ck));
       const bool first = (done == 0);
       done += chunk;
       if (first && fallback > 0 && ck.residual > fallback) {

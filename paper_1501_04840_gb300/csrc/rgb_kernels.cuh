@@ -759,7 +759,9 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   if (CHECK) {
     for (int i = threadIdx.x + kTX * threadIdx.y; i < 64; i += kTX * kTY) smass[i] = 0.0;
   }
-  double r_db = 0, r_kx = 0, r_J = 0;
+  // residual and energy terms: per-thread partial sums in the working precision (at most 3 P terms),
+  // every sum across threads in FP64
+  T r_db = 0, r_kx = 0, r_J = 0;
   pdl_wait();   // phi (inverse x/t pass) and the state are read from here on
 
   T phic[C], xfp[C], bbfp[C];
@@ -844,9 +846,9 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
           const T db = bn[c][k] - lb[c][k];
           db2 = fma(db, db, db2);
         }
-        r_db += (double)db2;
-        r_kx += (double)(k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3);
-        if (V > T(0)) r_J += (double)fdiv_fast(U0 * U0 + U1 * U1 + U2 * U2, T(2) * V);
+        r_db += db2;
+        r_kx += k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3;
+        if (V > T(0)) r_J += fdiv_fast(U0 * U0 + U1 * U1 + U2 * U2, T(2) * V);
       }
     }
     // neighbours' bbar: x+1 by shuffle, y+1 through shared memory
@@ -884,11 +886,12 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
         }
       }
       if (CHECK && tnext) {
-        double m = 0;
+        T mt = 0;
         if (out) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) m += (double)xr[c][3];
+          for (int c = 0; c < C; ++c) mt += xr[c][3];
         }
+        double m = (double)mt;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
         if (lane == 0) atomicAdd(&smass[t], m);
@@ -905,16 +908,17 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   pdl_trigger();
   if (CHECK) {
     __shared__ double red[kTY][3];
+    double d_db = (double)r_db, d_kx = (double)r_kx, d_J = (double)r_J;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      r_db += __shfl_xor_sync(0xffffffffu, r_db, o);
-      r_kx += __shfl_xor_sync(0xffffffffu, r_kx, o);
-      r_J += __shfl_xor_sync(0xffffffffu, r_J, o);
+      d_db += __shfl_xor_sync(0xffffffffu, d_db, o);
+      d_kx += __shfl_xor_sync(0xffffffffu, d_kx, o);
+      d_J += __shfl_xor_sync(0xffffffffu, d_J, o);
     }
     if (lane == 0) {
-      red[row][0] = r_db;
-      red[row][1] = r_kx;
-      red[row][2] = r_J;
+      red[row][0] = d_db;
+      red[row][1] = d_kx;
+      red[row][2] = d_J;
     }
     __syncthreads();
     const int tid = threadIdx.x + kTX * threadIdx.y;
