@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -295,6 +296,119 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad(Vol v, int Cin, int Cout, 
     const int r = e / 16, c = e % 16;
     const float s = red[0][r][c] + red[1][r][c] + red[2][r][c] + red[3][r][c];
     atomicAdd(&dw[((long long)(co0 + r) * 27 + tap) * Cin + ci0 + c], s);
+  }
+}
+
+// Weight gradient with shared-memory staging.  A block owns one (16 output x 16 input channel) slice
+// and a strided set of 4 x 32 voxel tiles; per tile it stages the input halo (as k_conv3d_tiled) and
+// the 128 voxels x 16 channels of dy, then every warp forms, for its taps (tap = warp + 4 i), the
+// 16 x 16 product dy^T x_shifted over the tile's voxels: A = dy^T and B = shifted x come from
+// ldmatrix.trans on the staged rows.  Each block writes its 27 x 16 x 16 partial sums to `part`;
+// k_wgrad_reduce adds the blocks' partials into dw (no atomics, a fixed summation order).
+constexpr int kWG_TAPS = 7;   // taps per warp (27 over 4 warps)
+
+__global__ void __launch_bounds__(128) k_conv3d_wgrad_tiled(Vol v, int Cin, int Cout, const bf16* __restrict__ x,
+                                                            int xs, int xo, const bf16* __restrict__ dy, int dys,
+                                                            int dyo, float* __restrict__ part, int ntiles) {
+  __shared__ __align__(128) unsigned char halo[kCT_HV * 32];
+  __shared__ __align__(128) unsigned char dyt[kCT_TY * kCT_TX * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int nci = Cin / 16;
+  const int ci0 = (blockIdx.y % nci) * 16, co0 = (blockIdx.y / nci) * 16;
+  const int nxb = (v.X + kCT_TX - 1) / kCT_TX, nyb = (v.Y + kCT_TY - 1) / kCT_TY;
+  float acc[kWG_TAPS][2][4];
+#pragma unroll
+  for (int i = 0; i < kWG_TAPS; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+  const unsigned hbase = (unsigned)__cvta_generic_to_shared(halo);
+  const unsigned dbase = (unsigned)__cvta_generic_to_shared(dyt);
+  // ldmatrix lane roles: matrix (lane >> 3): voxel block ((lane >> 3) >> 1) * 8, channel half (lane >> 3) & 1
+  // for A = dy^T; for B the same split with the channel half selecting the n8 tile
+  const int lrow = lane & 7, lmat = lane >> 3;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int xb = tile % nxb, yb = (tile / nxb) % nyb, nt = tile / (nxb * nyb);
+    const int x0 = xb * kCT_TX, y0 = yb * kCT_TY, t = nt % v.T, n = nt / v.T;
+    for (int i = threadIdx.x; i < kCT_HV * 2; i += blockDim.x) {
+      const int hv = i >> 1, half = i & 1;
+      const int hx = hv % kCT_HX, hy = (hv / kCT_HX) % kCT_HY, ht = hv / (kCT_HX * kCT_HY);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gt = t + ht - 1;
+      unsigned char* dst = halo + ct_half_off(hv, half);
+      if (gx >= 0 && gx < v.X && gy >= 0 && gy < v.Y && gt >= 0 && gt < v.T)
+        cp_async16(dst, x + ((((long long)n * v.T + gt) * v.Y + gy) * v.X + gx) * xs + xo + ci0 + half * 8);
+      else
+        *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int i = threadIdx.x; i < kCT_TY * kCT_TX * 2; i += blockDim.x) {
+      const int tv = i >> 1, half = i & 1;
+      const int gx = x0 + (tv % kCT_TX), gy = y0 + tv / kCT_TX;
+      unsigned char* dst = dyt + ct_half_off(tv, half);
+      if (gx < v.X && gy < v.Y)
+        cp_async16(dst, dy + ((((long long)n * v.T + t) * v.Y + gy) * v.X + gx) * dys + dyo + co0 + half * 8);
+      else
+        *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int ks = 0; ks < kCT_TY * kCT_TX / 16; ++ks) {
+      const int row = ks >> 1, xk = (ks & 1) * 16;   // 16 voxels x0 + xk .. + 15 of tile row `row`
+      // A = dy^T (co x voxel): matrices (voxels 0-7 | 8-15) x (co 0-7 | 8-15), transposed on load
+      uint32_t a0, a1, a2, a3;
+      {
+        const int tv = row * kCT_TX + xk + (lmat >> 1) * 8 + lrow;
+        const unsigned addr = dbase + (unsigned)ct_half_off(tv, lmat & 1);
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
+                     : "r"(addr));
+      }
+#pragma unroll
+      for (int i = 0; i < kWG_TAPS; ++i) {
+        const int tap = warp + 4 * i;
+        if (tap < 27) {
+          const int dt = tap / 9, ddy = (tap / 3) % 3, dx = tap % 3;
+          // B = shifted x (voxel x ci): matrices (voxels 0-7 | 8-15) x (ci 0-7 | 8-15), transposed on load
+          const int hv = (dt * kCT_HY + row + ddy) * kCT_HX + xk + (lmat >> 1) * 8 + lrow + dx;
+          const unsigned addr = hbase + (unsigned)ct_half_off(hv, lmat & 1);
+          uint32_t b00, b01, b10, b11;
+          asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                       : "=r"(b00), "=r"(b10), "=r"(b01), "=r"(b11)
+                       : "r"(addr));
+          mma_bf16(acc[i][0], a0, a1, a2, a3, b00, b01);
+          mma_bf16(acc[i][1], a0, a1, a2, a3, b10, b11);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // partials: part[block][tap][co 16][ci 16]
+  float* pp = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (27 * 256);
+#pragma unroll
+  for (int i = 0; i < kWG_TAPS; ++i) {
+    const int tap = warp + 4 * i;
+    if (tap >= 27) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float* q = pp + tap * 256;
+      const int ci = j * 8 + tig * 2;
+      q[gid * 16 + ci] = acc[i][j][0];
+      q[gid * 16 + ci + 1] = acc[i][j][1];
+      q[(gid + 8) * 16 + ci] = acc[i][j][2];
+      q[(gid + 8) * 16 + ci + 1] = acc[i][j][3];
+    }
+  }
+}
+
+// dw[co][tap][ci] += sum over the blocks of one channel slice of their partials
+__global__ void k_wgrad_reduce(int Cin, int nblk, const float* __restrict__ part, float* __restrict__ dw) {
+  const int slice = blockIdx.y, nci = Cin / 16;
+  const int ci0 = (slice % nci) * 16, co0 = (slice / nci) * 16;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 27 * 256; e += gridDim.x * blockDim.x) {
+    const float* p = part + (size_t)slice * nblk * (27 * 256) + e;
+    float s = 0.f;
+    for (int k = 0; k < nblk; ++k) s += p[(size_t)k * (27 * 256)];
+    const int tap = e / 256, co = (e / 16) % 16, ci = e % 16;
+    dw[((size_t)(co0 + co) * 27 + tap) * Cin + ci0 + ci] += s;
   }
 }
 
@@ -594,9 +708,35 @@ ot_status ot_nn_conv3d_wgrad(int N, int T, int Y, int X, int Cin, int Cout, cons
     return seterr(OT_EINVAL, "conv3d_wgrad: channel slices must fit their tensors");
   const Vol v{N, T, Y, X};
   const long long M = (long long)N * T * Y * X;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (xs % 8 == 0 && xo % 8 == 0 && dys % 8 == 0 && dyo % 8 == 0 && ((uintptr_t)x & 15) == 0 &&
+      ((uintptr_t)dy & 15) == 0) {
+    // shared-memory tiled form: per-block partials, then a fixed-order reduction into dw
+    const int nxb = (X + kCT_TX - 1) / kCT_TX, nyb = (Y + kCT_TY - 1) / kCT_TY;
+    const long long ntiles = (long long)N * T * nyb * nxb;
+    const int nslices = (Cin / 16) * (Cout / 16);
+    const int nblk = (int)std::max<long long>(1, std::min<long long>(ntiles, std::max(1, 4 * 152 / nslices)));
+    if (ntiles < (1LL << 31) && nslices < 65536) {
+      float* part = nullptr;
+      const size_t bytes = sizeof(float) * (size_t)nslices * nblk * 27 * 256;
+      CUDA_OK(cudaMallocAsync((void**)&part, bytes, st));
+      k_conv3d_wgrad_tiled<<<dim3(nblk, nslices), 128, 0, st>>>(v, Cin, Cout, (const bf16*)x, xs, xo,
+                                                                 (const bf16*)dy, dys, dyo, part, (int)ntiles);
+      const cudaError_t e1 = cudaGetLastError();
+      if (e1 == cudaSuccess) k_wgrad_reduce<<<dim3(27, nslices), 256, 0, st>>>(Cin, nblk, part, dw);
+      const cudaError_t e2 = cudaGetLastError();
+      CUDA_OK(cudaFreeAsync(part, st));
+      if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return seterr(OT_ECUDA, "%s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+      if (db) {
+        k_bias_grad<<<dim3(64, Cout), 256, 0, st>>>(M, Cout, (const bf16*)dy, dys, dyo, db);
+        NN_LAUNCH_CHECK();
+      }
+      return OT_OK;
+    }
+  }
   if (M * xs >= (1LL << 31)) return seterr(OT_EINVAL, "conv3d_wgrad: tensor too large for 32-bit offsets");
   const int chunk = 4096;
-  cudaStream_t st = (cudaStream_t)stream;
   k_conv3d_wgrad<<<dim3((unsigned)((M + chunk - 1) / chunk), 27, (Cout / 16) * (Cin / 16)), 128, 0, st>>>(
       v, Cin, Cout, (const bf16*)x, xs, xo, (const bf16*)dy, dys, dyo, dw, chunk);
   NN_LAUNCH_CHECK();
