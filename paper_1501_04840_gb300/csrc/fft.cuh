@@ -122,7 +122,9 @@ struct Rows {
 // in memory), true = row-pair index fastest (rows interleaved, as in the y
 // pass).  Pairs are processed in chunks of CP = NT / N1; the scratch holds
 // CP * N complex values.  Every index divisor is a compile-time constant.
-template <typename T, int N1, int N2, bool PFAST, int NT>
+// PERIODIC = true: the same machinery computes the real Fourier transform of rows of a periodic axis in the
+// slot layout of rdft_dense_rows (natural input order; slots 0, 2j-1, 2j, N-1 from the spectrum).
+template <typename T, int N1, int N2, bool PFAST, int NT, bool PERIODIC = false>
 struct DctPow2 {
   static constexpr int N = N1 * N2;
   static constexpr int CP = NT / N1;
@@ -161,7 +163,7 @@ struct DctPow2 {
 #pragma unroll
           for (int n1 = 0; n1 < N1; ++n1) {
             const int n = N2 * n1 + n2;
-            const int e = (n1 < N1 / 2 ? 2 * n : 2 * N - 1 - 2 * n) * R::es;   // Makhoul order
+            const int e = PERIODIC ? n * R::es : (n1 < N1 / 2 ? 2 * n : 2 * N - 1 - 2 * n) * R::es;   // Makhoul order
             z[n1] = mk2<T>(ra[e], rb[e]);
           }
           dft_reg<T, N1, N, false>(z, tw);
@@ -204,11 +206,27 @@ struct DctPow2 {
           // V_a = (Z_k + conj Z_m)/2 ; V_b = (Z_k - conj Z_m)/(2i)
           const T vax = T(0.5) * (zk.x + zm.x), vay = T(0.5) * (zk.y - zm.y);
           const T vbx = T(0.5) * (zk.y + zm.y), vby = T(0.5) * (zm.x - zk.x);
-          const c2<T> h = hw[k];  // (cos, -sin) of pi k/(2N)
           T* ra = rows.row(2 * (p0 + p));
           T* rb = rows.row(2 * (p0 + p) + 1);
-          ra[k * R::es] = h.x * vax - h.y * vay;
-          rb[k * R::es] = h.x * vbx - h.y * vby;
+          if constexpr (PERIODIC) {
+            // V = sum x exp(-2 pi i n k / N): slot 2k-1 = Re V (cos sum), slot 2k = -Im V (sin sum)
+            if (k == 0) {
+              ra[0] = vax;
+              rb[0] = vbx;
+            } else if (k < N / 2) {
+              ra[(2 * k - 1) * R::es] = vax;
+              ra[(2 * k) * R::es] = -vay;
+              rb[(2 * k - 1) * R::es] = vbx;
+              rb[(2 * k) * R::es] = -vby;
+            } else if (k == N / 2) {
+              ra[(N - 1) * R::es] = vax;
+              rb[(N - 1) * R::es] = vbx;
+            }
+          } else {
+            const c2<T> h = hw[k];  // (cos, -sin) of pi k/(2N)
+            ra[k * R::es] = h.x * vax - h.y * vay;
+            rb[k * R::es] = h.x * vbx - h.y * vby;
+          }
         }
       }
       __syncthreads();
@@ -236,14 +254,28 @@ struct DctPow2 {
 #pragma unroll
           for (int n1 = 0; n1 < N1; ++n1) {
             const int k = N2 * n1 + n2;
-            const T xa = ra[k * R::es], xb = rb[k * R::es];
-            const T xam = k ? ra[(N - k) * R::es] : T(0);
-            const T xbm = k ? rb[(N - k) * R::es] : T(0);
-            const c2<T> h = hw[k];                 // conj(h) = (cos, +sin)
-            // V_a = (h.x - i h.y) (xa - i xam)
-            const T vax = h.x * xa - h.y * xam, vay = -h.x * xam - h.y * xa;
-            const T vbx = h.x * xb - h.y * xbm, vby = -h.x * xbm - h.y * xb;
-            z[n1] = mk2<T>(vax - vby, vay + vbx);  // V_a + i V_b
+            if constexpr (PERIODIC) {
+              // the Hermitian spectrum of each row from its slots: V_k = X[2k-1] - i X[2k], V_{N-k} = conj V_k
+              auto spec = [&](const T* r, T& re, T& im) {
+                if (k == 0) { re = r[0]; im = T(0); }
+                else if (k < N / 2) { re = r[(2 * k - 1) * R::es]; im = -r[(2 * k) * R::es]; }
+                else if (k == N / 2) { re = r[(N - 1) * R::es]; im = T(0); }
+                else { const int kk = N - k; re = r[(2 * kk - 1) * R::es]; im = r[(2 * kk) * R::es]; }
+              };
+              T ax, ay, bx, by;
+              spec(ra, ax, ay);
+              spec(rb, bx, by);
+              z[n1] = mk2<T>(ax - by, ay + bx);    // V_a + i V_b
+            } else {
+              const T xa = ra[k * R::es], xb = rb[k * R::es];
+              const T xam = k ? ra[(N - k) * R::es] : T(0);
+              const T xbm = k ? rb[(N - k) * R::es] : T(0);
+              const c2<T> h = hw[k];                 // conj(h) = (cos, +sin)
+              // V_a = (h.x - i h.y) (xa - i xam)
+              const T vax = h.x * xa - h.y * xam, vay = -h.x * xam - h.y * xa;
+              const T vbx = h.x * xb - h.y * xbm, vby = -h.x * xbm - h.y * xb;
+              z[n1] = mk2<T>(vax - vby, vay + vbx);  // V_a + i V_b
+            }
           }
           dft_reg<T, N1, N, true>(z, tw);
 #pragma unroll
@@ -269,7 +301,7 @@ struct DctPow2 {
 #pragma unroll
           for (int k2 = 0; k2 < N2; ++k2) {
             const int m = k1 + N1 * k2;
-            const int e = (k2 < N2 / 2 ? 2 * m : 2 * N - 1 - 2 * m) * R::es;
+            const int e = PERIODIC ? m * R::es : (k2 < N2 / 2 ? 2 * m : 2 * N - 1 - 2 * m) * R::es;
             ra[e] = y[k2].x * invN;
             rb[e] = y[k2].y * invN;
           }

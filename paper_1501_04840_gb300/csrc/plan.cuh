@@ -102,19 +102,23 @@ KB<T> pick_kb(int n) {
 }
 template <typename T> using KD = void (*)(Geo<T>, Arrays<T>, int, double*);
 
-template <typename T, int C>
+template <typename T, int C, bool PXY>
 KD<T> pick_kd_c(bool check, bool wx) {
-  if (check) return wx ? k_update_tiled<T, C, true, true> : k_update_tiled<T, C, true, false>;
-  return wx ? k_update_tiled<T, C, false, true> : k_update_tiled<T, C, false, false>;
+  if (check) return wx ? k_update_tiled<T, C, true, true, PXY> : k_update_tiled<T, C, true, false, PXY>;
+  return wx ? k_update_tiled<T, C, false, true, PXY> : k_update_tiled<T, C, false, false, PXY>;
+}
+template <typename T, bool PXY>
+KD<T> pick_kd_p(int C, bool check, bool wx) {
+  switch (C) {
+    case 1: return pick_kd_c<T, 1, PXY>(check, wx);
+    case 2: return pick_kd_c<T, 2, PXY>(check, wx);
+    case 3: return pick_kd_c<T, 3, PXY>(check, wx);
+    default: return pick_kd_c<T, 4, PXY>(check, wx);
+  }
 }
 template <typename T>
-KD<T> pick_kd(int C, bool check, bool wx) {
-  switch (C) {
-    case 1: return pick_kd_c<T, 1>(check, wx);
-    case 2: return pick_kd_c<T, 2>(check, wx);
-    case 3: return pick_kd_c<T, 3>(check, wx);
-    default: return pick_kd_c<T, 4>(check, wx);
-  }
+KD<T> pick_kd(int C, bool check, bool wx, bool per_xy) {
+  return per_xy ? pick_kd_p<T, true>(C, check, wx) : pick_kd_p<T, false>(C, check, wx);
 }
 
 template <typename T>
@@ -154,7 +158,7 @@ struct Plan final : PlanBase {
   KC<T> kc = nullptr;
   KB<T> kb = nullptr;
   KH<T> kh = nullptr;
-  bool tiled = false;       // tiled update kernel (Neumann x and y)
+  bool tiled = false;       // tiled update kernel (up to four colour channels)
   int tc = 0;               // time-chunk length of the tiled update (autotuned)
   int par = 0;              // buffer holding the current state
   bool have_x = false;
@@ -176,9 +180,10 @@ struct Plan final : PlanBase {
     if (h_mass) cudaFreeHost(h_mass);
   }
 
-  // the FFT paths cover power-of-two Neumann axes; periodic x / y axes take the dense real DFT
-  bool x_fft() const { return fft_len(n1) && !g.per1; }
-  bool y_fft() const { return fft_len(n2) && !g.per2; }
+  // the FFT paths cover power-of-two axes (DCT for Neumann, real Fourier slots for periodic ones);
+  // other lengths take the dense transforms
+  bool x_fft() const { return fft_len(n1); }
+  bool y_fft() const { return fft_len(n2); }
   size_t xt_smem() const { return xt_layout<T>(nullptr, nullptr, P, n1, pmax, scrA, !x_fft()); }
   size_t yc_smem() const {
     T *t0, *t1, *t2, *t3;
@@ -235,7 +240,7 @@ struct Plan final : PlanBase {
     CUDA_OK(cudaMallocHost(&h_acc, sizeof(double) * B * kAcc));
     CUDA_OK(cudaMallocHost(&h_mass, sizeof(double) * (size_t)B * P));
     out_scale.assign(B, 1.0);
-    tiled = !hue && !g.per1 && !g.per2 && C <= 4;
+    tiled = !hue && C <= 4;
     if (tiled) OT_TRY(tune_update());
     return OT_OK;
   }
@@ -531,8 +536,9 @@ struct Plan final : PlanBase {
   }
 
   dim3 tiled_grid(int tchunk) const {
-    const int nbx = std::max(1, (n1 - 1 + kTX - 2) / (kTX - 1));
-    const int nby = std::max(1, (n2 - 1 + kTY - 2) / (kTY - 1));
+    // a Neumann axis leaves its last cell to the halo lane; a periodic one needs a block past it
+    const int nbx = std::max(1, ((g.per1 ? n1 : n1 - 1) + kTX - 2) / (kTX - 1));
+    const int nby = std::max(1, ((g.per2 ? n2 : n2 - 1) + kTY - 2) / (kTY - 1));
     const int nch = (P + tchunk - 1) / tchunk;
     return dim3(nbx, nby, B * nch);
   }
@@ -541,7 +547,7 @@ struct Plan final : PlanBase {
     const Arrays<T> A = arrays(p, wx);
     if (tiled) {
       const dim3 grd = tiled_grid(tc);
-      launch_pdl(pick_kd<T>(C, check, wx), grd, dim3(kTX, kTY), 0, st, g, A, tc, part);
+      launch_pdl(pick_kd<T>(C, check, wx, g.per1 || g.per2), grd, dim3(kTX, kTY), 0, st, g, A, tc, part);
       if (check) k_reduce_check<<<B, 256, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass);
       return;
     }

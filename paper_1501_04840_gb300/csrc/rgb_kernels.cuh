@@ -450,7 +450,8 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
   __syncthreads();
   Rows<T, 1, 1> rows{s.tile, n1, 0};
   if constexpr (N1 > 0) {
-    DctPow2<T, N1, N2, false, 256>::forward(rows, Pr, s.scr, s.tw, s.hw);
+    if (g.per1) DctPow2<T, N1, N2, false, 256, true>::forward(rows, Pr, s.scr, s.tw, s.hw);
+    else DctPow2<T, N1, N2, false, 256>::forward(rows, Pr, s.scr, s.tw, s.hw);
   } else {
     if (g.per1) rdft_dense_rows<T, false>(rows, P, n1, false, (T*)s.scr, 2 * scr_elems, (const c2<T>*)s.cos4);
     else dct_dense_rows<T, false>(rows, P, n1, false, (T*)s.scr, 2 * scr_elems, s.cos4);
@@ -507,7 +508,8 @@ __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const 
   __syncthreads();
   Rows<T, 1, 1> rows{s.tile, n1, 0};
   if constexpr (N1 > 0) {
-    DctPow2<T, N1, N2, false, 256>::inverse(rows, Pr, s.scr, s.tw, s.hw);
+    if (g.per1) DctPow2<T, N1, N2, false, 256, true>::inverse(rows, Pr, s.scr, s.tw, s.hw);
+    else DctPow2<T, N1, N2, false, 256>::inverse(rows, Pr, s.scr, s.tw, s.hw);
   } else {
     if (g.per1) rdft_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, (const c2<T>*)s.cos4);
     else dct_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, s.cos4);
@@ -616,7 +618,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restri
   Rows<T, W, W> rows{tile, cst, 1};
   const int nrows = C * W;
   if constexpr (M1 > 0) {
-    DctPow2<T, M1, M2, true, NT>::forward(rows, nrows, scr, tw, hw);
+    if (g.per2) DctPow2<T, M1, M2, true, NT, true>::forward(rows, nrows, scr, tw, hw);
+    else DctPow2<T, M1, M2, true, NT>::forward(rows, nrows, scr, tw, hw);
   } else {
     if (g.per2) rdft_dense_rows<T, true>(rows, nrows, n2, false, (T*)scr, 2 * scr_elems, (const c2<T>*)cos4);
     else dct_dense_rows<T, true>(rows, nrows, n2, false, (T*)scr, 2 * scr_elems, cos4);
@@ -667,7 +670,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restri
   }
   __syncthreads();
   if constexpr (M1 > 0) {
-    DctPow2<T, M1, M2, true, NT>::inverse(rows, nrows, scr, tw, hw);
+    if (g.per2) DctPow2<T, M1, M2, true, NT, true>::inverse(rows, nrows, scr, tw, hw);
+    else DctPow2<T, M1, M2, true, NT>::inverse(rows, nrows, scr, tw, hw);
   } else {
     if (g.per2) rdft_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, (const c2<T>*)cos4);
     else dct_dense_rows<T, true>(rows, nrows, n2, true, (T*)scr, 2 * scr_elems, cos4);
@@ -711,7 +715,7 @@ constexpr int kPart = 68;
 
 // The body of the tiled update.  INTERIOR: every thread of the block has both x and y neighbours
 // inside the grid, so the boundary tests fold away (about three quarters of the blocks at 256^2).
-template <typename T, int C, bool CHECK, bool WRITE_X, bool INTERIOR>
+template <typename T, int C, bool CHECK, bool WRITE_X, bool INTERIOR, bool PXY>
 __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<T>& A, int TC,
                                                   double* __restrict__ part, T (&sbb)[2][kTY][kTX][C],
                                                   double (&smass)[64]) {
@@ -723,13 +727,23 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   const int t0 = (blockIdx.z % nch) * TC;
   const int tend = min(t0 + TC, g.P);           // planes [t0, tend) are written
   const int tlast = min(tend, g.P - 1);          // planes [t0, tlast] are computed
+  // periodic x / y (edge blocks only): threads past the last cell stand for cells 0, 1, ... so that the
+  // shuffles and the shared-memory exchange see the wrapped neighbours; every cell is written by a lane
+  // that is not the block's halo lane or row (the grid has ceil(n / (kT - 1)) blocks on a periodic axis)
+  const bool px = PXY && !INTERIOR && g.per1, py = PXY && !INTERIOR && g.per2;
   const bool vx = INTERIOR || x < g.n1, vy = INTERIOR || y < g.n2;
   const bool live = vx && vy;
-  const int xs = vx ? x : g.n1 - 1, ys = vy ? y : g.n2 - 1;   // clamped for safe loads
-  const bool out = live && (lane < kTX - 1 || (!INTERIOR && x == g.n1 - 1)) &&
-                   (row < kTY - 1 || (!INTERIOR && y == g.n2 - 1));
-  const bool hasR = INTERIOR || xs < g.n1 - 1, hasL = INTERIOR || xs > 0;
-  const bool hasU = INTERIOR || ys < g.n2 - 1, hasD = INTERIOR || ys > 0;
+  const int xs = vx ? x : (px ? x % g.n1 : g.n1 - 1);   // clamped (Neumann) or wrapped (periodic)
+  const int ys = vy ? y : (py ? y % g.n2 : g.n2 - 1);
+  const bool out = live && (lane < kTX - 1 || (!INTERIOR && !px && x == g.n1 - 1)) &&
+                   (row < kTY - 1 || (!INTERIOR && !py && y == g.n2 - 1));
+  const bool hasR = INTERIOR || px || xs < g.n1 - 1, hasL = INTERIOR || px || xs > 0;
+  const bool hasU = INTERIOR || py || ys < g.n2 - 1, hasD = INTERIOR || py || ys > 0;
+  // offsets to the four neighbours in the plane (wrapped on a periodic axis)
+  const int dxr = (px && xs == g.n1 - 1) ? 1 - g.n1 : 1;
+  const int dxl = (px && xs == 0) ? g.n1 - 1 : -1;
+  const int dyu = (py && ys == g.n2 - 1) ? (1 - g.n2) * g.n1 : g.n1;
+  const int dyd = (py && ys == 0) ? (g.n2 - 1) * g.n1 : -g.n1;
   // 32-bit offsets from per-thread column bases (problem sizes stay below 2^31 cells)
   const int S = g.S, sy = g.n1, sc = g.n1 * g.n2;
   const size_t col = (size_t)b * g.P * S + xs + (size_t)sy * ys;
@@ -794,18 +808,18 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
       lb[c][2] = pb2[o];
       lb[c][3] = pb3[o];
       phn[c] = tnext ? pph[o + S] : T(0);
-      phy[c] = hasU ? pph[o + sy] : T(0);
-      phd[c] = hasD ? pph[o - sy] : T(0);
-      la1d[c] = hasD ? pa1[o - sy] : T(0);
-      la0l[c] = (lane == 0 && hasL) ? pa0[o - 1] : T(0);
-      phl[c] = (lane == 0 && hasL) ? pph[o - 1] : T(0);
+      phy[c] = hasU ? pph[o + dyu] : T(0);
+      phd[c] = hasD ? pph[o + dyd] : T(0);
+      la1d[c] = hasD ? pa1[o + dyd] : T(0);
+      la0l[c] = (lane == 0 && hasL) ? pa0[o + dxl] : T(0);
+      phl[c] = (lane == 0 && hasL) ? pph[o + dxl] : T(0);
     }
     // right faces of x^{r+1}
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const T ph = phic[c];
       T phx = __shfl_down_sync(0xffffffffu, ph, 1);
-      if (lane == kTX - 1 && hasR) phx = pph[pt + c * sc + 1];
+      if (lane == kTX - 1 && hasR) phx = pph[pt + c * sc + dxr];
       xr[c][0] = hasR ? la0[c] + s1 * (phx - ph) : T(0);
       xr[c][1] = hasU ? la1[c] + s2 * (phy[c] - ph) : T(0);
       xr[c][3] = tnext ? la3[c] + sp * (phn[c] - ph) : pf1[c * sc];
@@ -934,15 +948,17 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   }
 }
 
-template <typename T, int C, bool CHECK, bool WRITE_X>
+// PXY: the edge blocks handle periodic x / y (a separate instance, so that the Neumann kernel keeps its
+// register allocation)
+template <typename T, int C, bool CHECK, bool WRITE_X, bool PXY>
 __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<T> g, Arrays<T> A, int TC,
                                                                 double* __restrict__ part) {
   __shared__ T sbb[2][kTY][kTX][C];   // bbar_y exchange, double-buffered by plane parity
   __shared__ double smass[64];
   const int x0 = blockIdx.x * (kTX - 1), y0 = blockIdx.y * (kTY - 1);
   const bool interior = x0 >= 1 && x0 + kTX < g.n1 && y0 >= 1 && y0 + kTY < g.n2;
-  if (interior) update_tiled_body<T, C, CHECK, WRITE_X, true>(g, A, TC, part, sbb, smass);
-  else update_tiled_body<T, C, CHECK, WRITE_X, false>(g, A, TC, part, sbb, smass);
+  if (interior) update_tiled_body<T, C, CHECK, WRITE_X, true, PXY>(g, A, TC, part, sbb, smass);
+  else update_tiled_body<T, C, CHECK, WRITE_X, false, PXY>(g, A, TC, part, sbb, smass);
 }
 
 

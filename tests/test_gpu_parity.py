@@ -55,6 +55,9 @@ GRIDS = [
     ((32, 16, 3), ("periodic", "neumann", "periodic"), 6),
     ((16, 24), ("neumann", "periodic"), 5),
     ((33, 7), ("periodic", "periodic"), 4),
+    ((64, 128, 3), ("periodic", "periodic", "periodic"), 8),
+    ((256, 64, 3), ("periodic", "neumann", "periodic"), 4),
+    ((128, 64), ("neumann", "periodic"), 6),
     ((256, 256, 3), RGB, 32),
 ]
 IDS = ["x".join(map(str, n)) + "_" + "".join(b[0] for b in bc) + "_P%d" % P for n, bc, P in GRIDS]
@@ -229,6 +232,19 @@ def test_full_solve_periodic_xy_24x20x3x8(ot):
     for k in range(3):
         assert rel(path["m"][k][0], st.m[k] * scale) <= 1e-3
     assert abs(stats.energy - infos[-1].energy * scale) <= 1e-3 * infos[-1].energy * scale
+    assert stats.mass_drift <= 1e-5
+
+
+def test_full_solve_periodic_xy_64x32x3x8(ot):
+    """Periodic x, y and colour on power-of-two axes (the FFT real-Fourier transforms): 300 iterations
+    against the oracle."""
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(64, 32, 4, 6)
+    bc = ("periodic", "periodic", "periodic")
+    plan, g, stats, path, st, infos, scale = _solve_both(ot, (64, 32, 3), bc, 8, 300, f0, f1)
+    assert rel(path["f"][0], st.f * scale) <= 1e-3
+    for k in range(3):
+        assert rel(path["m"][k][0], st.m[k] * scale) <= 1e-3
     assert stats.mass_drift <= 1e-5
 
 
