@@ -51,38 +51,38 @@ __device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T inv
   const T s2 = am0 * am0 + am1 * am1 + am2 * am2;
   const T e = sigma * af;
   const T d = T(0.5) * sigma * sigma * s2;
-  if (!(e + d > T(0))) {
-    u0 = u1 = u2 = v = T(0);
-    return;
-  }
+  const bool live = e + d > T(0);
   const T c = T(1) + e;
   const T cbd = cbrt_start(d);
-  T z;
-  if (c > T(0)) {
-    const T del = min(cbd, fdiv_fast(d, c * c));
-    z = e + del;
-  } else {
-    z = min(cbd, sqrt(fdiv_fast(d, -c))) - T(1);
-  }
-  z = max(z, T(0));
+  // both starts are computed and one is selected, so that the three channels of a cell interleave
+  const T zpos = e + min(cbd, fdiv_fast(d, c * c));                  // c > 0
+  const T zneg = min(cbd, sqrt(fdiv_fast(d, fabs(c)))) - T(1);        // c <= 0
+  T z = live ? max(c > T(0) ? zpos : zneg, T(0)) : T(0);
   // Stop when the step is below a few units in the last place of the data
   // scale |e| + d + z: near e + d = 0 the root cannot be resolved more finely
   // in this precision, and a purely relative test would never be met there.
   const T tol = (sizeof(T) == 4 ? T(4.0 / 16777216.0) : T(4.0 / 9007199254740992.0)) * (fabs(e) + d);
   const T eps = sizeof(T) == 4 ? T(4.0 / 16777216.0) : T(4.0 / 9007199254740992.0);
   // Newton's method corrects its own rounding, so its steps use the fast
-  // division; the result below uses the correctly rounded one.
-#pragma unroll 1
-  for (int it = 0; it < 40; ++it) {
+  // division; the result below uses the correctly rounded one.  Three steps
+  // are taken unconditionally (the stop rule is met within three on typical
+  // cells, and a step from a converged z leaves it in place); the loop runs
+  // only while a cell has not met it.
+  auto newton = [&]() {
     const T w = T(1) + z;
     const T zme = z - e;
     const T q = w * w * zme - d;
     const T dq = w * (T(2) * zme + w);
     const T step = fdiv_fast(q, dq);
     z -= step;
-    if (!(fabs(step) > eps * z + tol)) break;
-  }
-  z = max(z, T(0));
+    return step;
+  };
+  newton();
+  newton();
+  T step = newton();
+#pragma unroll 1
+  for (int it = 3; it < 40 && live && fabs(step) > eps * z + tol; ++it) step = newton();
+  z = live ? max(z, T(0)) : T(0);
   const T r = fdiv_fast(z, T(1) + z);
   u0 = r * am0;
   u1 = r * am1;
@@ -813,6 +813,7 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
       la1d[c] = hasD ? pa1[o + dyd] : T(0);
       la0l[c] = (lane == 0 && hasL) ? pa0[o + dxl] : T(0);
       phl[c] = (lane == 0 && hasL) ? pph[o + dxl] : T(0);
+    }
     }
     // right faces of x^{r+1}
 #pragma unroll
