@@ -814,7 +814,6 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
       la0l[c] = (lane == 0 && hasL) ? pa0[o + dxl] : T(0);
       phl[c] = (lane == 0 && hasL) ? pph[o + dxl] : T(0);
     }
-    }
     // right faces of x^{r+1}
 #pragma unroll
     for (int c = 0; c < C; ++c) {
