@@ -15,7 +15,8 @@
 // V_a = (Z_k + conj Z_{N-k})/2, V_b = (Z_k - conj Z_{N-k})/(2i)).  The DFT of
 // length N = N1*N2 is Bailey's four-step split: N1-point DFTs in registers,
 // twiddles, a transpose through shared memory, N2-point DFTs in registers.
-// Each register DFT is an unrolled radix-2 Cooley-Tukey decimation in time.
+// Each register DFT is an unrolled radix-2 Cooley-Tukey decimation in time; an
+// N2 of 3 * 2^k (lengths 96 = 16 * 6 and 192 = 16 * 12) adds one radix-3 step.
 // Other lengths use the dense cosine sum (O(N) per output).
 #pragma once
 #include "common.cuh"
@@ -95,6 +96,47 @@ __device__ __forceinline__ void dft_reg_br(c2<T> (&a)[R], const c2<T>* __restric
   }
 }
 
+template <int R> struct IsPow2 { static constexpr bool v = R > 0 && (R & (R - 1)) == 0; };
+
+// In-register DFT of length R = 2^k or 3 * 2^k (same conventions as dft_reg).  For 3 * 2^k it is one
+// radix-3 decimation-in-time step: the three interleaved subsequences z[3m + r] are transformed with
+// dft_reg and combined as Z[k + j R/3] = sum_r w3^(j r) W_R^(k r) E_r[k] (w3 = W_R^(R/3), j = 0, 1, 2).
+template <typename T, int R, int NT, bool INV>
+__device__ __forceinline__ void dft_any(c2<T> (&z)[R], const c2<T>* __restrict__ twN) {
+  if constexpr (IsPow2<R>::v) {
+    dft_reg<T, R, NT, INV>(z, twN);
+  } else {
+    static_assert(R % 3 == 0 && IsPow2<R / 3>::v, "length 2^k or 3 * 2^k");
+    constexpr int M = R / 3;
+    c2<T> e[3][M];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) e[r][m] = z[3 * m + r];
+      if constexpr (M > 1) dft_reg<T, M, NT, INV>(e[r], twN);
+    }
+    const c2<T> w3 = twN[M * (NT / R)];             // exp(-2 pi i / 3)
+    const T wr = w3.x, wi = INV ? -w3.y : w3.y;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      c2<T> b = e[1][k], c = e[2][k];
+      if (k != 0) {
+        const c2<T> w1 = twN[k * (NT / R)], w2 = twN[2 * k * (NT / R)];
+        b = INV ? cmulc<T>(b, w1) : cmul<T>(b, w1);
+        c = INV ? cmulc<T>(c, w2) : cmul<T>(c, w2);
+      }
+      const c2<T> a = e[0][k];
+      const c2<T> s = cadd<T>(b, c), d = csub<T>(b, c);
+      // w b + conj(w) c = Re(w) (b + c) + i Im(w) (b - c)
+      const c2<T> base = mk2<T>(a.x + wr * s.x, a.y + wr * s.y);
+      const c2<T> rot = mk2<T>(-wi * d.y, wi * d.x);
+      z[k] = cadd<T>(a, s);
+      z[k + M] = cadd<T>(base, rot);
+      z[k + 2 * M] = csub<T>(base, rot);
+    }
+  }
+}
+
 // Fill twiddle tables in shared memory: tw[j] = exp(-2 pi i j/N), hw[k] = exp(-i pi k/(2N)).
 // gtw / ghw are the same tables precomputed in double on the host.
 template <typename T>
@@ -128,14 +170,15 @@ template <typename T, int N1, int N2, bool PFAST, int NT, bool PERIODIC = false>
 struct DctPow2 {
   static constexpr int N = N1 * N2;
   static constexpr int CP = NT / N1;
-  static_assert((N1 & (N1 - 1)) == 0 && (N2 & (N2 - 1)) == 0, "power-of-two factors");
+  static_assert(IsPow2<N1>::v && N2 % 2 == 0 && (IsPow2<N2>::v || (N2 % 3 == 0 && IsPow2<N2 / 3>::v)),
+                "N1 a power of two, N2 = 2^k or 3 * 2^k (even)");
   static_assert(CP >= 1 && CP * N1 == NT, "block size must be a multiple of N1");
 
   // scratch address of (pair p, slot j in [0, N))
   __device__ static __forceinline__ int sidx(int p, int j) { return PFAST ? j * CP + p : p * N + j; }
   // transpose slot of (k1, n2) with an XOR swizzle against bank conflicts (element-fast order)
   __device__ static __forceinline__ int tslot(int k1, int n2) {
-    return PFAST ? k1 * N2 + n2 : k1 * N2 + (n2 ^ (k1 & (N2 - 1)));
+    return (PFAST || !IsPow2<N2>::v) ? k1 * N2 + n2 : k1 * N2 + (n2 ^ (k1 & (N2 - 1)));
   }
   // split a work item into (pair, index) with `per` indices per pair
   template <int PER>
@@ -185,7 +228,7 @@ struct DctPow2 {
         if (act) {
 #pragma unroll
           for (int n2 = 0; n2 < N2; ++n2) y[n2] = scr[sidx(p, tslot(k1, n2))];
-          dft_reg<T, N2, N, false>(y, tw);
+          dft_any<T, N2, N, false>(y, tw);
         }
         __syncthreads();
         if (act) {
@@ -202,7 +245,7 @@ struct DctPow2 {
         split<N>(it, p, k);
         if (p < cp) {
           const c2<T> zk = scr[sidx(p, k)];
-          const c2<T> zm = scr[sidx(p, (N - k) & (N - 1))];
+          const c2<T> zm = scr[sidx(p, IsPow2<N>::v ? ((N - k) & (N - 1)) : (k == 0 ? 0 : N - k))];
           // V_a = (Z_k + conj Z_m)/2 ; V_b = (Z_k - conj Z_m)/(2i)
           const T vax = T(0.5) * (zk.x + zm.x), vay = T(0.5) * (zk.y - zm.y);
           const T vbx = T(0.5) * (zk.y + zm.y), vby = T(0.5) * (zm.x - zk.x);
@@ -295,7 +338,7 @@ struct DctPow2 {
           c2<T> y[N2];
 #pragma unroll
           for (int n2 = 0; n2 < N2; ++n2) y[n2] = scr[sidx(p, tslot(k1, n2))];
-          dft_reg<T, N2, N, true>(y, tw);
+          dft_any<T, N2, N, true>(y, tw);
           T* ra = rows.row(2 * (p0 + p));
           T* rb = rows.row(2 * (p0 + p) + 1);
 #pragma unroll

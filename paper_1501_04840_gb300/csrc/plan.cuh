@@ -25,7 +25,8 @@ constexpr int kThreadsUpd = 128;
 constexpr int kW = DYNOT_YC_W;   // x-strip width of the y/colour pass
 
 inline int pmax_for(int P) { return P <= 16 ? 16 : (P <= 32 ? 32 : 64); }
-inline bool fft_len(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+// lengths with an FFT path: 2^k (64-512) and 3 * 2^k (96 = 16 * 6, 192 = 16 * 12); N1 = fft_n1(n)
+inline bool fft_len(int n) { return n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512; }
 inline int fft_n1(int n) { return n == 64 ? 8 : (n == 128 ? 8 : 16); }
 // threads per block of the y/colour pass (matches pick_kb)
 inline int yc_threads(int n2) { return fft_len(n2) ? 12 * fft_n1(n2) : 256; }
@@ -66,7 +67,9 @@ template <typename T, int PM>
 KA<T> pick_ka_p(int n) {
   switch (n) {
     case 64: return k_rhs_fwd_xt<T, 8, 8, PM>;
+    case 96: return k_rhs_fwd_xt<T, 16, 6, PM>;
     case 128: return k_rhs_fwd_xt<T, 8, 16, PM>;
+    case 192: return k_rhs_fwd_xt<T, 16, 12, PM>;
     case 256: return k_rhs_fwd_xt<T, 16, 16, PM>;
     case 512: return k_rhs_fwd_xt<T, 16, 32, PM>;
     default: return k_rhs_fwd_xt<T, 0, 0, PM>;
@@ -80,7 +83,9 @@ template <typename T, int PM>
 KC<T> pick_kc_p(int n) {
   switch (n) {
     case 64: return k_inv_xt<T, 8, 8, PM>;
+    case 96: return k_inv_xt<T, 16, 6, PM>;
     case 128: return k_inv_xt<T, 8, 16, PM>;
+    case 192: return k_inv_xt<T, 16, 12, PM>;
     case 256: return k_inv_xt<T, 16, 16, PM>;
     case 512: return k_inv_xt<T, 16, 32, PM>;
     default: return k_inv_xt<T, 0, 0, PM>;
@@ -94,7 +99,9 @@ template <typename T>
 KB<T> pick_kb(int n) {
   switch (n) {
     case 64: return k_solve_yc<T, 8, 8, kW, 12 * 8>;
+    case 96: return k_solve_yc<T, 16, 6, kW, 12 * 16>;
     case 128: return k_solve_yc<T, 8, 16, kW, 12 * 8>;
+    case 192: return k_solve_yc<T, 16, 12, kW, 12 * 16>;
     case 256: return k_solve_yc<T, 16, 16, kW, 12 * 16>;
     case 512: return k_solve_yc<T, 16, 32, kW, 12 * 16>;
     default: return k_solve_yc<T, 0, 0, kW, 256>;

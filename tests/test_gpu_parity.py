@@ -58,6 +58,9 @@ GRIDS = [
     ((64, 128, 3), ("periodic", "periodic", "periodic"), 8),
     ((256, 64, 3), ("periodic", "neumann", "periodic"), 4),
     ((128, 64), ("neumann", "periodic"), 6),
+    ((192, 96, 3), RGB, 16),
+    ((96, 192, 3), ("periodic", "periodic", "periodic"), 8),
+    ((192, 64), ("periodic", "neumann"), 6),
     ((256, 256, 3), RGB, 32),
 ]
 IDS = ["x".join(map(str, n)) + "_" + "".join(b[0] for b in bc) + "_P%d" % P for n, bc, P in GRIDS]
@@ -242,6 +245,18 @@ def test_full_solve_periodic_xy_64x32x3x8(ot):
     f0, f1 = synth.rgb_pair(64, 32, 4, 6)
     bc = ("periodic", "periodic", "periodic")
     plan, g, stats, path, st, infos, scale = _solve_both(ot, (64, 32, 3), bc, 8, 300, f0, f1)
+    assert rel(path["f"][0], st.f * scale) <= 1e-3
+    for k in range(3):
+        assert rel(path["m"][k][0], st.m[k] * scale) <= 1e-3
+    assert stats.mass_drift <= 1e-5
+
+
+def test_full_solve_radix3_96x96x3x4(ot):
+    """Sides of 3 * 2^k take the FFT path with a radix-3 step (96 = 16 * 6): 300 iterations against the
+    oracle."""
+    from paper_1501_04840_gb300 import synth
+    f0, f1 = synth.rgb_pair(96, 96, 6, 7)
+    plan, g, stats, path, st, infos, scale = _solve_both(ot, (96, 96, 3), RGB, 4, 300, f0, f1)
     assert rel(path["f"][0], st.f * scale) <= 1e-3
     for k in range(3):
         assert rel(path["m"][k][0], st.m[k] * scale) <= 1e-3
