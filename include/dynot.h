@@ -253,7 +253,7 @@ int ot_batch_groups(ot_batch_t b);
 void ot_batch_destroy(ot_batch_t b);
 
 /*
- * Warm-start network kernels (SURVEY / north_star "learned warm start"; the
+ * Warm-start network kernels (a learned initial path for Algorithm 1; the
  * paper has no network).  A 3D U-Net over (t, y, x) maps the boundary densities
  * of an RGB pair to an initial path x0 for Algorithm 1 (ot_solve's init_path).
  * All pointers are DEVICE memory; work is ordered on `stream` (cudaStream_t,
