@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import shutil
 import statistics
 import subprocess
@@ -161,9 +162,19 @@ def measured_peak():
 
 
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
+    """Hash of the sources the measured solver kernels compile from: plan_f32.cu and the csrc files it
+    includes, directly or not (the C ABI, network and pipeline units do not enter these kernels)."""
     csrc = os.path.join(ROOT, "paper_1501_04840_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    seen, todo = set(), ["plan_f32.cu"]
+    while todo:
+        name = todo.pop()
+        if name in seen or not os.path.exists(os.path.join(csrc, name)):
+            continue
+        seen.add(name)
+        with open(os.path.join(csrc, name)) as fh:
+            todo += re.findall(r'^\s*#include\s+"([^"/]+)"', fh.read(), flags=re.M)
+    h = hashlib.sha256()
+    for name in sorted(seen):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
