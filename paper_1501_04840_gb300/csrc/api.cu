@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "abi_guard.h"
 #include "plan_base.h"
 
 using namespace dynot;
@@ -191,16 +192,18 @@ void ot_grid_hue(ot_grid* g, int bins, int P) {
 }
 
 ot_status ot_plan(const ot_grid* gi, int batch, void* cuda_stream, ot_plan_t* out) {
-  if (!out) return seterr(OT_EINVAL, "out is NULL");
-  *out = nullptr;
-  ot_grid g;
-  OT_TRY(validate(gi, batch, g));
-  std::unique_ptr<PlanBase> impl;
-  OT_TRY(make_plan(g, batch, cuda_stream, impl));
-  ot_plan_s* h = new ot_plan_s;
-  h->impl = std::move(impl);
-  *out = h;
-  return OT_OK;
+  return ot_guard([&]() -> ot_status {
+    if (!out) return seterr(OT_EINVAL, "out is NULL");
+    *out = nullptr;
+    ot_grid g;
+    OT_TRY(validate(gi, batch, g));
+    std::unique_ptr<PlanBase> impl;
+    OT_TRY(make_plan(g, batch, cuda_stream, impl));
+    ot_plan_s* h = new ot_plan_s;
+    h->impl = std::move(impl);
+    *out = h;
+    return OT_OK;
+  });
 }
 
 }  // extern "C"
@@ -234,45 +237,47 @@ ot_status make_plan(const ot_grid& g, int batch, void* cuda_stream, std::unique_
 extern "C" {
 
 ot_status ot_batch_create(const ot_grid* grids, int count, void* cuda_stream, ot_batch_t* out) {
-  if (!out || !grids || count < 1) return seterr(OT_EINVAL, "bad batch arguments");
-  *out = nullptr;
-  std::unique_ptr<ot_batch_s> b(new ot_batch_s);
-  std::vector<ot_grid> keys;
-  std::vector<int> counts;
-  b->grp.resize(count);
-  b->idx.resize(count);
-  for (int i = 0; i < count; ++i) {
-    ot_grid g;
-    OT_TRY(validate(&grids[i], 1, g));
-    int k = -1;
-    for (size_t j = 0; j < keys.size(); ++j)
-      if (same_shape(keys[j], g)) { k = (int)j; break; }
-    if (k < 0) {
-      k = (int)keys.size();
-      keys.push_back(g);
-      counts.push_back(0);
+  return ot_guard([&]() -> ot_status {
+    if (!out || !grids || count < 1) return seterr(OT_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    std::unique_ptr<ot_batch_s> b(new ot_batch_s);
+    std::vector<ot_grid> keys;
+    std::vector<int> counts;
+    b->grp.resize(count);
+    b->idx.resize(count);
+    for (int i = 0; i < count; ++i) {
+      ot_grid g;
+      OT_TRY(validate(&grids[i], 1, g));
+      int k = -1;
+      for (size_t j = 0; j < keys.size(); ++j)
+        if (same_shape(keys[j], g)) { k = (int)j; break; }
+      if (k < 0) {
+        k = (int)keys.size();
+        keys.push_back(g);
+        counts.push_back(0);
+      }
+      b->grp[i] = k;
+      b->idx[i] = counts[k]++;
     }
-    b->grp[i] = k;
-    b->idx[i] = counts[k]++;
-  }
-  for (size_t j = 0; j < keys.size(); ++j) {
-    std::unique_ptr<PlanBase> p;
-    OT_TRY(make_plan(keys[j], counts[j], nullptr, p));   // each group on a stream of its own
-    b->groups.push_back(std::move(p));
-  }
-  if (cuda_stream) {
-    b->main = (cudaStream_t)cuda_stream;
-  } else {
-    CUDA_OK(cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking));
-    b->own_main = true;
-  }
-  CUDA_OK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-  CUDA_OK(cudaEventCreate(&b->t0));
-  CUDA_OK(cudaEventCreate(&b->t1));
-  b->join.resize(b->groups.size());
-  for (auto& e : b->join) CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  *out = b.release();
-  return OT_OK;
+    for (size_t j = 0; j < keys.size(); ++j) {
+      std::unique_ptr<PlanBase> p;
+      OT_TRY(make_plan(keys[j], counts[j], nullptr, p));   // each group on a stream of its own
+      b->groups.push_back(std::move(p));
+    }
+    if (cuda_stream) {
+      b->main = (cudaStream_t)cuda_stream;
+    } else {
+      CUDA_OK(cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking));
+      b->own_main = true;
+    }
+    CUDA_OK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    CUDA_OK(cudaEventCreate(&b->t0));
+    CUDA_OK(cudaEventCreate(&b->t1));
+    b->join.resize(b->groups.size());
+    for (auto& e : b->join) CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    *out = b.release();
+    return OT_OK;
+  });
 }
 
 int ot_batch_groups(ot_batch_t b) { return b ? (int)b->groups.size() : 0; }
@@ -281,68 +286,72 @@ void ot_batch_destroy(ot_batch_t b) { delete b; }
 
 ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* const* f1, int iters, double tol,
                          int check_every, ot_solve_stats* stats) {
-  if (!b || !f0 || !f1 || iters < 1) return seterr(OT_EINVAL, "bad batch solve arguments");
-  const int count = (int)b->grp.size();
-  for (int i = 0; i < count; ++i) OT_TRY(b->groups[b->grp[i]]->stage_problem(b->idx[i], f0[i], f1[i]));
-  for (auto& g : b->groups) OT_TRY(g->prepare_staged());   // validation, rescaling, cold start
-  for (size_t i = 0; i < b->groups.size(); ++i) {
-    CUDA_OK(cudaEventRecord(b->join[i], b->groups[i]->st));
-    CUDA_OK(cudaStreamWaitEvent(b->main, b->join[i], 0));
-  }
-  CUDA_OK(cudaEventRecord(b->t0, b->main));
-  const int K = check_every > 0 ? check_every : iters;
-  int done = 0;
-  bool converged = false;
-  std::vector<std::vector<ProblemCheck>> per(b->groups.size());
-  while (done < iters) {
-    const int chunk = std::min(K, iters - done);
-    const int plain = chunk - 1;
-    const int par = b->groups[0]->parity();
-    if (plain >= 2) OT_TRY(batch_capture(*b, par));
-    for (int r = 0; r < plain / 2; ++r) CUDA_OK(cudaGraphLaunch(b->gexec[par], b->main));
-    // the remaining single iteration and the checked one, per group after the graph
-    CUDA_OK(cudaEventRecord(b->fork, b->main));
+  return ot_guard([&]() -> ot_status {
+    if (!b || !f0 || !f1 || iters < 1) return seterr(OT_EINVAL, "bad batch solve arguments");
+    const int count = (int)b->grp.size();
+    for (int i = 0; i < count; ++i) OT_TRY(b->groups[b->grp[i]]->stage_problem(b->idx[i], f0[i], f1[i]));
+    for (auto& g : b->groups) OT_TRY(g->prepare_staged());   // validation, rescaling, cold start
     for (size_t i = 0; i < b->groups.size(); ++i) {
-      PlanBase& P = *b->groups[i];
-      CUDA_OK(cudaStreamWaitEvent(P.st, b->fork, 0));
-      if (plain % 2) OT_TRY(P.enqueue_single());
-      OT_TRY(P.enqueue_check_async());
-      CUDA_OK(cudaEventRecord(b->join[i], P.st));
+      CUDA_OK(cudaEventRecord(b->join[i], b->groups[i]->st));
       CUDA_OK(cudaStreamWaitEvent(b->main, b->join[i], 0));
     }
-    CUDA_OK(cudaStreamSynchronize(b->main));
-    done += chunk;
-    double worst = 0;
-    for (size_t i = 0; i < b->groups.size(); ++i) {
-      OT_TRY(b->groups[i]->collect(per[i]));
-      for (const ProblemCheck& c : per[i]) worst = std::max(worst, c.residual);
+    CUDA_OK(cudaEventRecord(b->t0, b->main));
+    const int K = check_every > 0 ? check_every : iters;
+    int done = 0;
+    bool converged = false;
+    std::vector<std::vector<ProblemCheck>> per(b->groups.size());
+    while (done < iters) {
+      const int chunk = std::min(K, iters - done);
+      const int plain = chunk - 1;
+      const int par = b->groups[0]->parity();
+      if (plain >= 2) OT_TRY(batch_capture(*b, par));
+      for (int r = 0; r < plain / 2; ++r) CUDA_OK(cudaGraphLaunch(b->gexec[par], b->main));
+      // the remaining single iteration and the checked one, per group after the graph
+      CUDA_OK(cudaEventRecord(b->fork, b->main));
+      for (size_t i = 0; i < b->groups.size(); ++i) {
+        PlanBase& P = *b->groups[i];
+        CUDA_OK(cudaStreamWaitEvent(P.st, b->fork, 0));
+        if (plain % 2) OT_TRY(P.enqueue_single());
+        OT_TRY(P.enqueue_check_async());
+        CUDA_OK(cudaEventRecord(b->join[i], P.st));
+        CUDA_OK(cudaStreamWaitEvent(b->main, b->join[i], 0));
+      }
+      CUDA_OK(cudaStreamSynchronize(b->main));
+      done += chunk;
+      double worst = 0;
+      for (size_t i = 0; i < b->groups.size(); ++i) {
+        OT_TRY(b->groups[i]->collect(per[i]));
+        for (const ProblemCheck& c : per[i]) worst = std::max(worst, c.residual);
+      }
+      if (tol > 0 && worst <= tol) {
+        converged = true;
+        break;
+      }
     }
-    if (tol > 0 && worst <= tol) {
-      converged = true;
-      break;
+    CUDA_OK(cudaEventRecord(b->t1, b->main));
+    CUDA_OK(cudaEventSynchronize(b->t1));
+    float ms = 0;
+    CUDA_OK(cudaEventElapsedTime(&ms, b->t0, b->t1));
+    if (stats) {
+      for (int i = 0; i < count; ++i) {
+        const ProblemCheck& c = per[b->grp[i]][b->idx[i]];
+        stats[i].iterations = done;
+        stats[i].residual = c.residual;
+        stats[i].energy = c.energy;
+        stats[i].mass_drift = c.drift;
+        stats[i].elapsed_ms = ms;
+      }
     }
-  }
-  CUDA_OK(cudaEventRecord(b->t1, b->main));
-  CUDA_OK(cudaEventSynchronize(b->t1));
-  float ms = 0;
-  CUDA_OK(cudaEventElapsedTime(&ms, b->t0, b->t1));
-  if (stats) {
-    for (int i = 0; i < count; ++i) {
-      const ProblemCheck& c = per[b->grp[i]][b->idx[i]];
-      stats[i].iterations = done;
-      stats[i].residual = c.residual;
-      stats[i].energy = c.energy;
-      stats[i].mass_drift = c.drift;
-      stats[i].elapsed_ms = ms;
-    }
-  }
-  if (tol > 0 && !converged) return seterr(OT_ENOTCONV, "batch: tolerance not reached after %d iterations", done);
-  return OT_OK;
+    if (tol > 0 && !converged) return seterr(OT_ENOTCONV, "batch: tolerance not reached after %d iterations", done);
+    return OT_OK;
+  });
 }
 
 ot_status ot_batch_path(ot_batch_t b, int i, float* f, float* m0, float* m1, float* m2) {
-  if (!b || i < 0 || i >= (int)b->grp.size()) return seterr(OT_EINVAL, "bad batch problem index");
-  return b->groups[b->grp[i]]->path_one(b->idx[i], f, m0, m1, m2);
+  return ot_guard([&]() -> ot_status {
+    if (!b || i < 0 || i >= (int)b->grp.size()) return seterr(OT_EINVAL, "bad batch problem index");
+    return b->groups[b->grp[i]]->path_one(b->idx[i], f, m0, m1, m2);
+  });
 }
 
 void ot_destroy(ot_plan_t p) {
@@ -368,28 +377,34 @@ static ot_status call_grid(PlanBase& P, const ot_grid* g) {
 
 ot_status ot_solve(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
                    const float* init_path, ot_solve_stats* stats) {
-  if (!p) return seterr(OT_EINVAL, "plan is NULL");
-  PlanBase& P = *p->impl;
-  OT_TRY(call_grid(P, g));
-  return P.solve(f0, f1, iters, tol, init_path, nullptr, 0, 0.0, 0.0, stats, nullptr);
+  return ot_guard([&]() -> ot_status {
+    if (!p) return seterr(OT_EINVAL, "plan is NULL");
+    PlanBase& P = *p->impl;
+    OT_TRY(call_grid(P, g));
+    return P.solve(f0, f1, iters, tol, init_path, nullptr, 0, 0.0, 0.0, stats, nullptr);
+  });
 }
 
 ot_status ot_solve_warm(ot_plan_t p, const float* f0, const float* f1, const ot_grid* g, int iters, double tol,
                         const float* init_path, const float* init_dual, int dual_init, double dual_support,
                         double fallback_residual, ot_solve_stats* stats, int* used_cold) {
-  if (!p) return seterr(OT_EINVAL, "plan is NULL");
-  if (!init_path) return seterr(OT_EINVAL, "init_path is required");
-  if (!(fallback_residual >= 0) || !(dual_support >= 0))
-    return seterr(OT_EINVAL, "fallback_residual and dual_support must be >= 0");
-  PlanBase& P = *p->impl;
-  OT_TRY(call_grid(P, g));
-  return P.solve(f0, f1, iters, tol, init_path, init_dual, dual_init, dual_support, fallback_residual, stats,
-                 used_cold);
+  return ot_guard([&]() -> ot_status {
+    if (!p) return seterr(OT_EINVAL, "plan is NULL");
+    if (!init_path) return seterr(OT_EINVAL, "init_path is required");
+    if (!(fallback_residual >= 0) || !(dual_support >= 0))
+      return seterr(OT_EINVAL, "fallback_residual and dual_support must be >= 0");
+    PlanBase& P = *p->impl;
+    OT_TRY(call_grid(P, g));
+    return P.solve(f0, f1, iters, tol, init_path, init_dual, dual_init, dual_support, fallback_residual, stats,
+                   used_cold);
+  });
 }
 
 ot_status ot_path(ot_plan_t p, float* f, float* m0, float* m1, float* m2) {
-  if (!p) return seterr(OT_EINVAL, "plan is NULL");
-  return p->impl->path(f, m0, m1, m2);
+  return ot_guard([&]() -> ot_status {
+    if (!p) return seterr(OT_EINVAL, "plan is NULL");
+    return p->impl->path(f, m0, m1, m2);
+  });
 }
 
 size_t ot_path_size(ot_plan_t p) { return p ? (size_t)p->impl->B * p->impl->cp.total : 0; }
@@ -399,23 +414,31 @@ size_t ot_dual_size(ot_plan_t p) {
 
 ot_status ot_state_set(ot_plan_t p, const float* f0, const float* f1, const float* x, const float* b,
                        const float* bb) {
-  if (!p) return seterr(OT_EINVAL, "plan is NULL");
-  return p->impl->state_set(f0, f1, x, b, bb);
+  return ot_guard([&]() -> ot_status {
+    if (!p) return seterr(OT_EINVAL, "plan is NULL");
+    return p->impl->state_set(f0, f1, x, b, bb);
+  });
 }
 
 ot_status ot_state_get(ot_plan_t p, float* x, float* b, float* bb) {
-  if (!p) return seterr(OT_EINVAL, "plan is NULL");
-  return p->impl->state_get(x, b, bb);
+  return ot_guard([&]() -> ot_status {
+    if (!p) return seterr(OT_EINVAL, "plan is NULL");
+    return p->impl->state_get(x, b, bb);
+  });
 }
 
 ot_status ot_iterate(ot_plan_t p, int iters, ot_solve_stats* stats) {
-  if (!p) return seterr(OT_EINVAL, "plan is NULL");
-  return p->impl->iterate(iters, stats);
+  return ot_guard([&]() -> ot_status {
+    if (!p) return seterr(OT_EINVAL, "plan is NULL");
+    return p->impl->iterate(iters, stats);
+  });
 }
 
 ot_status ot_project(ot_plan_t p, const float* f0, const float* f1, const float* a, float* x, float* phi) {
-  if (!p) return seterr(OT_EINVAL, "plan is NULL");
-  return p->impl->project(f0, f1, a, x, phi);
+  return ot_guard([&]() -> ot_status {
+    if (!p) return seterr(OT_EINVAL, "plan is NULL");
+    return p->impl->project(f0, f1, a, x, phi);
+  });
 }
 
 static ot_status prox_impl(bool cardano, int count, int ncomp, double sigma, const float* am, const float* af,
@@ -442,19 +465,25 @@ static ot_status prox_impl(bool cardano, int count, int ncomp, double sigma, con
 }
 
 ot_status ot_prox(int count, int ncomp, double sigma, const float* am, const float* af, float* u, float* v) {
-  return prox_impl(false, count, ncomp, sigma, am, af, u, v);
+  return ot_guard([&]() -> ot_status {
+    return prox_impl(false, count, ncomp, sigma, am, af, u, v);
+  });
 }
 
 ot_status ot_prox_cardano(int count, int ncomp, double sigma, const float* am, const float* af, float* u, float* v) {
-  return prox_impl(true, count, ncomp, sigma, am, af, u, v);
+  return ot_guard([&]() -> ot_status {
+    return prox_impl(true, count, ncomp, sigma, am, af, u, v);
+  });
 }
 
 ot_status ot_profile(ot_plan_t p, int iters, double ms[5], const char** names) {
-  if (!p || !ms) return seterr(OT_EINVAL, "plan or ms is NULL");
-  if (names)
-    *names = p->impl->hue ? "hue_fwd,hue_t,hue_inv,update,iteration"
-                          : "rhs_fwd_xt,solve_yc,inv_xt,update,iteration";
-  return p->impl->profile(iters, ms);
+  return ot_guard([&]() -> ot_status {
+    if (!p || !ms) return seterr(OT_EINVAL, "plan or ms is NULL");
+    if (names)
+      *names = p->impl->hue ? "hue_fwd,hue_t,hue_inv,update,iteration"
+                            : "rhs_fwd_xt,solve_yc,inv_xt,update,iteration";
+    return p->impl->profile(iters, ms);
+  });
 }
 
 const char* ot_last_error(void) { return t_err.c_str(); }

@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "abi_guard.h"
 #include "plan_base.h"
 
 namespace dynot {
@@ -214,94 +215,96 @@ ot_status ot_hue_histogram(int npix, const float* h, int bins, float* hist, void
 }
 
 ot_status ot_hue_specify(int npix, const float* h, int bins, const float* target, float* h_out, void* stream) {
-  if (npix < 1 || npix > (1 << 26) || bins < 2 || !h || !target || !h_out)
-    return seterr(OT_EINVAL, "hue_specify: need 1 <= npix <= 2^26, bins >= 2");
-  cudaStream_t st = (cudaStream_t)stream;
-  // exact counts of the target (host: bins values)
-  std::vector<float> tg(bins);
-  CUDA_OK(cudaMemcpyAsync(tg.data(), target, sizeof(float) * bins, cudaMemcpyDefault, st));
-  CUDA_OK(cudaStreamSynchronize(st));
-  // negative entries (an unconverged path can hold a few) count as empty; the rest is renormalised
-  double mass = 0;
-  for (int b = 0; b < bins; ++b) {
-    if (!std::isfinite(tg[b])) return seterr(OT_EINVAL, "hue_specify: non-finite target");
-    mass += tg[b] > 0.f ? (double)tg[b] : 0.0;
-  }
-  if (!(mass > 0)) return seterr(OT_EINVAL, "hue_specify: empty target");
-  std::vector<long long> cnt(bins);
-  std::vector<double> rem(bins);
-  long long tot = 0;
-  for (int b = 0; b < bins; ++b) {
-    const double xb = (tg[b] > 0.f ? (double)tg[b] / mass : 0.0) * npix;
-    cnt[b] = (long long)std::floor(xb);
-    rem[b] = xb - (double)cnt[b];
-    tot += cnt[b];
-  }
-  long long shortfall = npix - tot;
-  if (shortfall < 0 || shortfall > bins) return seterr(OT_EINVAL, "hue_specify: bad target");
-  std::vector<int> ord(bins);
-  for (int b = 0; b < bins; ++b) ord[b] = b;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return rem[a] > rem[c]; });
-  for (long long k = 0; k < shortfall; ++k) cnt[ord[k]] += 1;
-  std::vector<long long> C(bins + 1, 0);
-  for (int b = 0; b < bins; ++b) C[b + 1] = C[b] + cnt[b];
-  // device workspace
-  int m = 1;
-  while (m < npix) m <<= 1;
-  const int D = (npix + 1023) / 1024;
-  const int ncoarse = (npix + D - 1) / D;
-  const int ncand = std::max(ncoarse, 2 * D + 1);
-  DevMem ws;
-  const size_t bytes = sizeof(unsigned long long) * m + 2 * sizeof(double) * npix + sizeof(int) * npix +
-                       sizeof(long long) * (bins + 1) + (sizeof(int) + sizeof(double)) * ncand + 64;
-  CUDA_OK(cudaMalloc(&ws.p, bytes));
-  char* q = (char*)ws.p;
-  auto take = [&](size_t b) { char* r = q; q += (b + 15) & ~size_t(15); return r; };
-  unsigned long long* key = (unsigned long long*)take(sizeof(unsigned long long) * m);
-  double* x = (double*)take(sizeof(double) * npix);
-  double* y = (double*)take(sizeof(double) * npix);
-  int* idx = (int*)take(sizeof(int) * npix);
-  long long* dC = (long long*)take(sizeof(long long) * (bins + 1));
-  int* dsh = (int*)take(sizeof(int) * ncand);
-  double* dcost = (double*)take(sizeof(double) * ncand);
-  // strict order of the source hues
-  k_hue_keys<<<grid_for(m), 256, 0, st>>>(npix, m, h, key);
-  HP_CHECK();
-  for (int k = 2; k <= m; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) k_bitonic<<<grid_for(m), 256, 0, st>>>(key, m, k, j);
-  HP_CHECK();
-  k_sorted_hues<<<grid_for(npix), 256, 0, st>>>(npix, key, h, x, idx);
-  CUDA_OK(cudaMemcpyAsync(dC, C.data(), sizeof(long long) * (bins + 1), cudaMemcpyHostToDevice, st));
-  k_target_hues<<<grid_for(npix), 256, 0, st>>>(npix, bins, dC, y);
-  HP_CHECK();
-  // least-cost cyclic shift: coarse candidates, then the neighbourhood of the best
-  auto best_of = [&](const std::vector<int>& cands, int& best) -> ot_status {
-    CUDA_OK(cudaMemcpyAsync(dsh, cands.data(), sizeof(int) * cands.size(), cudaMemcpyHostToDevice, st));
-    k_shift_costs<<<(unsigned)cands.size(), 256, 0, st>>>(npix, x, y, dsh, dcost);
-    HP_CHECK();
-    std::vector<double> c(cands.size());
-    CUDA_OK(cudaMemcpyAsync(c.data(), dcost, sizeof(double) * c.size(), cudaMemcpyDeviceToHost, st));
+  return ot_guard([&]() -> ot_status {
+    if (npix < 1 || npix > (1 << 26) || bins < 2 || !h || !target || !h_out)
+      return seterr(OT_EINVAL, "hue_specify: need 1 <= npix <= 2^26, bins >= 2");
+    cudaStream_t st = (cudaStream_t)stream;
+    // exact counts of the target (host: bins values)
+    std::vector<float> tg(bins);
+    CUDA_OK(cudaMemcpyAsync(tg.data(), target, sizeof(float) * bins, cudaMemcpyDefault, st));
     CUDA_OK(cudaStreamSynchronize(st));
-    size_t bi = 0;
-    for (size_t k = 1; k < c.size(); ++k)
-      if (c[k] < c[bi]) bi = k;   // candidates are in increasing order: ties go to the smaller shift
-    best = cands[bi];
+    // negative entries (an unconverged path can hold a few) count as empty; the rest is renormalised
+    double mass = 0;
+    for (int b = 0; b < bins; ++b) {
+      if (!std::isfinite(tg[b])) return seterr(OT_EINVAL, "hue_specify: non-finite target");
+      mass += tg[b] > 0.f ? (double)tg[b] : 0.0;
+    }
+    if (!(mass > 0)) return seterr(OT_EINVAL, "hue_specify: empty target");
+    std::vector<long long> cnt(bins);
+    std::vector<double> rem(bins);
+    long long tot = 0;
+    for (int b = 0; b < bins; ++b) {
+      const double xb = (tg[b] > 0.f ? (double)tg[b] / mass : 0.0) * npix;
+      cnt[b] = (long long)std::floor(xb);
+      rem[b] = xb - (double)cnt[b];
+      tot += cnt[b];
+    }
+    long long shortfall = npix - tot;
+    if (shortfall < 0 || shortfall > bins) return seterr(OT_EINVAL, "hue_specify: bad target");
+    std::vector<int> ord(bins);
+    for (int b = 0; b < bins; ++b) ord[b] = b;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return rem[a] > rem[c]; });
+    for (long long k = 0; k < shortfall; ++k) cnt[ord[k]] += 1;
+    std::vector<long long> C(bins + 1, 0);
+    for (int b = 0; b < bins; ++b) C[b + 1] = C[b] + cnt[b];
+    // device workspace
+    int m = 1;
+    while (m < npix) m <<= 1;
+    const int D = (npix + 1023) / 1024;
+    const int ncoarse = (npix + D - 1) / D;
+    const int ncand = std::max(ncoarse, 2 * D + 1);
+    DevMem ws;
+    const size_t bytes = sizeof(unsigned long long) * m + 2 * sizeof(double) * npix + sizeof(int) * npix +
+                         sizeof(long long) * (bins + 1) + (sizeof(int) + sizeof(double)) * ncand + 64;
+    CUDA_OK(cudaMalloc(&ws.p, bytes));
+    char* q = (char*)ws.p;
+    auto take = [&](size_t b) { char* r = q; q += (b + 15) & ~size_t(15); return r; };
+    unsigned long long* key = (unsigned long long*)take(sizeof(unsigned long long) * m);
+    double* x = (double*)take(sizeof(double) * npix);
+    double* y = (double*)take(sizeof(double) * npix);
+    int* idx = (int*)take(sizeof(int) * npix);
+    long long* dC = (long long*)take(sizeof(long long) * (bins + 1));
+    int* dsh = (int*)take(sizeof(int) * ncand);
+    double* dcost = (double*)take(sizeof(double) * ncand);
+    // strict order of the source hues
+    k_hue_keys<<<grid_for(m), 256, 0, st>>>(npix, m, h, key);
+    HP_CHECK();
+    for (int k = 2; k <= m; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) k_bitonic<<<grid_for(m), 256, 0, st>>>(key, m, k, j);
+    HP_CHECK();
+    k_sorted_hues<<<grid_for(npix), 256, 0, st>>>(npix, key, h, x, idx);
+    CUDA_OK(cudaMemcpyAsync(dC, C.data(), sizeof(long long) * (bins + 1), cudaMemcpyHostToDevice, st));
+    k_target_hues<<<grid_for(npix), 256, 0, st>>>(npix, bins, dC, y);
+    HP_CHECK();
+    // least-cost cyclic shift: coarse candidates, then the neighbourhood of the best
+    auto best_of = [&](const std::vector<int>& cands, int& best) -> ot_status {
+      CUDA_OK(cudaMemcpyAsync(dsh, cands.data(), sizeof(int) * cands.size(), cudaMemcpyHostToDevice, st));
+      k_shift_costs<<<(unsigned)cands.size(), 256, 0, st>>>(npix, x, y, dsh, dcost);
+      HP_CHECK();
+      std::vector<double> c(cands.size());
+      CUDA_OK(cudaMemcpyAsync(c.data(), dcost, sizeof(double) * c.size(), cudaMemcpyDeviceToHost, st));
+      CUDA_OK(cudaStreamSynchronize(st));
+      size_t bi = 0;
+      for (size_t k = 1; k < c.size(); ++k)
+        if (c[k] < c[bi]) bi = k;   // candidates are in increasing order: ties go to the smaller shift
+      best = cands[bi];
+      return OT_OK;
+    };
+    std::vector<int> cands;
+    for (int s = 0; s < npix; s += D) cands.push_back(s);
+    int sc = 0;
+    OT_TRY(best_of(cands, sc));
+    cands.clear();
+    for (int k = -D; k <= D; ++k) cands.push_back(((sc + k) % npix + npix) % npix);
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    int s = 0;
+    OT_TRY(best_of(cands, s));
+    k_assign<<<grid_for(npix), 256, 0, st>>>(npix, s, idx, y, h_out);
+    HP_CHECK();
+    CUDA_OK(cudaStreamSynchronize(st));
     return OT_OK;
-  };
-  std::vector<int> cands;
-  for (int s = 0; s < npix; s += D) cands.push_back(s);
-  int sc = 0;
-  OT_TRY(best_of(cands, sc));
-  cands.clear();
-  for (int k = -D; k <= D; ++k) cands.push_back(((sc + k) % npix + npix) % npix);
-  std::sort(cands.begin(), cands.end());
-  cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
-  int s = 0;
-  OT_TRY(best_of(cands, s));
-  k_assign<<<grid_for(npix), 256, 0, st>>>(npix, s, idx, y, h_out);
-  HP_CHECK();
-  CUDA_OK(cudaStreamSynchronize(st));
-  return OT_OK;
+  });
 }
 
 }  // extern "C"
