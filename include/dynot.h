@@ -37,7 +37,9 @@
  * every call returns after its results are in the caller's buffers.
  *
  * Errors: every entry point returns an ot_status; ot_last_error() gives a
- * thread-local message for the last failure on the calling thread.
+ * thread-local message for the last failure on the calling thread.  No C++
+ * exception crosses this interface: a failed host allocation inside a call
+ * returns OT_ENOMEM, any other internal exception OT_ECUDA.
  */
 #ifndef DYNOT_H
 #define DYNOT_H
@@ -56,7 +58,7 @@ typedef enum {
   OT_OK = 0,
   OT_EINVAL = 1,       /* bad argument or unsupported grid */
   OT_EMASS = 2,        /* negative / non-finite density or ||f0||_1 != ||f1||_1 */
-  OT_ENOMEM = 3,       /* device allocation failed */
+  OT_ENOMEM = 3,       /* device or host allocation failed */
   OT_ECUDA = 4,        /* a CUDA call failed (message in ot_last_error) */
   OT_ETIMEOUT = 5,     /* reserved: a device wait exceeded its limit */
   OT_ENUMERIC = 6,     /* NaN or Inf in a residual */
