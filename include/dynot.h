@@ -104,7 +104,10 @@ void ot_grid_hue(ot_grid* g, int bins, int P);
  * Create a plan for `batch` problems of the shape *g, ordered on `cuda_stream`
  * (a cudaStream_t; NULL => the plan creates its own stream).  Allocates the
  * device workspace on the current device.  Returns OT_EINVAL / OT_EUNSUPPORTED
- * for grids the kernels do not cover, OT_ENOMEM when allocation fails.
+ * for grids the kernels do not cover, OT_ENOMEM when allocation fails.  The
+ * kernels cover 2 <= P <= 64, axes of at most 4096 cells (hue: 8192 bins), a
+ * colour axis of at most 4, fewer than 2^31 cells P n1 n2 C per problem and
+ * batch * P <= 65535.
  */
 ot_status ot_plan(const ot_grid* g, int batch, void* cuda_stream, ot_plan_t* out);
 

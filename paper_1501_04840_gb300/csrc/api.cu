@@ -90,6 +90,9 @@ ot_status validate(const ot_grid* gi, int batch, ot_grid& g) {
   if (g.lam_fp64 <= 0) g.lam_fp64 = 64.0;
   if (g.precision < 0 || g.precision > 2) return seterr(OT_EINVAL, "precision invalid");
   const bool hue = g.ndim == 1 && g.bc[0] == OT_BC_PERIODIC;
+  // the kernels address the cells of one problem with 32-bit offsets
+  if ((long long)g.P * g.n[0] * g.n[1] * g.n[2] >= (1LL << 31))
+    return seterr(OT_EUNSUPPORTED, "a problem must have fewer than 2^31 cells (P n1 n2 C)");
   if (!hue) {
     if (g.n[2] > dynot::kMaxC) return seterr(OT_EUNSUPPORTED, "colour axis longer than %d", kMaxC);
     if (g.n[0] < 2) return seterr(OT_EUNSUPPORTED, "n[0] must be >= 2");
@@ -210,6 +213,8 @@ ot_status ot_plan(const ot_grid* gi, int batch, void* cuda_stream, ot_plan_t* ou
 
 namespace {
 ot_status make_plan(const ot_grid& g, int batch, void* cuda_stream, std::unique_ptr<PlanBase>& impl) {
+  // problems x time steps index the third grid dimension of the per-step kernels (at most 65535)
+  if ((long long)batch * g.P > 65535) return seterr(OT_EUNSUPPORTED, "batch * P must be at most 65535");
   if (g.precision == OT_PREC_FP64) impl.reset(new_plan_f64());
   else impl.reset(new_plan_f32());
   PlanBase& P = *impl;

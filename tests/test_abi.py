@@ -63,3 +63,16 @@ def test_invalid_grids_are_rejected_before_any_device_work(lib):
     with pytest.raises(b.OTError) as ei:
         b.Plan(g)
     assert ei.value.status == b.OT_EUNSUPPORTED
+
+
+def test_sizes_beyond_the_kernels_index_range_are_rejected(lib):
+    """Problems of 2^31 cells or more (32-bit in-problem offsets) and batches whose problems x time
+    steps exceed a grid dimension (65535) are refused before any device work."""
+    from paper_1501_04840_gb300 import binding as b
+    g = b.grid([4096, 4096, 4], ["neumann", "neumann", "periodic"], 32)      # 2^31 cells
+    with pytest.raises(b.OTError) as ei:
+        b.Plan(g)
+    assert ei.value.status == b.OT_EUNSUPPORTED
+    with pytest.raises(b.OTError) as ei:
+        b.Plan(b.hue_grid(64, 64), batch=1024)                               # 1024 * 64 > 65535
+    assert ei.value.status == b.OT_EUNSUPPORTED
