@@ -55,6 +55,31 @@ def D_nper_dense(n, scale=None):
     return D
 
 
+def read_golden(name):
+    """Matrices of a text fixture under tests/golden: a header line 'name rows cols', then the rows."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    lines = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    out, i = {}, 0
+    while i < len(lines):
+        key, r, c = lines[i][0], int(lines[i][1]), int(lines[i][2])
+        out[key] = np.array([[float(v) for v in lines[i + 1 + j]] for j in range(r)]).reshape(r, c)
+        i += 1 + r
+    return out
+
+
+def test_dense_builders_match_the_printed_matrices():
+    """The builders above against the section 2 matrices written out by hand at p = 3, n = 4
+    (tests/golden/operators_p3_n4.txt), and Remark 2's colour eigenvalues."""
+    gold = read_golden("operators_p3_n4.txt")
+    np.testing.assert_array_equal(S_p_dense(3), gold["S_p"])
+    np.testing.assert_array_equal(D_p_dense(3), gold["D_p"])
+    np.testing.assert_array_equal(S_nper_dense(4), gold["S_nper"])
+    np.testing.assert_array_equal(D_nper_dense(4), gold["D_nper"])
+    Dc = D_nper_dense(3, scale=1.0)
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(Dc.T @ Dc)), gold["eig_colour_laplacian_3"][0], atol=1e-12)
+
+
 def space_factor(g, k, M):
     """I (x) ... (x) M (x) ... (x) I acting on spatial axis k (x fastest)."""
     out = np.ones((1, 1))
