@@ -69,6 +69,23 @@ def test_specification_to_a_slightly_rotated_histogram_rotates_every_pixel(k):
     assert np.array_equal(hp.hue_bin(out, bins), (hp.hue_bin(h, bins) + k) % bins)
 
 
+def test_exact_counts_by_hand():
+    """Largest remainders, worked by hand: shares 3.5, 2.1, 1.4 of 7 pixels floor to 3, 2, 1 and the one
+    pixel left goes to the largest remainder (bin 0); equal remainders go to the lower bin; negative
+    entries count as empty and the rest is renormalised."""
+    assert hp.exact_counts([0.5, 0.3, 0.2], 7).tolist() == [4, 2, 1]
+    assert hp.exact_counts([1 / 3, 1 / 3, 1 / 3], 4).tolist() == [2, 1, 1]
+    assert hp.exact_counts([0.5, -0.1, 0.6], 11).tolist() == [5, 0, 6]
+    assert hp.exact_counts([0.1, 0.2, 0.3, 0.4], 10).tolist() == [1, 2, 3, 4]
+
+
+def test_target_hues_by_hand():
+    """Counts (2, 0, 1) over 3 bins: the two ranks of bin 0 sit at its quarter points, the one rank of
+    bin 2 at its centre."""
+    np.testing.assert_allclose(hp.target_hues(np.array([2, 0, 1]), 3), [0.25 / 3, 0.75 / 3, 2.5 / 3], rtol=0,
+                               atol=1e-15)
+
+
 def test_shift_search_is_the_exhaustive_minimum_on_small_inputs():
     h = _hues(300, 5)
     bins = 20

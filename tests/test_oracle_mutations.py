@@ -15,10 +15,14 @@ import pytest
 
 import oracle
 import oracle.dynot as od
+import oracle.huepipe as ohp
+import oracle.unet as ou
+import test_oracle_huepipe as thp
 import test_oracle_operators as ops
 import test_oracle_projection as proj
 import test_oracle_prox as prx
 import test_oracle_solve as slv
+import test_oracle_unet as tun
 
 # (function, expression as written in oracle/dynot.py, planted mistake)
 MUTANTS = [
@@ -44,11 +48,38 @@ MUTANTS = [
 ]
 
 
-def _mutant(name, old, new):
-    src = textwrap.dedent(inspect.getsource(getattr(od, name)))
+# the network layers (oracle/unet.py) and the hue pipeline (oracle/huepipe.py)
+UNET_MUTANTS = [
+    ("conv3d", "win = xp[:, 1 + dt:1 + dt + T, 1 + dy:1 + dy + Y, 1 + dx:1 + dx + X, :]",
+     "win = xp[:, 1 - dt:1 - dt + T, 1 - dy:1 - dy + Y, 1 - dx:1 - dx + X, :]"),
+    ("conv3d_dgrad", "win = gp[:, 1 - dt:1 - dt + T, 1 - ddy:1 - ddy + Y, 1 - dxx:1 - dxx + X, :]",
+     "win = gp[:, 1 + dt:1 + dt + T, 1 + ddy:1 + ddy + Y, 1 + dxx:1 + dxx + X, :]"),
+    ("conv3d_wgrad", 'dw[:, k, :] = np.einsum("ntyxo,ntyxc->oc", g, win)', 'dw[:, 26 - k, :] = np.einsum("ntyxo,ntyxc->oc", g, win)'),
+    ("pool_backward", "axis=3) * 0.25", "axis=3)"),
+    ("upsample_backward", ".sum(axis=(3, 5))", ".mean(axis=(3, 5))"),
+    ("relu_backward", "np.asarray(y) > 0", "np.asarray(y) >= 0"),
+    ("mse", "2.0 * d / d.size", "d / d.size"),
+    ("adamw", "p * (1 - lr * wd)", "p * (1 - wd)"),
+    ("adamw", "(m / (1 - b1 ** step))", "m"),
+    ("round_bf16", "(u + 0x7FFF + ((u >> 16) & 1))", "(u + 0x8000)"),
+]
+HUE_MUTANTS = [
+    ("rgb_to_hsv", "(b - r) / safe + 2.0", "(r - b) / safe + 2.0"),
+    ("hsv_to_rgb", "np.choose(i, [t, v, v, q, p, p])", "np.choose(i, [t, v, q, v, p, p])"),
+    ("hue_bin", "np.floor(np.asarray(h, np.float64) * bins)", "np.round(np.asarray(h, np.float64) * bins)"),
+    ("exact_counts", "np.lexsort((np.arange(len(x)), -rem))", "np.lexsort((np.arange(len(x)), rem))"),
+    ("target_hues", "(q - C[b] + 0.5) / counts[b]", "(q - C[b]) / counts[b]"),
+    ("shift_cost", "d = np.minimum(d, 1.0 - d)", "d = d"),
+    ("strict_order", "np.lexsort((np.arange(len(q)), q.astype(np.uint64)))",
+     "np.lexsort((q.astype(np.uint64), np.arange(len(q))))"),
+]
+
+
+def _mutant(name, old, new, mod=od):
+    src = textwrap.dedent(inspect.getsource(getattr(mod, name)))
     assert src.count(old) == 1, "the expression to mutate must occur once in %s" % name
     scope = {}
-    exec(compile(src.replace(old, new), "<mutant of %s>" % name, "exec"), od.__dict__, scope)
+    exec(compile(src.replace(old, new), "<mutant of %s>" % name, "exec"), mod.__dict__, scope)
     return scope[name]
 
 
@@ -83,3 +114,38 @@ def test_pins_reject_planted_mistake(monkeypatch, name, old, new):
     monkeypatch.setattr(oracle, name, fn)    # calls from the pins
     with pytest.raises((AssertionError, FloatingPointError, ValueError)), np.errstate(all="ignore"):
         _pins()
+
+
+def _unet_pins():
+    tun.test_conv3d_matches_scipy_correlate()
+    tun.test_conv3d_gradients_by_finite_differences()
+    tun.test_pool_upsample_adjoint_pairs()
+    tun.test_mse_gradient()
+    tun.test_adamw_closed_forms()
+    tun.test_round_bf16_against_the_format()
+    tun.test_unet_gradients_by_finite_differences()
+
+
+def _hue_pins():
+    thp.test_hsv_against_colorsys()
+    thp.test_exact_counts_by_hand()
+    thp.test_target_hues_by_hand()
+    thp.test_specification_is_exact()
+    thp.test_specification_to_the_source_histogram_keeps_every_bin()
+    for k in (1, 3, 58, 59):
+        thp.test_specification_to_a_slightly_rotated_histogram_rotates_every_pixel(k)
+    thp.test_shift_search_is_the_exhaustive_minimum_on_small_inputs()
+
+
+@pytest.mark.parametrize("name,old,new", UNET_MUTANTS, ids=["%s:%d" % (m[0], i) for i, m in enumerate(UNET_MUTANTS)])
+def test_network_pins_reject_planted_mistake(monkeypatch, name, old, new):
+    monkeypatch.setattr(ou, name, _mutant(name, old, new, ou))
+    with pytest.raises((AssertionError, FloatingPointError, ValueError)), np.errstate(all="ignore"):
+        _unet_pins()
+
+
+@pytest.mark.parametrize("name,old,new", HUE_MUTANTS, ids=["%s:%d" % (m[0], i) for i, m in enumerate(HUE_MUTANTS)])
+def test_hue_pipeline_pins_reject_planted_mistake(monkeypatch, name, old, new):
+    monkeypatch.setattr(ohp, name, _mutant(name, old, new, ohp))
+    with pytest.raises((AssertionError, FloatingPointError, ValueError)), np.errstate(all="ignore"):
+        _hue_pins()

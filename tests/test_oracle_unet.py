@@ -71,6 +71,22 @@ def _net(widths, cin, cout, seed):
     return params
 
 
+def test_adamw_closed_forms():
+    """AdamW (Loshchilov and Hutter, decoupled weight decay) on cases whose update is known in closed form:
+    with zero gradient only the decay acts, p (1 - lr wd); with a constant gradient the bias corrections make
+    m_hat = g and v_hat = g^2 at every step, so each step moves p by -lr g / (|g| + eps) besides the decay."""
+    lr, b1, b2, eps, wd = 1e-2, 0.9, 0.999, 1e-8, 0.1
+    p0 = np.array([1.0, -2.0, 0.5])
+    p, m, v = unet.adamw(p0.copy(), np.zeros(3), np.zeros(3), np.zeros(3), lr, b1, b2, eps, wd, 1)
+    np.testing.assert_allclose(p, p0 * (1 - lr * wd), rtol=0, atol=1e-15)
+    g = np.array([0.3, -4.0, 1e-3])
+    p, m, v = p0.copy(), np.zeros(3), np.zeros(3)
+    for step in range(1, 6):
+        expect = p * (1 - lr * wd) - lr * g / (np.abs(g) + eps)
+        p, m, v = unet.adamw(p, g, m, v, lr, b1, b2, eps, wd, step)
+        np.testing.assert_allclose(p, expect, rtol=1e-12, atol=1e-15)
+
+
 def test_round_bf16_against_the_format():
     # representable values stay, halfway cases go to the even neighbour, 1 + 2^-9 is below halfway
     assert unet.round_bf16(1.0) == 1.0
