@@ -76,3 +76,20 @@ def test_sizes_beyond_the_kernels_index_range_are_rejected(lib):
     with pytest.raises(b.OTError) as ei:
         b.Plan(b.hue_grid(64, 64), batch=1024)                               # 1024 * 64 > 65535
     assert ei.value.status == b.OT_EUNSUPPORTED
+
+
+def test_product_code_never_reaches_the_oracle():
+    """The package and its CUDA sources neither import nor include anything from oracle/ (the oracle is
+    test infrastructure; the product path has no CPU fallback)."""
+    pkg = os.path.join(ROOT, "paper_1501_04840_gb300")
+    offenders = []
+    for dirpath, _, files in os.walk(pkg):
+        for name in files:
+            if not name.endswith((".py", ".cu", ".cuh", ".h")):
+                continue
+            path = os.path.join(dirpath, name)
+            src = open(path).read()
+            if re.search(r"^\s*(import\s+oracle|from\s+oracle\b|from\s+\.\.\s*import\s+oracle)", src, flags=re.M) or \
+                    re.search(r'#include\s+"[^"]*oracle/', src):
+                offenders.append(os.path.relpath(path, ROOT))
+    assert not offenders, offenders
