@@ -7,7 +7,7 @@ CUDA stream.  Activations are channel slices of channels-last bf16 buffers
 from __future__ import annotations
 
 import ctypes
-from ctypes import POINTER, c_float, c_int, c_longlong, c_void_p
+from ctypes import c_float, c_int, c_longlong, c_void_p
 from dataclasses import dataclass
 
 import torch

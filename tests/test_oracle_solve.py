@@ -4,7 +4,6 @@ zero-energy cases f0 = f1 and Remark 1, equivariance under a cyclic colour
 shift and under time reversal, translation of a blob, and the 1D quantile
 closed form of optimal transport on the line (section 1)."""
 import numpy as np
-import pytest
 
 import oracle as o
 
