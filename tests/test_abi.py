@@ -93,3 +93,42 @@ def test_product_code_never_reaches_the_oracle():
                     re.search(r'#include\s+"[^"]*oracle/', src):
                 offenders.append(os.path.relpath(path, ROOT))
     assert not offenders, offenders
+
+
+def test_header_and_library_from_plain_c(lib, tmp_path):
+    """include/dynot.h is plain C99 (pedantic, no warnings), and a C program links against libdynot.so and
+    calls host-only entry points: the ABI version, the grid defaults and an invalid plan's status and
+    message."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    from paper_1501_04840_gb300 import _build
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "dynot.h"
+int main(void) {
+  ot_grid g;
+  ot_plan_t p = 0;
+  if (ot_abi_version() != 1) return 1;
+  ot_grid_rgb(&g, 64, 48, 16);
+  if (g.ndim != 3 || g.n[0] != 64 || g.n[1] != 48 || g.n[2] != 3 || g.P != 16) return 2;
+  g.P = 1;                                   /* below the supported range */
+  if (ot_plan(&g, 1, NULL, &p) != OT_EUNSUPPORTED || p != NULL) return 3;
+  if (strlen(ot_last_error()) == 0) return 4;
+  puts(ot_last_error());
+  return 0;
+}
+''')
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(_build.LIB)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-ldynot", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
+    assert "P must be" in run.stdout
