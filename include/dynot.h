@@ -217,11 +217,14 @@ ot_status ot_profile(ot_plan_t p, int iters, double ms[5], const char** names);
  * no counterpart; this serves callers that cannot call cudaMalloc, such as
  * hosts that reserve all device memory up front or forbid allocation after
  * start-up).  Computes, for `batch` problems of `bins` periodic bins and P
- * time intervals, x = a - A^T (A A^T)^+ (A a - f_b^-) and phi = (A A^T)^+ (A a - f_b^-)
- * exactly as a hue plan's ot_project does, with axis_scale <= 0 meaning `bins`.
+ * time intervals, x = a - A^T (A A^T)^+ (A a - f_b^-) and phi = (A A^T)^+ (A a - f_b^-),
+ * the operator of a hue plan's ot_project (results within 1e-5 of it; eigenvalues
+ * below 64 divided in double as the plan does), with axis_scale == 0 meaning `bins`
+ * (a negative, infinite or NaN axis_scale returns OT_EINVAL).
  * All pointers are DEVICE memory: f0, f1 [batch][bins]; a_packed, x_packed
- * [batch][packed path]; phi [batch][P][bins].  Work is ordered on cuda_stream
- * (NULL = legacy default stream) and the call returns after it finished.
+ * [batch][packed path]; phi [batch][P][bins].  The work is queued on cuda_stream
+ * (NULL = legacy default stream) and the call returns without waiting for it:
+ * order later work and reads of x_packed and phi after it on that stream.
  * Working memory is a fixed file-scope device array of 4,194,304 floats
  * (16 MiB) held by every GPU that loads the library until exit; a call needs
  * batch * 2 * bins * P floats of it and returns OT_EINVAL above that.  The
@@ -335,10 +338,11 @@ ot_status ot_nn_dual_channels(int N, int Y, int X, int P, int to_channels, float
  *   renormalised to mass 1; integer counts by largest remainders).  The paper cites its circular specification method without
  *   printing it; the reading implemented: pixels ranked by (hue, index), rank
  *   r gets target rank (r - s) mod npix, where the cyclic shift s has the least
- *   squared circular distance (searched on the multiples of ceil(npix / 1024),
- *   then around the best), and target rank q in bin b gets the hue
- *   (b + (q - C_b + 1/2) / c_b) / bins.  Allocates its workspace and
- *   synchronises `stream`; 1 <= npix <= 2^26.
+ *   squared circular distance of all npix shifts (exhaustive search, ties to the
+ *   smaller shift; for sorted points on the circle an optimal matching under a
+ *   cost convex in the distance is such a shift), and target rank q in bin b
+ *   gets the hue (b + (q - C_b + 1/2) / c_b) / bins.  Allocates its workspace
+ *   and synchronises `stream`; 1 <= npix <= 2^21 (the search costs npix^2 terms).
  */
 ot_status ot_rgb_to_hsv(int npix, const float* rgb, float* h, float* s, float* v, void* stream);
 ot_status ot_hsv_to_rgb(int npix, const float* h, const float* s, const float* v, float* rgb, void* stream);

@@ -23,16 +23,16 @@ and value.  The steps, as written here:
     paper's transport) is least: with the source hues sorted, x_r, and the
     target hues of the exact counts sorted, y_q, a shift s assigns rank r the
     target rank (r - s) mod npix at cost sum_r d(x_r, y_{(r-s) mod npix})^2,
-    d the distance on the circle of circumference 1.  s minimises it over the
-    multiples of D = ceil(npix / 1024), then over the 2 D + 1 shifts around
-    that one (ties to the smaller shift); on small inputs this is the
-    exhaustive minimum;
+    d the distance on the circle of circumference 1, and s is the minimiser
+    over all npix shifts (ties to the smaller shift);
   - target rank q inside bin b (cumulative count C_b, count c_b) gets the hue
     (b + (q - C_b + 1/2) / c_b) / bins.
   Pinned: the output histogram equals the target counts exactly; the source's
   own histogram keeps every pixel in its bin; a target rotated by up to three bins
-  moves every pixel by that rotation (either way, across the seam); the shift
-  search equals the exhaustive minimum on small inputs.
+  moves every pixel by that rotation (either way, across the seam); the best
+  cyclic shift reaches the optimal assignment over all permutations (Hungarian
+  method) on small inputs; a single bump rotated by k bins on 4096 and more
+  pixels is cut at the rotation, whose shift and cost are known in closed form.
 """
 from __future__ import annotations
 
@@ -103,23 +103,36 @@ def target_hues(counts, bins):
     return (b + (q - C[b] + 0.5) / counts[b]) / bins
 
 
+def circular_sq(x, y):
+    """Squared distance on the circle of circumference 1 between hues x and y (elementwise)."""
+    d = np.abs(x - y)
+    d = np.minimum(d, 1.0 - d)
+    return d * d
+
+
 def shift_cost(x, y, s):
     """sum_r d(x_r, y_{(r - s) mod n})^2 with d the distance on the unit circle."""
-    d = np.abs(x - np.roll(y, s))
-    d = np.minimum(d, 1.0 - d)
-    return float(np.sum(d * d))
+    return float(np.sum(circular_sq(x, np.roll(y, s))))
+
+
+def all_shift_costs(x, y):
+    """shift_cost for every s in [0, n), evaluated in blocks of shifts."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    n = len(x)
+    r = np.arange(n)
+    out = np.empty(n)
+    step = max(1, min(n, (1 << 22) // max(n, 1)))
+    for s0 in range(0, n, step):
+        s = np.arange(s0, min(n, s0 + step))
+        out[s0:s0 + len(s)] = np.sum(circular_sq(x[None, :], y[(r[None, :] - s[:, None]) % n]), axis=1)
+    return out
 
 
 def best_shift(x, y):
-    """Coarse-to-fine minimisation of shift_cost over s in [0, n) (ties to the smaller shift)."""
-    n = len(x)
-    D = -(-n // 1024)
-    coarse = np.arange(0, n, D)
-    costs = np.array([shift_cost(x, y, int(s)) for s in coarse])
-    sc = int(coarse[int(np.argmin(costs))])
-    fine = sorted({(sc + k) % n for k in range(-D, D + 1)})
-    costs = np.array([shift_cost(x, y, s) for s in fine])
-    return int(fine[int(np.argmin(costs))])
+    """The least-cost cyclic shift: the first minimiser of shift_cost over every s in [0, n) (ties go
+    to the smaller shift)."""
+    return int(np.argmin(all_shift_costs(x, y)))
 
 
 def strict_order(h):

@@ -8,9 +8,11 @@
 // index); the target histogram becomes exact integer counts (largest
 // remainders, ties to the lower bin); target rank q in bin b gets the hue
 // (b + (q - C_b + 1/2) / c_b) / bins; the circle is cut at the cyclic shift s of
-// least squared circular distance sum_r d(x_r, y_{(r-s) mod n})^2, searched on
-// the multiples of D = ceil(n / 1024) and then on the 2 D + 1 shifts around the
-// best one (ties to the smaller shift).
+// least squared circular distance sum_r d(x_r, y_{(r-s) mod n})^2 over all n
+// shifts (ties to the smaller shift).  For sorted points on the circle and a
+// cost convex in the circular distance an optimal matching is a cyclic shift of
+// the sorted orders, so this cut is the optimal assignment of the source pixels
+// to the target hues.
 #include "../../include/dynot.h"
 
 #include <cuda_runtime.h>
@@ -137,33 +139,103 @@ __global__ void k_target_hues(int n, int bins, const long long* __restrict__ C, 
   }
 }
 
-// cost[c] = sum_r d(x_r, y_{(r - s_c) mod n})^2 for the candidate shifts s_c, one block per candidate
-__global__ void k_shift_costs(int n, const double* __restrict__ x, const double* __restrict__ y,
-                              const int* __restrict__ shifts, double* __restrict__ cost) {
-  const int s = shifts[blockIdx.x];
-  double acc = 0;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    int q = r - s;
-    if (q < 0) q += n;
-    double d = fabs(x[r] - y[q]);
-    d = fmin(d, 1.0 - d);
-    acc += d * d;
-  }
-  __shared__ double red[32];
+// cost[s] = sum_r d(x_r, y_{(r - s) mod n})^2 for every shift s (exhaustive search).  A block takes
+// kShiftBlock consecutive shifts, kShiftPer per thread (s = s0 + tid + kShiftThreads u), and walks r in
+// tiles of kShiftTile: the tile of x and the window of y that its shifts reach sit in shared memory, x
+// read as a broadcast and y at consecutive addresses across the threads.  The target hue is held as a
+// float pair (hi + lo = y to about 2^-48), so x - y is formed to about one unit in the last place of
+// the difference; the terms of a tile are summed in float, the tiles in double.
+constexpr int kShiftThreads = 256, kShiftPer = 4, kShiftBlock = kShiftThreads * kShiftPer, kShiftTile = 256;
+constexpr int kShiftWin = kShiftTile + kShiftBlock - 1;
+
+__global__ void __launch_bounds__(kShiftThreads) k_shift_costs(int n, const float* __restrict__ xs,
+                                                               const float2* __restrict__ ys,
+                                                               double* __restrict__ cost) {
+  __shared__ float sx[kShiftTile];
+  __shared__ float2 sy[kShiftWin];
+  const int s0 = blockIdx.x * kShiftBlock, tid = threadIdx.x;
+  double acc[kShiftPer];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int u = 0; u < kShiftPer; ++u) acc[u] = 0.0;
+  for (int r0 = 0; r0 < n; r0 += kShiftTile) {
+    const int len = min(kShiftTile, n - r0);
+    __syncthreads();
+    for (int i = tid; i < len; i += kShiftThreads) sx[i] = xs[r0 + i];
+    // window entry i holds y at q = r0 - s0 - (kShiftBlock - 1) + i (mod n)
+    const long long qb = (long long)r0 - s0 - (kShiftBlock - 1);
+    for (int i = tid; i < len + kShiftBlock - 1; i += kShiftThreads) {
+      long long q = (qb + i) % n;
+      if (q < 0) q += n;
+      sy[i] = ys[q];
+    }
+    __syncthreads();
+    float part[kShiftPer];
+#pragma unroll
+    for (int u = 0; u < kShiftPer; ++u) part[u] = 0.f;
+    // thread (tid, u) has shift s = s0 + tid + kShiftThreads u; term r reads sy[r - r0 + kShiftBlock - 1 - (s - s0)]
+    const int wb = kShiftBlock - 1 - tid;
+#pragma unroll 4
+    for (int r = 0; r < len; ++r) {
+      const float xv = sx[r];
+#pragma unroll
+      for (int u = 0; u < kShiftPer; ++u) {
+        const float2 yv = sy[r + wb - kShiftThreads * u];
+        const float e = fabsf((xv - yv.x) - yv.y);
+        const float d = fminf(e, 1.f - e);
+        part[u] = fmaf(d, d, part[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kShiftPer; ++u) acc[u] += (double)part[u];
+  }
+#pragma unroll
+  for (int u = 0; u < kShiftPer; ++u) {
+    const int s = s0 + tid + kShiftThreads * u;
+    if (s < n) cost[s] = acc[u];
+  }
+}
+
+// the first minimiser of cost over [0, n) (ties to the smaller shift), one block
+__global__ void k_argmin_shift(int n, const double* __restrict__ cost, int* __restrict__ best) {
+  double bc = INFINITY;
+  int bs = n;
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    const double c = cost[s];
+    if (c < bc) { bc = c; bs = s; }   // s increases within a thread: the first minimiser is kept
+  }
+  __shared__ double rc[1024];
+  __shared__ int rs[1024];
+  rc[threadIdx.x] = bc;
+  rs[threadIdx.x] = bs;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    cost[blockIdx.x] = t;
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double c2 = rc[threadIdx.x + w];
+      const int s2 = rs[threadIdx.x + w];
+      if (c2 < rc[threadIdx.x] || (c2 == rc[threadIdx.x] && s2 < rs[threadIdx.x])) {
+        rc[threadIdx.x] = c2;
+        rs[threadIdx.x] = s2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *best = rs[0] < n ? rs[0] : 0;
+}
+
+// float source hues of the sorted ranks and the target hues as float pairs
+__global__ void k_shift_inputs(int n, const double* __restrict__ x, const double* __restrict__ y,
+                               float* __restrict__ xs, float2* __restrict__ ys) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    xs[r] = (float)x[r];
+    const float hi = (float)y[r];
+    ys[r] = make_float2(hi, (float)(y[r] - (double)hi));
   }
 }
 
 // rank r receives target rank (r - s) mod n
-__global__ void k_assign(int n, int s, const int* __restrict__ idx, const double* __restrict__ y,
-                         float* __restrict__ out) {
+__global__ void k_assign(int n, const int* __restrict__ shift, const int* __restrict__ idx,
+                         const double* __restrict__ y, float* __restrict__ out) {
+  const int s = *shift;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     int q = r - s;
     if (q < 0) q += n;
@@ -172,6 +244,9 @@ __global__ void k_assign(int n, int s, const int* __restrict__ idx, const double
 }
 
 inline int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152 * 16); }
+
+// the exhaustive shift search costs npix^2 terms (about 0.15 s on one GPU at 2^20 pixels)
+constexpr int kMaxSpecifyPixels = 1 << 21;
 
 }  // namespace
 }  // namespace dynot
@@ -216,8 +291,8 @@ ot_status ot_hue_histogram(int npix, const float* h, int bins, float* hist, void
 
 ot_status ot_hue_specify(int npix, const float* h, int bins, const float* target, float* h_out, void* stream) {
   return ot_guard([&]() -> ot_status {
-    if (npix < 1 || npix > (1 << 26) || bins < 2 || !h || !target || !h_out)
-      return seterr(OT_EINVAL, "hue_specify: need 1 <= npix <= 2^26, bins >= 2");
+    if (npix < 1 || npix > kMaxSpecifyPixels || bins < 2 || !h || !target || !h_out)
+      return seterr(OT_EINVAL, "hue_specify: need 1 <= npix <= 2^21, bins >= 2");
     cudaStream_t st = (cudaStream_t)stream;
     // exact counts of the target (host: bins values)
     std::vector<float> tg(bins);
@@ -250,12 +325,10 @@ ot_status ot_hue_specify(int npix, const float* h, int bins, const float* target
     // device workspace
     int m = 1;
     while (m < npix) m <<= 1;
-    const int D = (npix + 1023) / 1024;
-    const int ncoarse = (npix + D - 1) / D;
-    const int ncand = std::max(ncoarse, 2 * D + 1);
     DevMem ws;
     const size_t bytes = sizeof(unsigned long long) * m + 2 * sizeof(double) * npix + sizeof(int) * npix +
-                         sizeof(long long) * (bins + 1) + (sizeof(int) + sizeof(double)) * ncand + 64;
+                         sizeof(long long) * (bins + 1) + sizeof(float) * npix + sizeof(float2) * npix +
+                         sizeof(double) * npix + 16 * 8 + 64;
     CUDA_OK(cudaMalloc(&ws.p, bytes));
     char* q = (char*)ws.p;
     auto take = [&](size_t b) { char* r = q; q += (b + 15) & ~size_t(15); return r; };
@@ -264,8 +337,10 @@ ot_status ot_hue_specify(int npix, const float* h, int bins, const float* target
     double* y = (double*)take(sizeof(double) * npix);
     int* idx = (int*)take(sizeof(int) * npix);
     long long* dC = (long long*)take(sizeof(long long) * (bins + 1));
-    int* dsh = (int*)take(sizeof(int) * ncand);
-    double* dcost = (double*)take(sizeof(double) * ncand);
+    float* xs = (float*)take(sizeof(float) * npix);
+    float2* ys = (float2*)take(sizeof(float2) * npix);
+    double* dcost = (double*)take(sizeof(double) * npix);
+    int* dbest = (int*)take(sizeof(int));
     // strict order of the source hues
     k_hue_keys<<<grid_for(m), 256, 0, st>>>(npix, m, h, key);
     HP_CHECK();
@@ -276,31 +351,14 @@ ot_status ot_hue_specify(int npix, const float* h, int bins, const float* target
     CUDA_OK(cudaMemcpyAsync(dC, C.data(), sizeof(long long) * (bins + 1), cudaMemcpyHostToDevice, st));
     k_target_hues<<<grid_for(npix), 256, 0, st>>>(npix, bins, dC, y);
     HP_CHECK();
-    // least-cost cyclic shift: coarse candidates, then the neighbourhood of the best
-    auto best_of = [&](const std::vector<int>& cands, int& best) -> ot_status {
-      CUDA_OK(cudaMemcpyAsync(dsh, cands.data(), sizeof(int) * cands.size(), cudaMemcpyHostToDevice, st));
-      k_shift_costs<<<(unsigned)cands.size(), 256, 0, st>>>(npix, x, y, dsh, dcost);
-      HP_CHECK();
-      std::vector<double> c(cands.size());
-      CUDA_OK(cudaMemcpyAsync(c.data(), dcost, sizeof(double) * c.size(), cudaMemcpyDeviceToHost, st));
-      CUDA_OK(cudaStreamSynchronize(st));
-      size_t bi = 0;
-      for (size_t k = 1; k < c.size(); ++k)
-        if (c[k] < c[bi]) bi = k;   // candidates are in increasing order: ties go to the smaller shift
-      best = cands[bi];
-      return OT_OK;
-    };
-    std::vector<int> cands;
-    for (int s = 0; s < npix; s += D) cands.push_back(s);
-    int sc = 0;
-    OT_TRY(best_of(cands, sc));
-    cands.clear();
-    for (int k = -D; k <= D; ++k) cands.push_back(((sc + k) % npix + npix) % npix);
-    std::sort(cands.begin(), cands.end());
-    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
-    int s = 0;
-    OT_TRY(best_of(cands, s));
-    k_assign<<<grid_for(npix), 256, 0, st>>>(npix, s, idx, y, h_out);
+    // least-cost cyclic shift over all npix shifts
+    k_shift_inputs<<<grid_for(npix), 256, 0, st>>>(npix, x, y, xs, ys);
+    HP_CHECK();
+    k_shift_costs<<<(npix + kShiftBlock - 1) / kShiftBlock, kShiftThreads, 0, st>>>(npix, xs, ys, dcost);
+    HP_CHECK();
+    k_argmin_shift<<<1, 1024, 0, st>>>(npix, dcost, dbest);
+    HP_CHECK();
+    k_assign<<<grid_for(npix), 256, 0, st>>>(npix, dbest, idx, y, h_out);
     HP_CHECK();
     CUDA_OK(cudaStreamSynchronize(st));
     return OT_OK;

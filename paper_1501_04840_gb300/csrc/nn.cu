@@ -7,8 +7,10 @@
 // (mma.sync m16n8k16, bf16 inputs, fp32 accumulators): M = voxels,
 // N = output channels, K = 27 taps x input channels.  The data gradient is the
 // same convolution with rotated, transposed weights; the weight gradient is a
-// second implicit GEMM (M = cout, N = cin, K = voxels) per tap, reduced over
-// voxel chunks with fp32 atomics.
+// second implicit GEMM (M = cout, N = cin, K = voxels) per tap: the tiled
+// kernel writes per-block partial sums over voxel chunks that a second kernel
+// adds in a fixed order; the direct fallback for unaligned channel slices
+// reduces with fp32 atomics.
 #include "../../include/dynot.h"
 
 #include <cuda_bf16.h>

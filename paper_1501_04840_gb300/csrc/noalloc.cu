@@ -6,7 +6,8 @@
 // must not trigger the implicit synchronisation an allocation can cause.
 // Such callers cannot create a plan (ot_plan allocates its workspace), so this
 // entry point keeps its working memory in a fixed array that lives in the
-// library's own device image.
+// library's own device image.  The call only queues its kernel on the caller's
+// stream and does not wait for it.
 //
 // The intermediate spectral array lives in kScratchFloats floats of file-scope
 // device memory (16 MiB).  Every GPU that loads this library holds that array
@@ -33,6 +34,7 @@ constexpr size_t kScratchFloats = size_t(1) << 22;  // 16 MiB of float32
 constexpr int kMaxDevices = 64;
 constexpr int kMaxBins = 8192;
 constexpr int kMaxP = 64;
+constexpr float kLamFp64 = 64.f;   // eigenvalues below this are divided in double (the plans' default)
 
 static __device__ __align__(256) float g_noalloc_scratch[kScratchFloats];
 
@@ -124,7 +126,8 @@ __global__ void __launch_bounds__(256) k_hue_project_noalloc(int n, int P, doubl
     h[q] = acc;
   }
   __syncthreads();
-  // DCT-II along t, divide by the eigenvalue (zero mode -> 0), exact inverse
+  // DCT-II along t, divide by the eigenvalue (zero mode -> 0), exact inverse.  Eigenvalues below
+  // lam_fp64 (the hue plan's default threshold of 64) are formed and divided in double, as the plan does.
   for (int slot = tid; slot < n; slot += nt) {
     float v[kMaxP], w[kMaxP];
     for (int t = 0; t < P; ++t) v[t] = h[(size_t)t * n + slot];
@@ -132,7 +135,17 @@ __global__ void __launch_bounds__(256) k_hue_project_noalloc(int n, int P, doubl
       float acc = 0.f;
       for (int t = 0; t < P; ++t) acc += Mt[k * P + t] * v[t];
       const float l = lam[slot] + lamt[k];
-      w[k] = l > 0.f ? acc / l : 0.f;
+      if (!(l > 0.f)) {
+        w[k] = 0.f;
+      } else if (l < kLamFp64) {
+        int j = (slot + 1) / 2;
+        if ((n & 1) == 0 && slot == n - 1) j = n / 2;
+        const double vs = sinpi((double)j / n), vt = sinpi((double)k / (2.0 * P));
+        const double ld = s * s * 4.0 * vs * vs + (double)P * P * 4.0 * vt * vt;
+        w[k] = ld > 0.0 ? (float)((double)acc / ld) : 0.f;
+      } else {
+        w[k] = acc / l;
+      }
     }
     for (int t = 0; t < P; ++t) {
       float acc = 0.f;
@@ -141,17 +154,20 @@ __global__ void __launch_bounds__(256) k_hue_project_noalloc(int n, int P, doubl
     }
   }
   __syncthreads();
-  // inverse real DFT -> phi
+  // inverse real DFT -> phi: frequency j has the slot pair (2j - 1, 2j) and the basis index
+  // i j mod n, which advances by i per frequency
   float* ph = phi + (size_t)b * mlen;
   for (size_t q = tid; q < mlen; q += nt) {
     const int t = (int)(q / n), i = (int)(q % n);
     const float* row = h + (size_t)t * n;
     float acc = row[0];
     const int last = (n & 1) ? n : n - 1;
-    for (int slot = 1; slot < last; ++slot) {
-      const int j = (slot + 1) / 2;
-      const float2 w = cs[(int)(((long long)i * j) % n)];
-      acc += 2.f * row[slot] * ((slot & 1) ? w.x : w.y);
+    int m = 0;
+    for (int slot = 1; slot < last; slot += 2) {
+      m += i;
+      if (m >= n) m -= n;
+      const float2 w = cs[m];
+      acc += 2.f * (row[slot] * w.x + row[slot + 1] * w.y);
     }
     if ((n & 1) == 0) acc += row[n - 1] * ((i & 1) ? -1.f : 1.f);
     ph[q] = acc / (float)n;
@@ -185,6 +201,8 @@ extern "C" ot_status ot_hue_project_noalloc(int bins, int P, int batch, double a
                   "batch * 2 * bins * P = %zu floats exceeds the fixed scratch of %zu floats; "
                   "split the batch into smaller calls",
                   need, kScratchFloats);
+  if (!(axis_scale >= 0.0) || std::isinf(axis_scale))
+    return seterr(OT_EINVAL, "axis_scale must be > 0 (or 0 for the default, bins)");
   const double s = axis_scale > 0 ? axis_scale : (double)bins;
   float* scratch = nullptr;
   ot_status st = scratch_for_current_device(&scratch);
@@ -197,9 +215,7 @@ extern "C" ot_status ot_hue_project_noalloc(int bins, int P, int batch, double a
   }
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   k_hue_project_noalloc<<<batch, 256, smem, stream>>>(bins, P, s, f0, f1, a_packed, x_packed, phi, scratch);
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return seterr(OT_ECUDA, "launch: %s", cudaGetErrorString(e));
-  e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) return seterr(OT_ECUDA, "kernel: %s", cudaGetErrorString(e));
-  return OT_OK;
+  return OT_OK;   // queued on the stream; the caller orders its later work (and reads) after it
 }

@@ -315,6 +315,31 @@ def test_input_validation(ot):
     assert st.iterations == 5
 
 
+@pytest.mark.parametrize("where", ["dual", "path"])
+def test_non_finite_state_is_reported(ot, where):
+    """The detector of non-finite residuals: a NaN planted on the host in the dual (or an Inf in the
+    path) through ot_state_set makes the residual of the next check non-finite, and ot_iterate returns
+    OT_ENUMERIC.  Nothing faults on the device, and the plan stays usable: a finite state set
+    afterwards iterates normally."""
+    plan, g = make_plan(ot, (32, 24, 3), RGB, 6)
+    f0, f1 = random_pair(g, 11)
+    st = _random_state(g, 12)
+    xp = f32(pack_path(g, st.m, st.f))
+    bp = f32(pack_dual(g, st.bm, st.bf))
+    bad_x, bad_b = xp.copy(), bp.copy()
+    if where == "dual":
+        bad_b[bad_b.size // 3] = np.nan
+    else:
+        bad_x[bad_x.size // 2] = np.inf
+    plan.state_set(f32(f0), f32(f1), bad_x, bad_b)
+    with pytest.raises(ot.OTError) as ei:
+        plan.iterate(3)
+    assert ei.value.status == ot.OT_ENUMERIC
+    plan.state_set(f32(f0), f32(f1), xp, bp)
+    out = plan.iterate(3)
+    assert out.iterations == 3 and np.isfinite(out.residual)
+
+
 def test_tolerance_stops_early_and_reports(ot):
     from paper_1501_04840_gb300 import synth
     f0, f1 = synth.rgb_pair(32, 32, 8, 0)

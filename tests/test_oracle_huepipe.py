@@ -86,14 +86,52 @@ def test_target_hues_by_hand():
                                atol=1e-15)
 
 
-def test_shift_search_is_the_exhaustive_minimum_on_small_inputs():
-    h = _hues(300, 5)
-    bins = 20
-    rng = np.random.default_rng(6)
-    target = rng.random(bins)
-    target /= target.sum()
-    order = hp.strict_order(h)
-    x = h[order].astype(np.float64)
-    y = hp.target_hues(hp.exact_counts(target, len(h)), bins)
-    costs = [hp.shift_cost(x, y, s) for s in range(len(h))]
-    assert hp.best_shift(x, y) == int(np.argmin(costs))
+@pytest.mark.parametrize("seed", range(6))
+def test_best_cyclic_shift_is_the_optimal_assignment(seed):
+    """For sorted points on the circle with a cost convex in the circular distance, an optimal matching
+    of two equal-size sets is a cyclic shift of the sorted orders.  The Hungarian method (scipy's
+    linear_sum_assignment) over all permutations pins the shift search: the least-cost cyclic shift
+    reaches the optimal assignment cost."""
+    from scipy.optimize import linear_sum_assignment
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(40, 160))
+    x = np.sort(_hues(n, seed).astype(np.float64))
+    y = np.sort((rng.normal(rng.random(), 0.05 + 0.3 * rng.random(), n)) % 1.0)
+    d = np.abs(x[:, None] - y[None, :])
+    d = np.minimum(d, 1.0 - d)
+    r, c = linear_sum_assignment(d * d)
+    optimal = float(np.sum((d * d)[r, c]))
+    s = hp.best_shift(x, y)
+    assert hp.shift_cost(x, y, s) <= optimal * (1 + 1e-12) + 1e-15
+
+
+def _bump_counts(n, bins, centre=0.97, width=0.03, support=0.1):
+    """Exact counts of a truncated Gaussian bump on the circle (support 0.2 of the circle, across the
+    0 = 1 seam for the default centre)."""
+    c = (np.arange(bins) + 0.5) / bins
+    d = np.abs(c - centre)
+    d = np.minimum(d, 1.0 - d)
+    dens = np.where(d < support, np.exp(-0.5 * (d / width) ** 2), 0.0)
+    return hp.exact_counts(dens / dens.sum(), n)
+
+
+@pytest.mark.parametrize("n,k", [(4096, 1), (4096, 5), (4096, -3), (8192, 2)])
+def test_rotated_bump_is_cut_at_the_rotation(n, k):
+    """A closed-form case on thousands of pixels: the source hues sit at the target hues of their own
+    exact counts, and the target is that histogram turned by k bins.  Every target hue is then a source
+    hue moved by delta = k / bins, and with all mass inside an arc shorter than half the circle the
+    rotation is the optimal transport (on an arc, translation is the monotone and hence optimal map):
+    cost n delta^2.  The sorted target is the sorted source rotated by the m pixels that cross the seam,
+    so the least-cost shift is -m mod n when they wrap forwards (k > 0) and m when backwards (k < 0)."""
+    bins = 90
+    counts = _bump_counts(n, bins)
+    x = hp.target_hues(counts, bins)
+    y = hp.target_hues(np.roll(counts, k), bins)
+    delta = k / bins
+    if k > 0:
+        expect = (n - int(np.sum(x + delta >= 1.0))) % n
+    else:
+        expect = int(np.sum(x + delta < 0.0))
+    s = hp.best_shift(x, y)
+    assert s == expect
+    assert hp.shift_cost(x, y, s) == pytest.approx(n * delta ** 2, rel=1e-12)

@@ -69,7 +69,8 @@ HUE_MUTANTS = [
     ("hue_bin", "np.floor(np.asarray(h, np.float64) * bins)", "np.round(np.asarray(h, np.float64) * bins)"),
     ("exact_counts", "np.lexsort((np.arange(len(x)), -rem))", "np.lexsort((np.arange(len(x)), rem))"),
     ("target_hues", "(q - C[b] + 0.5) / counts[b]", "(q - C[b]) / counts[b]"),
-    ("shift_cost", "d = np.minimum(d, 1.0 - d)", "d = d"),
+    ("circular_sq", "d = np.minimum(d, 1.0 - d)", "d = d"),
+    ("best_shift", "int(np.argmin(all_shift_costs(x, y)))", "int(np.argmin(all_shift_costs(x, y)[:len(x) // 2]))"),
     ("strict_order", "np.lexsort((np.arange(len(q)), q.astype(np.uint64)))",
      "np.lexsort((q.astype(np.uint64), np.arange(len(q))))"),
 ]
@@ -134,7 +135,10 @@ def _hue_pins():
     thp.test_specification_to_the_source_histogram_keeps_every_bin()
     for k in (1, 3, 58, 59):
         thp.test_specification_to_a_slightly_rotated_histogram_rotates_every_pixel(k)
-    thp.test_shift_search_is_the_exhaustive_minimum_on_small_inputs()
+    for seed in range(3):
+        thp.test_best_cyclic_shift_is_the_optimal_assignment(seed)
+    for n, k in ((4096, 1), (4096, -3)):
+        thp.test_rotated_bump_is_cut_at_the_rotation(n, k)
 
 
 @pytest.mark.parametrize("name,old,new", UNET_MUTANTS, ids=["%s:%d" % (m[0], i) for i, m in enumerate(UNET_MUTANTS)])
