@@ -59,10 +59,13 @@ def test_noalloc_matches_plan_projection_twice(env, bins, P, batch):
         # both sides sum the dense real DFT over the bins in float32, each with a rounding error of about
         # eps32 sqrt(bins) relative: 1e-5 up to about 1600 bins, 4 eps32 sqrt(bins) beyond
         assert rel(phi, phi_ref) <= max(1e-5, 4 * EPS32 * np.sqrt(bins))
-        # x = a - A^T phi: the tolerance of the parity tests for this correction
+        # x = a - A^T phi: the tolerance of the parity tests for this correction, plus the difference of
+        # the two phi carried through A^T (||A^T d|| <= sqrt(lam_max) ||d||), which the dense float32
+        # sums over thousands of bins make larger than the FFT-based transforms' ten epsilons
         lam_max = (2 * bins) ** 2 + (2 * P) ** 2
         kappa = np.sqrt(lam_max) * np.linalg.norm(phi_ref) / np.linalg.norm(x_ref)
-        assert rel(x, x_ref) <= 1e-5 + 10 * EPS32 * kappa
+        carried = np.sqrt(lam_max) * np.linalg.norm(phi.astype(np.float64) - phi_ref) / np.linalg.norm(x_ref)
+        assert rel(x, x_ref) <= 1e-5 + 10 * EPS32 * kappa + 1.01 * carried
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(env):
