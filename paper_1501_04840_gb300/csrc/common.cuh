@@ -3,11 +3,14 @@
 // Layout of every cell-aligned array of one problem (batch index b, half-time
 // cell t = 0..P-1, spatial cell s = x + n1*(y + n2*c)):
 //     index = ((b*P + t)*S + s),  S = n1*n2*C.
+// The iteration state (a and the scaled dual b) and the primal output x hold
+// four components per cell, interleaved (one 16-byte vector per cell in FP32):
+// (m_x, m_y, m_c, f) for a and x, (b_mx, b_my, b_mc, b_f) for b.
 // Faces are stored cell-aligned: component k at index of cell s holds the face
 // to the right of s along axis k (between s and s+e_k, wrapping for a periodic
 // axis).  For a Neumann axis the last face (i_k = n_k-1) is a boundary face of
 // the paper's model (section 2: kappa = 1, m absent there) and is kept at zero.
-// f at time (t+1)/P sits at slot t = 0..P-2 of the f array; slot P-1 is zero.
+// f at time (t+1)/P sits in the f component of slot t = 0..P-2; slot P-1 holds zero.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -92,22 +95,42 @@ struct Geo {
   T sigma;              // step 2 of Algorithm 1
 };
 
-template <typename T>
-struct CPtr4 {
-  const T* p[4];
+// Four components of one cell, one aligned vector: float4 in FP32, 32-byte aligned in FP64.
+struct __align__(32) dvec4 {
+  double x, y, z, w;
 };
+template <typename T> struct vec4;
+template <> struct vec4<float> { using type = float4; };
+template <> struct vec4<double> { using type = dvec4; };
+template <typename T> using v4 = typename vec4<T>::type;
 
-// Device pointers of the iteration state of one plan (all cell-aligned).
+template <typename T>
+__host__ __device__ __forceinline__ v4<T> mk4(T a, T b, T c, T d) {
+  v4<T> r;
+  r.x = a; r.y = b; r.z = c; r.w = d;
+  return r;
+}
+template <typename T>
+__host__ __device__ __forceinline__ T cget(const v4<T>& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+// component k of cell i of an interleaved array, as a scalar load
+template <typename T>
+__host__ __device__ __forceinline__ T comp(const v4<T>* p, size_t i, int k) {
+  return reinterpret_cast<const T*>(p)[4 * i + k];
+}
+
+// Device pointers of the iteration state of one plan (all cell-aligned, four components per cell).
 template <typename T>
 struct Arrays {
-  const T* a[4];   // a = x - tau sigma K^T bbar at faces: m_x, m_y, m_c, f
-  const T* b[4];   // scaled dual b: b_mx, b_my, b_mc, b_f (cells)
-  T* an[4];        // next a
-  T* bn[4];        // next b
+  const v4<T>* a;  // a = x - tau sigma K^T bbar at faces: (m_x, m_y, m_c, f)
+  const v4<T>* b;  // scaled dual b: (b_mx, b_my, b_mc, b_f) at cells
+  v4<T>* an;       // next a
+  v4<T>* bn;       // next b
   const T* phi;    // (A A^T)^+ r of this iteration, physical cells
   const T* f0;     // boundary densities (solver units), [b][s]
   const T* f1;
-  T* x[4];         // optional output: x^{r+1} (faces), nullptr when not wanted
+  v4<T>* x;        // optional output: x^{r+1} (faces), nullptr when not wanted
 };
 
 }  // namespace dynot

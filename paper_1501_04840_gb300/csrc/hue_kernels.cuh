@@ -40,7 +40,7 @@ __device__ __forceinline__ T hue_basis(const c2<T>* cs, int n, int slot, int i) 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_hue_fwd(Geo<T> g, CPtr4<T> ap, const T* __restrict__ f0,
+__global__ void __launch_bounds__(256) k_hue_fwd(Geo<T> g, const v4<T>* __restrict__ ap, const T* __restrict__ f0,
                                                  const T* __restrict__ f1, T* __restrict__ hat, HueTables tb) {
   extern __shared__ __align__(16) char smraw[];
   const int t = blockIdx.x, b = blockIdx.y;
@@ -48,14 +48,13 @@ __global__ void __launch_bounds__(256) k_hue_fwd(Geo<T> g, CPtr4<T> ap, const T*
   T* row = (T*)smraw;
   c2<T>* cs = (c2<T>*)(smraw + ((sizeof(T) * n + 15) & ~size_t(15)));
   for (int m = threadIdx.x; m < n; m += blockDim.x) cs[m] = ((const c2<T>*)tb.cs)[m];
-  const T* ax = ap.p[0];
-  const T* af = ap.p[3];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int im = i > 0 ? i - 1 : n - 1;  // periodic
     const size_t i0 = (size_t)(b * P + t) * n + i;
-    T r = g.s1 * (ax[i0] - ax[(size_t)(b * P + t) * n + im]);
-    const T fnext = (t == P - 1) ? f1[(size_t)b * n + i] : af[i0];
-    const T fprev = (t == 0) ? f0[(size_t)b * n + i] : af[i0 - n];
+    const v4<T> av = ap[i0];
+    T r = g.s1 * (av.x - comp<T>(ap, (size_t)(b * P + t) * n + im, 0));
+    const T fnext = (t == P - 1) ? f1[(size_t)b * n + i] : av.w;
+    const T fprev = (t == 0) ? f0[(size_t)b * n + i] : comp<T>(ap, i0 - n, 3);
     r += g.sp * (fnext - fprev);
     row[i] = r;
   }

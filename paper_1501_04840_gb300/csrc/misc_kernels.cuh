@@ -102,12 +102,10 @@ struct Compact {
   }
 };
 
-// internal (T, scaled by inv) <- packed (float)
+// internal (T, four components per cell, scaled by `scale`) <- packed (float)
 template <typename T>
-__global__ void k_unpack_path(Geo<T> g, Compact cp, const float* __restrict__ packed, double scale,
-                              T* x0, T* x1, T* x2, T* x3) {
+__global__ void k_unpack_path(Geo<T> g, Compact cp, const float* __restrict__ packed, double scale, v4<T>* xo) {
   const long long tot = (long long)g.B * g.N;
-  T* xs[4] = {x0, x1, x2, x3};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
     long long r = id;
     const int x = r % g.n1; r /= g.n1;
@@ -115,20 +113,21 @@ __global__ void k_unpack_path(Geo<T> g, Compact cp, const float* __restrict__ pa
     const int c = r % g.C; r /= g.C;
     const int t = r % g.P;
     const int b = (int)(r / g.P);
+    T v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const long long ci = cp.index(k, t, x, y, c);
-      xs[k][id] = ci < 0 ? T(0) : (T)((double)packed[(long long)b * cp.total + ci] * scale);
+      v[k] = ci < 0 ? T(0) : (T)((double)packed[(long long)b * cp.total + ci] * scale);
     }
+    xo[id] = mk4<T>(v[0], v[1], v[2], v[3]);
   }
 }
 
 // packed (float, times scale) <- internal; dst[k] may be separate arrays (stride per problem lenk)
 template <typename T>
-__global__ void k_pack_path(Geo<T> g, Compact cp, const T* x0, const T* x1, const T* x2, const T* x3, double scale,
+__global__ void k_pack_path(Geo<T> g, Compact cp, const v4<T>* xi, double scale,
                             float* __restrict__ packed, float* d0, float* d1, float* d2, float* d3) {
   const long long tot = (long long)g.B * g.N;
-  const T* xs[4] = {x0, x1, x2, x3};
   float* ds[4] = {d0, d1, d2, d3};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
     long long r = id;
@@ -141,7 +140,7 @@ __global__ void k_pack_path(Geo<T> g, Compact cp, const T* x0, const T* x1, cons
     for (int k = 0; k < 4; ++k) {
       const long long ci = cp.index(k, t, x, y, c);
       if (ci < 0) continue;
-      const float v = (float)((double)xs[k][id] * scale);
+      const float v = (float)((double)comp<T>(xi, id, k) * scale);
       if (packed) packed[(long long)b * cp.total + ci] = v;
       if (ds[k]) ds[k][(long long)b * cp.len[k] + ci - cp.off[k]] = v;
     }
@@ -150,7 +149,7 @@ __global__ void k_pack_path(Geo<T> g, Compact cp, const T* x0, const T* x1, cons
 
 // a = x - tau sigma K^T bbar at the right faces (step 1 of Algorithm 1).
 template <typename T>
-__global__ void k_make_a(Geo<T> g, CPtr4<T> x, CPtr4<T> bb, T* a0, T* a1, T* a2, T* a3) {
+__global__ void k_make_a(Geo<T> g, const v4<T>* __restrict__ x, const v4<T>* __restrict__ bb, v4<T>* __restrict__ a) {
   const long long tot = (long long)g.B * g.N;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
     long long r = id;
@@ -165,25 +164,22 @@ __global__ void k_make_a(Geo<T> g, CPtr4<T> x, CPtr4<T> bb, T* a0, T* a1, T* a2,
       int j = ix + 1;
       bool ok = true;
       if (j == g.n1) { ok = g.per1; j = 0; }
-      out[0] = ok ? x.p[0][id] - g.ts * T(0.5) * (bb.p[0][id] + bb.p[0][cidx(g, b, t, j, iy, ic)]) : T(0);
+      out[0] = ok ? comp<T>(x, id, 0) - g.ts * T(0.5) * (comp<T>(bb, id, 0) + comp<T>(bb, cidx(g, b, t, j, iy, ic), 0)) : T(0);
     }
     {
       int j = iy + 1;
       bool ok = true;
       if (j == g.n2) { ok = g.per2; j = 0; }
-      out[1] = ok ? x.p[1][id] - g.ts * T(0.5) * (bb.p[1][id] + bb.p[1][cidx(g, b, t, ix, j, ic)]) : T(0);
+      out[1] = ok ? comp<T>(x, id, 1) - g.ts * T(0.5) * (comp<T>(bb, id, 1) + comp<T>(bb, cidx(g, b, t, ix, j, ic), 1)) : T(0);
     }
     {
       int j = ic + 1;
       bool ok = true;
       if (j == g.C) { ok = g.perc; j = 0; }
-      out[2] = ok ? x.p[2][id] - g.ts * T(0.5) * (bb.p[2][id] + bb.p[2][cidx(g, b, t, ix, iy, j)]) : T(0);
+      out[2] = ok ? comp<T>(x, id, 2) - g.ts * T(0.5) * (comp<T>(bb, id, 2) + comp<T>(bb, cidx(g, b, t, ix, iy, j), 2)) : T(0);
     }
-    out[3] = (t + 1 < g.P) ? x.p[3][id] - g.ts * T(0.5) * (bb.p[3][id] + bb.p[3][cidx(g, b, t + 1, ix, iy, ic)]) : T(0);
-    a0[id] = out[0];
-    a1[id] = out[1];
-    a2[id] = out[2];
-    a3[id] = out[3];
+    out[3] = (t + 1 < g.P) ? comp<T>(x, id, 3) - g.ts * T(0.5) * (comp<T>(bb, id, 3) + comp<T>(bb, cidx(g, b, t + 1, ix, iy, ic), 3)) : T(0);
+    a[id] = mk4<T>(out[0], out[1], out[2], out[3]);
   }
 }
 
@@ -197,8 +193,8 @@ __global__ void k_make_a(Geo<T> g, CPtr4<T> x, CPtr4<T> bb, T* a0, T* a1, T* a2,
 // path lies anywhere in the subdifferential of J at 0, which this formula does
 // not predict).
 template <typename T>
-__global__ void k_dual_init(Geo<T> g, CPtr4<T> x, const T* __restrict__ f0, const T* __restrict__ f1, T inv_sigma,
-                            T vmin, T wmax, T vsup, T* b0, T* b1, T* b2, T* b3) {
+__global__ void k_dual_init(Geo<T> g, const v4<T>* __restrict__ x, const T* __restrict__ f0, const T* __restrict__ f1,
+                            T inv_sigma, T vmin, T wmax, T vsup, v4<T>* __restrict__ bo) {
   const long long tot = (long long)g.B * g.N;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
     long long r = id;
@@ -209,14 +205,14 @@ __global__ void k_dual_init(Geo<T> g, CPtr4<T> x, const T* __restrict__ f0, cons
     const int b = (int)(r / g.P);
     // left faces: the right face of the previous cell (wrapping on periodic axes, zero on Neumann ones)
     T left[3];
-    left[0] = ix > 0 ? x.p[0][cidx(g, b, t, ix - 1, iy, ic)] : (g.per1 ? x.p[0][cidx(g, b, t, g.n1 - 1, iy, ic)] : T(0));
-    left[1] = iy > 0 ? x.p[1][cidx(g, b, t, ix, iy - 1, ic)] : (g.per2 ? x.p[1][cidx(g, b, t, ix, g.n2 - 1, ic)] : T(0));
-    left[2] = ic > 0 ? x.p[2][cidx(g, b, t, ix, iy, ic - 1)] : (g.perc ? x.p[2][cidx(g, b, t, ix, iy, g.C - 1)] : T(0));
+    left[0] = ix > 0 ? comp<T>(x, cidx(g, b, t, ix - 1, iy, ic), 0) : (g.per1 ? comp<T>(x, cidx(g, b, t, g.n1 - 1, iy, ic), 0) : T(0));
+    left[1] = iy > 0 ? comp<T>(x, cidx(g, b, t, ix, iy - 1, ic), 1) : (g.per2 ? comp<T>(x, cidx(g, b, t, ix, g.n2 - 1, ic), 1) : T(0));
+    left[2] = ic > 0 ? comp<T>(x, cidx(g, b, t, ix, iy, ic - 1), 2) : (g.perc ? comp<T>(x, cidx(g, b, t, ix, iy, g.C - 1), 2) : T(0));
     T u[3];
-    for (int k = 0; k < 3; ++k) u[k] = T(0.5) * (left[k] + x.p[k][id]);   // right faces are zero where absent
+    for (int k = 0; k < 3; ++k) u[k] = T(0.5) * (left[k] + comp<T>(x, id, k));   // right faces are zero where absent
     const size_t s = (size_t)b * g.S + ix + (size_t)g.n1 * (iy + (size_t)g.n2 * ic);
-    const T fl = t == 0 ? f0[s] : x.p[3][cidx(g, b, t - 1, ix, iy, ic)];
-    const T fr = t == g.P - 1 ? f1[s] : x.p[3][id];
+    const T fl = t == 0 ? f0[s] : comp<T>(x, cidx(g, b, t - 1, ix, iy, ic), 3);
+    const T fr = t == g.P - 1 ? f1[s] : comp<T>(x, id, 3);
     const T vraw = T(0.5) * (fl + fr);
     const T v = max(vraw, vmin);
     const T on = vraw >= vsup ? T(1) : T(0);
@@ -224,10 +220,8 @@ __global__ void k_dual_init(Geo<T> g, CPtr4<T> x, const T* __restrict__ f0, cons
     const T w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     const T lim = w2 > wmax * wmax ? wmax / sqrt(w2) : T(1);
     for (int k = 0; k < 3; ++k) w[k] *= lim;
-    b0[id] = w[0] * inv_sigma;
-    b1[id] = w[1] * inv_sigma;
-    b2[id] = w[2] * inv_sigma;
-    b3[id] = -T(0.5) * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]) * inv_sigma;
+    bo[id] = mk4<T>(w[0] * inv_sigma, w[1] * inv_sigma, w[2] * inv_sigma,
+                    -T(0.5) * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]) * inv_sigma);
   }
 }
 
@@ -243,8 +237,7 @@ __global__ void k_correct(Geo<T> g, Arrays<T> A) {
     const int t = r % g.P;
     const int b = (int)(r / g.P);
     CellCtx<T> cc{g, A, b};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) A.x[k][id] = cc.xr(k, t, ix, iy, ic);
+    A.x[id] = mk4<T>(cc.xr(0, t, ix, iy, ic), cc.xr(1, t, ix, iy, ic), cc.xr(2, t, ix, iy, ic), cc.xr(3, t, ix, iy, ic));
   }
 }
 
@@ -266,6 +259,26 @@ template <typename To, typename Ti>
 __global__ void k_convert(long long n, const Ti* __restrict__ in, To* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = (To)in[i];
+}
+
+// component k of an interleaved array <-> a plain float array of n cells
+template <typename T>
+__global__ void k_comp_in(long long n, const float* __restrict__ in, v4<T>* __restrict__ out, int k) {
+  T* o = reinterpret_cast<T*>(out);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    o[4 * i + k] = (T)in[i];
+}
+template <typename T>
+__global__ void k_comp_out(long long n, const v4<T>* __restrict__ in, int k, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)comp<T>(in, i, k);
+}
+// component k of bbar = 2 b - bprev, formed in T
+template <typename T>
+__global__ void k_bbar_out(long long n, const v4<T>* __restrict__ b, const v4<T>* __restrict__ bprev, int k,
+                           float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)(T(2) * comp<T>(b, i, k) - comp<T>(bprev, i, k));
 }
 
 template <bool CARDANO>

@@ -58,7 +58,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // --------------------------------------------------------------------------
 // kernel selection
 // --------------------------------------------------------------------------
-template <typename T> using KA = void (*)(Geo<T>, CPtr4<T>, const T*, const T*, T*, XtTables, int);
+template <typename T> using KA = void (*)(Geo<T>, const v4<T>*, const T*, const T*, T*, XtTables, int);
 template <typename T> using KC = void (*)(Geo<T>, const T*, T*, XtTables, int);
 template <typename T> using KB = void (*)(Geo<T>, T*, YcTables, int);
 template <typename T> using KH = void (*)(Geo<T>, T*, HueTables);
@@ -137,11 +137,11 @@ template <typename T>
 struct Plan final : PlanBase {
   Geo<T> g{};
   DevMem mem;           // one allocation for every array
-  T* a[2][4]{};
-  T* b[2][4]{};
+  v4<T>* a[2]{};        // a = x - tau sigma K^T bbar, two buffers (current and next)
+  v4<T>* b[2]{};        // scaled dual b, two buffers
   T* phi = nullptr;
   T* hat = nullptr;
-  T* x[4]{};
+  v4<T>* x = nullptr;   // primal output x of the last check
   T* f0n = nullptr;
   T* f1n = nullptr;
   float* stage = nullptr;   // float staging: 2*B*S inputs, then path packing
@@ -225,13 +225,11 @@ struct Plan final : PlanBase {
     CUDA_OK(cudaMalloc(&mem.p, bytes));
     char* q = (char*)mem.p;
     auto take = [&](size_t nb) { char* r = q; q += rnd16(nb); return r; };
-    for (int i = 0; i < 2; ++i)
-      for (int k = 0; k < 4; ++k) a[i][k] = (T*)take(cells * sizeof(T));
-    for (int i = 0; i < 2; ++i)
-      for (int k = 0; k < 4; ++k) b[i][k] = (T*)take(cells * sizeof(T));
+    for (int i = 0; i < 2; ++i) a[i] = (v4<T>*)take(cells * sizeof(v4<T>));
+    for (int i = 0; i < 2; ++i) b[i] = (v4<T>*)take(cells * sizeof(v4<T>));
     phi = (T*)take(cells * sizeof(T));
     hat = (T*)take(cells * sizeof(T));
-    for (int k = 0; k < 4; ++k) x[k] = (T*)take(cells * sizeof(T));
+    x = (v4<T>*)take(cells * sizeof(v4<T>));
     f0n = (T*)take((size_t)B * S * sizeof(T));
     f1n = (T*)take((size_t)B * S * sizeof(T));
     stage = (float*)take(stage_floats * sizeof(float));
@@ -265,8 +263,7 @@ struct Plan final : PlanBase {
     if (cands.size() == 1) return OT_OK;
     // a state on which the prox takes its Newton branch: b_f = 1, b_m = 0.5, a = phi = 0
     const long long cells = (long long)B * N;
-    for (int k = 0; k < 4; ++k)
-      k_fill<T><<<grid1d(cells), 256, 0, st>>>(cells, k == 3 ? T(1) : T(0.5), b[0][k]);
+    k_fill<v4<T>><<<grid1d(cells), 256, 0, st>>>(cells, mk4<T>(T(0.5), T(0.5), T(0.5), T(1)), b[0]);
     CUDA_OK(cudaGetLastError());
     float best = 1e30f;
     for (int c : cands) {
@@ -286,11 +283,10 @@ struct Plan final : PlanBase {
     }
     tc = tune_tc;
     // clear both buffer sets again
-    for (int i = 0; i < 2; ++i)
-      for (int k = 0; k < 4; ++k) {
-        CUDA_OK(cudaMemsetAsync(a[i][k], 0, (size_t)B * N * sizeof(T), st));
-        CUDA_OK(cudaMemsetAsync(b[i][k], 0, (size_t)B * N * sizeof(T), st));
-      }
+    for (int i = 0; i < 2; ++i) {
+      CUDA_OK(cudaMemsetAsync(a[i], 0, (size_t)B * N * sizeof(v4<T>), st));
+      CUDA_OK(cudaMemsetAsync(b[i], 0, (size_t)B * N * sizeof(v4<T>), st));
+    }
     return OT_OK;
   }
   int tune_tc = 0;
@@ -500,19 +496,17 @@ struct Plan final : PlanBase {
 
   Arrays<T> arrays(int p, bool wx) const {
     Arrays<T> A{};
-    for (int k = 0; k < 4; ++k) {
-      A.a[k] = a[p][k];
-      A.b[k] = b[p][k];
-      A.an[k] = a[1 - p][k];
-      A.bn[k] = b[1 - p][k];
-      A.x[k] = wx ? x[k] : nullptr;
-    }
+    A.a = a[p];
+    A.b = b[p];
+    A.an = a[1 - p];
+    A.bn = b[1 - p];
+    A.x = wx ? x : nullptr;
     A.phi = phi;
     A.f0 = f0n;
     A.f1 = f1n;
     return A;
   }
-  CPtr4<T> aptr(int p) const { return CPtr4<T>{{a[p][0], a[p][1], a[p][2], a[p][3]}}; }
+  const v4<T>* aptr(int p) const { return a[p]; }
 
   // ---- the Poisson solve phi = (A A^T)^+ (A a - f_b^-) for a in buffer p
   void enqueue_poisson(int p, cudaEvent_t* evs) {
@@ -798,17 +792,15 @@ struct Plan final : PlanBase {
   ot_status unpack_x(const float* packed) {
     const size_t n = (size_t)B * cp.total;
     CUDA_OK(cudaMemcpyAsync(stage, packed, n * sizeof(float), cudaMemcpyDefault, st));
-    k_unpack_path<T><<<grid1d((long long)B * N), 256, 0, st>>>(g, cp, stage, 1.0, x[0], x[1], x[2], x[3]);
+    k_unpack_path<T><<<grid1d((long long)B * N), 256, 0, st>>>(g, cp, stage, 1.0, x);
     CUDA_OK(cudaGetLastError());
     return OT_OK;
   }
 
   ot_status cold_start() {
-    for (int k = 0; k < 4; ++k) {
-      CUDA_OK(cudaMemsetAsync(a[0][k], 0, (size_t)B * N * sizeof(T), st));
-      CUDA_OK(cudaMemsetAsync(b[0][k], 0, (size_t)B * N * sizeof(T), st));
-      CUDA_OK(cudaMemsetAsync(b[1][k], 0, (size_t)B * N * sizeof(T), st));
-    }
+    CUDA_OK(cudaMemsetAsync(a[0], 0, (size_t)B * N * sizeof(v4<T>), st));
+    CUDA_OK(cudaMemsetAsync(b[0], 0, (size_t)B * N * sizeof(v4<T>), st));
+    CUDA_OK(cudaMemsetAsync(b[1], 0, (size_t)B * N * sizeof(v4<T>), st));
     par = 0;
     have_x = false;
     return OT_OK;
@@ -830,14 +822,13 @@ struct Plan final : PlanBase {
         g1.B = 1;
         const size_t off = (size_t)bi * N;
         k_unpack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, stage + (size_t)bi * cp.total, 1.0 / out_scale[bi],
-                                                    x[0] + off, x[1] + off, x[2] + off, x[3] + off);
+                                                    x + off);
         CUDA_OK(cudaGetLastError());
       }
       const long long cells = (long long)B * N;
       if (init_dual) {
         OT_TRY(load_dual(init_dual, b[0]));
-        for (int k = 0; k < 4; ++k)
-          CUDA_OK(cudaMemcpyAsync(b[1][k], b[0][k], cells * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        CUDA_OK(cudaMemcpyAsync(b[1], b[0], cells * sizeof(v4<T>), cudaMemcpyDeviceToDevice, st));
       } else if (dual_init) {
         // the domain's diameter: extent n_k / scale_k per axis, half of it on periodic axes
         double diam2 = 0;
@@ -845,17 +836,13 @@ struct Plan final : PlanBase {
           const double e = grid.n[k] / grid.axis_scale[k] * (grid.bc[k] == OT_BC_PERIODIC ? 0.5 : 1.0);
           diam2 += e * e;
         }
-        k_dual_init<T><<<grid1d(cells), 256, 0, st>>>(g, CPtr4<T>{{x[0], x[1], x[2], x[3]}}, f0n, f1n,
-                                                      T(1.0 / grid.sigma), T(1e-3), T(std::sqrt(diam2)),
-                                                      T(dual_support), b[0][0], b[0][1], b[0][2], b[0][3]);
+        k_dual_init<T><<<grid1d(cells), 256, 0, st>>>(g, x, f0n, f1n, T(1.0 / grid.sigma), T(1e-3),
+                                                      T(std::sqrt(diam2)), T(dual_support), b[0]);
         CUDA_OK(cudaGetLastError());
-        for (int k = 0; k < 4; ++k)
-          CUDA_OK(cudaMemcpyAsync(b[1][k], b[0][k], cells * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        CUDA_OK(cudaMemcpyAsync(b[1], b[0], cells * sizeof(v4<T>), cudaMemcpyDeviceToDevice, st));
       }
       // a = x0 - tau sigma K^T bbar0 (bbar0 = b0)
-      k_make_a<T><<<grid1d(cells), 256, 0, st>>>(g, CPtr4<T>{{x[0], x[1], x[2], x[3]}},
-                                                CPtr4<T>{{b[0][0], b[0][1], b[0][2], b[0][3]}}, a[0][0], a[0][1],
-                                                a[0][2], a[0][3]);
+      k_make_a<T><<<grid1d(cells), 256, 0, st>>>(g, x, b[0], a[0]);
       CUDA_OK(cudaGetLastError());
     }
     return drive(iters, tol, grid.check_every, stats, init ? fallback : 0.0, used_cold);
@@ -892,8 +879,8 @@ struct Plan final : PlanBase {
       if (!ds[k]) continue;
       float* dd[4] = {nullptr, nullptr, nullptr, nullptr};
       dd[k] = stage;
-      k_pack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, x[0] + off, x[1] + off, x[2] + off, x[3] + off,
-                                                out_scale[bi], nullptr, dd[0], dd[1], dd[2], dd[3]);
+      k_pack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, x + off, out_scale[bi], nullptr, dd[0], dd[1], dd[2],
+                                                dd[3]);
       CUDA_OK(cudaGetLastError());
       CUDA_OK(cudaMemcpyAsync(ds[k], stage, (size_t)cp.len[k] * sizeof(float), cudaMemcpyDefault, st));
       CUDA_OK(cudaStreamSynchronize(st));
@@ -913,8 +900,8 @@ struct Plan final : PlanBase {
         const size_t off = (size_t)bi * N;
         float* dd[4] = {nullptr, nullptr, nullptr, nullptr};
         dd[k] = stage + (size_t)bi * cp.len[k];
-        k_pack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, x[0] + off, x[1] + off, x[2] + off, x[3] + off,
-                                                  out_scale[bi], nullptr, dd[0], dd[1], dd[2], dd[3]);
+        k_pack_path<T><<<grid1d(N), 256, 0, st>>>(g1, cp, x + off, out_scale[bi], nullptr, dd[0], dd[1], dd[2],
+                                                  dd[3]);
         CUDA_OK(cudaGetLastError());
       }
       CUDA_OK(cudaMemcpyAsync(ds[k], stage, (size_t)B * cp.len[k] * sizeof(float), cudaMemcpyDefault, st));
@@ -930,21 +917,17 @@ struct Plan final : PlanBase {
     OT_TRY(unpack_x(xp));
     const long long cells = (long long)B * N;
     // b -> b[0]; bbar -> b[1] temporarily
-    for (int k = 0; k < 4; ++k) {
-      CUDA_OK(cudaMemsetAsync(b[0][k], 0, cells * sizeof(T), st));
-      CUDA_OK(cudaMemsetAsync(b[1][k], 0, cells * sizeof(T), st));
-    }
+    CUDA_OK(cudaMemsetAsync(b[0], 0, cells * sizeof(v4<T>), st));
+    CUDA_OK(cudaMemsetAsync(b[1], 0, cells * sizeof(v4<T>), st));
     OT_TRY(load_dual(bp, b[0]));
     if (bbp) OT_TRY(load_dual(bbp, b[1]));
-    else for (int k = 0; k < 4; ++k) CUDA_OK(cudaMemcpyAsync(b[1][k], b[0][k], cells * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    else CUDA_OK(cudaMemcpyAsync(b[1], b[0], cells * sizeof(v4<T>), cudaMemcpyDeviceToDevice, st));
     // a[0] = x - tau sigma K^T bbar
-    k_make_a<T><<<grid1d(cells), 256, 0, st>>>(g, CPtr4<T>{{x[0], x[1], x[2], x[3]}},
-                                              CPtr4<T>{{b[1][0], b[1][1], b[1][2], b[1][3]}}, a[0][0], a[0][1],
-                                              a[0][2], a[0][3]);
+    k_make_a<T><<<grid1d(cells), 256, 0, st>>>(g, x, b[1], a[0]);
     CUDA_OK(cudaGetLastError());
-    // keep 2 b - bbar in b[1] so that bbar = 2 b[par] - b[1 - par] holds
-    for (int k = 0; k < 4; ++k)
-      k_axpby<T><<<grid1d(cells), 256, 0, st>>>(cells, T(2), b[0][k], T(-1), b[1][k], b[1][k]);
+    // keep 2 b - bbar in b[1] so that bbar = 2 b[par] - b[1 - par] holds (all four components)
+    k_axpby<T><<<grid1d(4 * cells), 256, 0, st>>>(4 * cells, T(2), (const T*)b[0], T(-1), (const T*)b[1],
+                                                    (T*)b[1]);
     CUDA_OK(cudaGetLastError());
     par = 0;
     have_x = true;
@@ -953,15 +936,15 @@ struct Plan final : PlanBase {
   }
 
   // packed dual (float, d+1 components of B*N cells... laid out problem-major) -> internal
-  ot_status load_dual(const float* src, T* const* dst) {
+  ot_status load_dual(const float* src, v4<T>* dst) {
     const long long cells = (long long)B * N;
     // packed dual: per problem (d+1) components of N cells
     std::vector<int> comp = comps();
     CUDA_OK(cudaMemcpyAsync(stage, src, (size_t)B * (d + 1) * N * sizeof(float), cudaMemcpyDefault, st));
     for (int bi = 0; bi < B; ++bi)
       for (int j = 0; j <= d; ++j) {
-        k_convert<T, float><<<grid1d(N), 256, 0, st>>>(N, stage + ((size_t)bi * (d + 1) + j) * N,
-                                                       dst[comp[j]] + (size_t)bi * N);
+        k_comp_in<T><<<grid1d(N), 256, 0, st>>>(N, stage + ((size_t)bi * (d + 1) + j) * N, dst + (size_t)bi * N,
+                                                comp[j]);
       }
     CUDA_OK(cudaGetLastError());
     (void)cells;
@@ -978,8 +961,7 @@ struct Plan final : PlanBase {
     const long long cells = (long long)B * N;
     if (xp) {
       if (!have_x) return seterr(OT_EINVAL, "x is not available: run ot_iterate first");
-      k_pack_path<T><<<grid1d(cells), 256, 0, st>>>(g, cp, x[0], x[1], x[2], x[3], 1.0, stage, nullptr, nullptr,
-                                                   nullptr, nullptr);
+      k_pack_path<T><<<grid1d(cells), 256, 0, st>>>(g, cp, x, 1.0, stage, nullptr, nullptr, nullptr, nullptr);
       CUDA_OK(cudaGetLastError());
       CUDA_OK(cudaMemcpyAsync(xp, stage, (size_t)B * cp.total * sizeof(float), cudaMemcpyDefault, st));
       CUDA_OK(cudaStreamSynchronize(st));
@@ -993,12 +975,10 @@ struct Plan final : PlanBase {
           const size_t off = (size_t)bi * N;
           float* o = stage + ((size_t)bi * (d + 1) + j) * N;
           if (which == 0) {
-            k_convert<float, T><<<grid1d(N), 256, 0, st>>>(N, b[par][comp[j]] + off, o);
+            k_comp_out<T><<<grid1d(N), 256, 0, st>>>(N, b[par] + off, comp[j], o);
           } else {
             // bbar = 2 b[par] - b[1-par], computed in T then converted
-            k_axpby<T><<<grid1d(N), 256, 0, st>>>(N, T(2), b[par][comp[j]] + off, T(-1),
-                                                   b[1 - par][comp[j]] + off, hat + off);
-            k_convert<float, T><<<grid1d(N), 256, 0, st>>>(N, hat + off, o);
+            k_bbar_out<T><<<grid1d(N), 256, 0, st>>>(N, b[par] + off, b[1 - par] + off, comp[j], o);
           }
         }
       CUDA_OK(cudaGetLastError());
@@ -1017,14 +997,12 @@ struct Plan final : PlanBase {
     OT_TRY(unpack_x(ap));
     const long long cells = (long long)B * N;
     // a[0] <- unpacked a (stored in x), run the Poisson solve, then x = a - A^T phi
-    for (int k = 0; k < 4; ++k)
-      CUDA_OK(cudaMemcpyAsync(a[0][k], x[k], cells * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    CUDA_OK(cudaMemcpyAsync(a[0], x, cells * sizeof(v4<T>), cudaMemcpyDeviceToDevice, st));
     enqueue_poisson(0, nullptr);
     Arrays<T> A = arrays(0, true);
     k_correct<T><<<grid1d(cells), 256, 0, st>>>(g, A);
     CUDA_OK(cudaGetLastError());
-    k_pack_path<T><<<grid1d(cells), 256, 0, st>>>(g, cp, x[0], x[1], x[2], x[3], 1.0, stage, nullptr, nullptr,
-                                                 nullptr, nullptr);
+    k_pack_path<T><<<grid1d(cells), 256, 0, st>>>(g, cp, x, 1.0, stage, nullptr, nullptr, nullptr, nullptr);
     CUDA_OK(cudaGetLastError());
     CUDA_OK(cudaMemcpyAsync(xp, stage, (size_t)B * cp.total * sizeof(float), cudaMemcpyDefault, st));
     if (phip) {

@@ -156,18 +156,18 @@ struct CellCtx {
     if (k == 0) {
       int x1 = x + 1;
       if (x1 == g.n1) { if (!g.per1) return T(0); x1 = 0; }
-      return A.a[0][i0] + g.s1 * (A.phi[cidx(g, b, t, x1, y, c)] - A.phi[i0]);
+      return comp<T>(A.a, i0, 0) + g.s1 * (A.phi[cidx(g, b, t, x1, y, c)] - A.phi[i0]);
     } else if (k == 1) {
       int y1 = y + 1;
       if (y1 == g.n2) { if (!g.per2) return T(0); y1 = 0; }
-      return A.a[1][i0] + g.s2 * (A.phi[cidx(g, b, t, x, y1, c)] - A.phi[i0]);
+      return comp<T>(A.a, i0, 1) + g.s2 * (A.phi[cidx(g, b, t, x, y1, c)] - A.phi[i0]);
     } else if (k == 2) {
       int c1 = c + 1;
       if (c1 == g.C) { if (!g.perc) return T(0); c1 = 0; }
-      return A.a[2][i0] + g.sc * (A.phi[cidx(g, b, t, x, y, c1)] - A.phi[i0]);
+      return comp<T>(A.a, i0, 2) + g.sc * (A.phi[cidx(g, b, t, x, y, c1)] - A.phi[i0]);
     } else {
       if (t == g.P - 1) return T(0);
-      return A.a[3][i0] + g.sp * (A.phi[cidx(g, b, t + 1, x, y, c)] - A.phi[i0]);
+      return comp<T>(A.a, i0, 3) + g.sp * (A.phi[cidx(g, b, t + 1, x, y, c)] - A.phi[i0]);
     }
   }
   // x^{r+1} at the left face = right face of the previous cell (wrapping), or the boundary value
@@ -203,9 +203,8 @@ struct CellCtx {
     kx[2] = T(0.5) * (xl(2, t, x, y, c) + xrr[2]);
     kx[3] = T(0.5) * (xl(3, t, x, y, c) + xrr[3]);
     const size_t i0 = cidx(g, b, t, x, y, c);
-    T bo[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) bo[k] = A.b[k][i0];
+    const v4<T> bv = A.b[i0];
+    const T bo[4] = {bv.x, bv.y, bv.z, bv.w};
     const T am0 = kx[0] + bo[0], am1 = kx[1] + bo[1], am2 = kx[2] + bo[2], af = kx[3] + bo[3];
     prox_cell<T>(am0, am1, am2, af, g.sigma, T(1) / g.sigma, U0, U1, U2, V);
     bn[0] = am0 - U0;
@@ -280,19 +279,15 @@ __global__ void __launch_bounds__(128) k_update(Geo<T> g, Arrays<T> A, double* _
     } else {
       an[3] = T(0);
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      A.an[k][i0] = an[k];
-      A.bn[k][i0] = bn[k];
-    }
-    if (WRITE_X) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) A.x[k][i0] = xrr[k];
-    }
+    A.an[i0] = mk4<T>(an[0], an[1], an[2], an[3]);
+    A.bn[i0] = mk4<T>(bn[0], bn[1], bn[2], bn[3]);
+    if (WRITE_X) A.x[i0] = mk4<T>(xrr[0], xrr[1], xrr[2], xrr[3]);
     if (CHECK) {
+      const v4<T> bo4 = A.b[i0];
+      const T bo[4] = {bo4.x, bo4.y, bo4.z, bo4.w};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const double db = (double)bn[k] - (double)A.b[k][i0];
+        const double db = (double)bn[k] - (double)bo[k];
         r_db += db * db;
         r_kx += (double)kx[k] * (double)kx[k];
       }
@@ -388,7 +383,7 @@ __host__ __device__ __forceinline__ size_t xt_layout(XtSmem<T>* s, char* sm, int
 
 // N1 == 0 selects the dense x transform.
 template <typename T, int N1, int N2, int PMAX>
-__global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPtr4<T> ap,
+__global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, const v4<T>* __restrict__ ap,
                                                     const T* __restrict__ f0, const T* __restrict__ f1,
                                                     T* __restrict__ rhat, XtTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
@@ -396,10 +391,7 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
   const int n1 = g.n1, P = g.P;
   XtSmem<T> s;
   xt_layout<T>(&s, smraw, P, n1, PMAX, scr_elems, N1 == 0);
-  const T* ax = ap.p[0];
-  const T* ay = ap.p[1];
-  const T* ac = ap.p[2];
-  const T* af = ap.p[3];
+  const T* as = reinterpret_cast<const T*>(ap);   // component k of cell i at as[4 i + k]
   // tables
   if (N1) load_tables<T>(s.tw, s.hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
   else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) s.cos4[j] = ((const T*)tb.cos4)[j];
@@ -425,22 +417,19 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, CPt
     const int xm = x > 0 ? x - 1 : (g.per1 ? n1 - 1 : -1);
     const size_t sb = (size_t)b * S + x + (size_t)n1 * (y + (size_t)g.n2 * c);
     const T f0v = f0[sb], f1v = f1[sb];
-    const T* px = ax + rowbase + x;
-    const T* py = ay + rowbase + x;
-    const T* pc = ac + rowbase + x;
-    const T* pf = af + rowbase + x;
-    const T* pxm = px + (xm - x);   // dereferenced only when the face exists
-    const T* pym = py + dy;
-    const T* pcm = pc + dc;
+    const size_t c0 = rowbase + x;                 // this cell at t = 0
+    const long long dx = xm - x;                   // offset to the x-1 cell (used only when it exists)
+    T fprev = f0v;                                 // f face below plane t (f0 at t = 0)
 #pragma unroll kRhsUnroll
     for (int t = 0; t < P; ++t) {
-      const size_t o = (size_t)t * S;
-      T r = g.s1 * (px[o] - (xm >= 0 ? pxm[o] : T(0)));
-      r += g.s2 * (py[o] - (ym >= 0 ? pym[o] : T(0)));
-      r += g.sc * (pc[o] - (cm >= 0 ? pcm[o] : T(0)));
-      const T fnext = (t == P - 1) ? f1v : pf[o];
-      const T fprev = (t == 0) ? f0v : pf[o - S];
+      const size_t o = c0 + (size_t)t * S;
+      const v4<T> av = ap[o];
+      T r = g.s1 * (av.x - (xm >= 0 ? as[4 * (o + dx)] : T(0)));
+      r += g.s2 * (av.y - (ym >= 0 ? as[4 * (o + dy) + 1] : T(0)));
+      r += g.sc * (av.z - (cm >= 0 ? as[4 * (o + dc) + 2] : T(0)));
+      const T fnext = (t == P - 1) ? f1v : av.w;
       r += g.sp * (fnext - fprev);
+      fprev = av.w;
       s.tile[t * n1 + x] = r;
     }
   }
@@ -748,25 +737,14 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   const int S = g.S, sy = g.n1, sc = g.n1 * g.n2;
   const size_t col = (size_t)b * g.P * S + xs + (size_t)sy * ys;
   const size_t col2 = (size_t)b * S + xs + (size_t)sy * ys;
-  const T* __restrict__ pa0 = A.a[0] + col;
-  const T* __restrict__ pa1 = A.a[1] + col;
-  const T* __restrict__ pa2 = A.a[2] + col;
-  const T* __restrict__ pa3 = A.a[3] + col;
-  const T* __restrict__ pb0 = A.b[0] + col;
-  const T* __restrict__ pb1 = A.b[1] + col;
-  const T* __restrict__ pb2 = A.b[2] + col;
-  const T* __restrict__ pb3 = A.b[3] + col;
+  const v4<T>* __restrict__ pa = A.a + col;
+  const v4<T>* __restrict__ pb = A.b + col;
+  const T* __restrict__ pas = reinterpret_cast<const T*>(pa);   // scalar component loads: pas[4 o + k]
   const T* __restrict__ pph = A.phi + col;
   const T* __restrict__ pf0 = A.f0 + col2;
   const T* __restrict__ pf1 = A.f1 + col2;
-  T* __restrict__ qa0 = A.an[0] + col;
-  T* __restrict__ qa1 = A.an[1] + col;
-  T* __restrict__ qa2 = A.an[2] + col;
-  T* __restrict__ qa3 = A.an[3] + col;
-  T* __restrict__ qb0 = A.bn[0] + col;
-  T* __restrict__ qb1 = A.bn[1] + col;
-  T* __restrict__ qb2 = A.bn[2] + col;
-  T* __restrict__ qb3 = A.bn[3] + col;
+  v4<T>* __restrict__ qa = A.an + col;
+  v4<T>* __restrict__ qb = A.bn + col;
   const T s1 = g.s1, s2 = g.s2, scl = g.sc, sp = g.sp, ts = g.ts, half = T(0.5);
   const T isg = T(1) / g.sigma;
   const bool perc = g.perc;
@@ -779,13 +757,17 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   pdl_wait();   // phi (inverse x/t pass) and the state are read from here on
 
   T phic[C], xfp[C], bbfp[C];
+  // the next a of the previous plane's faces along x, y, colour: stored together with its f face,
+  // which is known one plane later
+  T cax[C], cay[C], cac[C];
   // state entering plane t0: phi(t0), x_f at the face t0 - 1 (or f0)
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     const int o = t0 * S + c * sc;
     phic[c] = pph[o];
-    xfp[c] = (t0 == 0) ? pf0[c * sc] : pa3[o - S] + sp * (phic[c] - pph[o - S]);
+    xfp[c] = (t0 == 0) ? pf0[c * sc] : pas[4 * (o - S) + 3] + sp * (phic[c] - pph[o - S]);
     bbfp[c] = T(0);
+    cax[c] = cay[c] = cac[c] = T(0);
   }
 
 #pragma unroll 1
@@ -795,24 +777,27 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
     const bool tnext = t + 1 < g.P;
     T bb[C][4], bn[C][4], xr[C][4], phn[C];
     // loads of this plane (all channels first, so that they overlap)
-    T la0[C], la1[C], la2[C], la3[C], lb[C][4], phy[C], phd[C], la1d[C], la0l[C], phl[C];
+    v4<T> la[C], lb4[C];
+    T phy[C], phd[C], la1d[C], la0l[C], phl[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const int o = pt + c * sc;
-      la0[c] = pa0[o];
-      la1[c] = pa1[o];
-      la2[c] = pa2[o];
-      la3[c] = pa3[o];
-      lb[c][0] = pb0[o];
-      lb[c][1] = pb1[o];
-      lb[c][2] = pb2[o];
-      lb[c][3] = pb3[o];
+      la[c] = pa[o];
+      lb4[c] = pb[o];
       phn[c] = tnext ? pph[o + S] : T(0);
       phy[c] = hasU ? pph[o + dyu] : T(0);
       phd[c] = hasD ? pph[o + dyd] : T(0);
-      la1d[c] = hasD ? pa1[o + dyd] : T(0);
-      la0l[c] = (lane == 0 && hasL) ? pa0[o + dxl] : T(0);
+      la1d[c] = hasD ? pas[4 * (o + dyd) + 1] : T(0);
+      la0l[c] = (lane == 0 && hasL) ? pas[4 * (o + dxl)] : T(0);
       phl[c] = (lane == 0 && hasL) ? pph[o + dxl] : T(0);
+    }
+    T lb[C][4];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      lb[c][0] = lb4[c].x;
+      lb[c][1] = lb4[c].y;
+      lb[c][2] = lb4[c].z;
+      lb[c][3] = lb4[c].w;
     }
     // right faces of x^{r+1}
 #pragma unroll
@@ -820,15 +805,15 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
       const T ph = phic[c];
       T phx = __shfl_down_sync(0xffffffffu, ph, 1);
       if (lane == kTX - 1 && hasR) phx = pph[pt + c * sc + dxr];
-      xr[c][0] = hasR ? la0[c] + s1 * (phx - ph) : T(0);
-      xr[c][1] = hasU ? la1[c] + s2 * (phy[c] - ph) : T(0);
-      xr[c][3] = tnext ? la3[c] + sp * (phn[c] - ph) : pf1[c * sc];
+      xr[c][0] = hasR ? la[c].x + s1 * (phx - ph) : T(0);
+      xr[c][1] = hasU ? la[c].y + s2 * (phy[c] - ph) : T(0);
+      xr[c][3] = tnext ? la[c].w + sp * (phn[c] - ph) : pf1[c * sc];
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const int c1 = (c + 1 == C) ? 0 : c + 1;
       const bool hasC = perc || (c + 1 < C);
-      xr[c][2] = hasC ? la2[c] + scl * (phic[c1] - phic[c]) : T(0);
+      xr[c][2] = hasC ? la[c].z + scl * (phic[c1] - phic[c]) : T(0);
     }
     // left faces, interpolation to the cell, prox, dual update
 #pragma unroll
@@ -871,32 +856,25 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
     for (int c = 0; c < C; ++c) sbb[par][row][lane][c] = bb[c][1];
     __syncthreads();
     if (out && t > t0) {
-      // the f face t-1 (between planes t-1 and t), owned by this chunk when t > t0
+      // plane t-1 is complete with its f face t-1 (between planes t-1 and t), owned by this chunk when t > t0
 #pragma unroll
-      for (int c = 0; c < C; ++c) qa3[pt - S + c * sc] = xfp[c] - ts * half * (bbfp[c] + bb[c][3]);
+      for (int c = 0; c < C; ++c)
+        qa[pt - S + c * sc] = mk4<T>(cax[c], cay[c], cac[c], xfp[c] - ts * half * (bbfp[c] + bb[c][3]));
     }
     if (write_plane) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const T bxn = __shfl_down_sync(0xffffffffu, bb[c][0], 1);
         const T byn = (row + 1 < kTY) ? sbb[par][row + 1][lane][c] : T(0);
+        const int c1 = (c + 1 == C) ? 0 : c + 1;
+        const bool hasC = perc || (c + 1 < C);
+        cax[c] = hasR ? xr[c][0] - ts * half * (bb[c][0] + bxn) : T(0);
+        cay[c] = hasU ? xr[c][1] - ts * half * (bb[c][1] + byn) : T(0);
+        cac[c] = hasC ? xr[c][2] - ts * half * (bb[c][2] + bb[c1][2]) : T(0);
         if (out) {
           const int o = pt + c * sc;
-          const int c1 = (c + 1 == C) ? 0 : c + 1;
-          const bool hasC = perc || (c + 1 < C);
-          qa0[o] = hasR ? xr[c][0] - ts * half * (bb[c][0] + bxn) : T(0);
-          qa1[o] = hasU ? xr[c][1] - ts * half * (bb[c][1] + byn) : T(0);
-          qa2[o] = hasC ? xr[c][2] - ts * half * (bb[c][2] + bb[c1][2]) : T(0);
-          qb0[o] = bn[c][0];
-          qb1[o] = bn[c][1];
-          qb2[o] = bn[c][2];
-          qb3[o] = bn[c][3];
-          if (WRITE_X) {
-            A.x[0][col + o] = xr[c][0];
-            A.x[1][col + o] = xr[c][1];
-            A.x[2][col + o] = xr[c][2];
-            A.x[3][col + o] = tnext ? xr[c][3] : T(0);
-          }
+          qb[o] = mk4<T>(bn[c][0], bn[c][1], bn[c][2], bn[c][3]);
+          if (WRITE_X) A.x[col + o] = mk4<T>(xr[c][0], xr[c][1], xr[c][2], tnext ? xr[c][3] : T(0));
         }
       }
       if (CHECK && tnext) {
@@ -918,6 +896,11 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
       bbfp[c] = bb[c][3];
       phic[c] = phn[c];
     }
+  }
+  // the last plane of the problem has no f face (f1 is a boundary value): store it with zero there
+  if (out && tlast == tend - 1) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) qa[tlast * S + c * sc] = mk4<T>(cax[c], cay[c], cac[c], T(0));
   }
   pdl_trigger();
   if (CHECK) {
