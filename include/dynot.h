@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define OT_ABI_VERSION 1
+#define OT_ABI_VERSION 2
 
 typedef struct ot_plan_s* ot_plan_t;
 
@@ -93,7 +93,21 @@ typedef struct {
   double energy;         /* (1/#cells) sum J(u, v) in the caller's density units */
   double mass_drift;     /* max_t |sum_x f(t) - M| / M over the interior times */
   double elapsed_ms;     /* device time of the call (CUDA events) */
+  double dual_value;     /* dual objective at p = sigma b of the last check, caller units (see below) */
+  double gap;            /* primal-dual gap |energy - dual_value| / max(|energy|, |dual_value|) */
 } ot_solve_stats;
+/*
+ * The dual value (no counterpart in the paper; a convergence measure beside
+ * the residual): the problem's Lagrangian dual function at p = sigma b,
+ *   D = sigma (<b_m, S_M m0> + <b_f, S_F f0 + f_b^+>) / #cells,
+ * where (m0, f0) = Pi_{C_d}(0) is the least-norm path that meets the continuity
+ * constraint.  Step 2 keeps sigma b in the subdifferential of J (so J*(p) = 0)
+ * and D takes the infimum of <K^T p, x> over C_d at x0, which is exact once
+ * K^T p lies in the range of A^T.  At a saddle point D equals the energy, so
+ * the gap tends to zero with the iteration.  Residual, energy and dual sums
+ * are formed from per-thread compensated sums in the working precision and
+ * summed across threads in FP64.
+ */
 
 /* Fill *g with the defaults for an RGB grid n1 x n2 x 3 with P time intervals. */
 void ot_grid_rgb(ot_grid* g, int n1, int n2, int P);

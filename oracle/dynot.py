@@ -414,6 +414,7 @@ class StepInfo:
     primal_change: float     # ||x^{r+1} - x^r|| / ||x^{r+1}||
     continuity: float        # ||A x^{r+1} - f_b^-|| / ||f_b^-||
     energy: float            # (1/#cells) sum J(u^{r+1}, v^{r+1})
+    dual: Optional[float] = None   # dual_value at p = sigma b^{r+1} (when the step is given x0)
     u: List[np.ndarray] = field(repr=False, default=None)
     v: np.ndarray = field(repr=False, default=None)
 
@@ -422,9 +423,36 @@ def _norm2(arrs) -> float:
     return float(np.sqrt(sum(float(np.sum(a * a)) for a in arrs)))
 
 
+def min_norm_path(g: Grid, f0: np.ndarray, f1: np.ndarray) -> Tuple[List[np.ndarray], np.ndarray]:
+    """x0 = Pi_{C_d}(0) = A^T (A A^T)^+ f_b^-: the path of least norm that meets the continuity
+    constraint (the projection of section 3 applied to a = 0)."""
+    zm = [np.zeros(g.m_shape(k)) for k in range(g.d)]
+    m, f, _ = project(g, zm, np.zeros(g.f_shape), f0, f1)
+    return m, f
+
+
+def dual_value(g: Grid, bm: Sequence[np.ndarray], bf: np.ndarray, x0, f0: np.ndarray, f1: np.ndarray,
+               sigma: float) -> float:
+    """Dual objective of the discrete problem at p = sigma b, per cell (no counterpart in the paper).
+
+    The problem is min over x in C_d of ||J(K x + (0, f_b^+))||_1.  Its Lagrangian dual function at p is
+    -J*(p) + <p_f, f_b^+> + inf_{x in C_d} <K^T p, x>.  J is the support function of
+    {(a, b): b + |a|^2 / 2 <= 0}, so J* = 0 on that set; step 2 of Algorithm 1 puts sigma b^{r+1} in the
+    subdifferential of J at (u, v), hence in it.  The infimum over C_d = x0 + ker A equals <K^T p, x0>
+    when K^T p lies in the range of A^T (the dual constraint), and this value is taken:
+        D = sigma (<b_m, S_M m0> + <b_f, S_F f0 + f_b^+>) / #cells,  (m0, f0) = min_norm_path.
+    At a saddle point the primal energy (1/#cells) sum J(u, v) equals D; the difference is the
+    primal-dual gap."""
+    sm, sf = K(g, x0[0], x0[1])
+    fbp = f_b_plus(g, f0, f1)
+    tot = sum(float(np.sum(bm[k] * sm[k])) for k in range(g.d)) + float(np.sum(bf * (sf + fbp)))
+    return sigma * tot / g.ncells
+
+
 def pdhg_step(g: Grid, st: State, f0: np.ndarray, f1: np.ndarray, sigma: float, tau: float,
-              theta: float = 1.0) -> Tuple[State, StepInfo]:
-    """One iteration of Algorithm 1 (steps 1-4), in the paper's order."""
+              theta: float = 1.0, x0=None) -> Tuple[State, StepInfo]:
+    """One iteration of Algorithm 1 (steps 1-4), in the paper's order.  With x0 = min_norm_path the
+    step also reports the dual value of its dual iterate."""
     # step 1: x^{r+1} = Pi_{C_d}(x^r - tau sigma K^T bbar^r)
     km, kf = K_T(g, st.bbm, st.bbf)
     am = [st.m[k] - tau * sigma * km[k] for k in range(g.d)]
@@ -452,6 +480,7 @@ def pdhg_step(g: Grid, st: State, f0: np.ndarray, f1: np.ndarray, sigma: float, 
         primal_change=_norm2(dx) / max(_norm2(list(m) + [f]), 1e-300),
         continuity=_norm2([A(g, m, f) - fbm]) / max(_norm2([fbm]), 1e-300),
         energy=float(np.sum(J_energy(u, v))) / g.ncells,
+        dual=None if x0 is None else dual_value(g, bm, bf, x0, f0, f1, sigma),
         u=u, v=v)
     return new, info
 
@@ -516,21 +545,23 @@ def normalise_pair(g: Grid, f0: np.ndarray, f1: np.ndarray, rel_tol: float = 1e-
 
 def solve(g: Grid, f0: np.ndarray, f1: np.ndarray, iters: int, sigma: float, tau: float,
           state: Optional[State] = None, normalise: bool = True, tol: float = 0.0,
-          check_every: int = 1, callback=None):
+          check_every: int = 1, callback=None, with_dual: bool = False):
     """Run Algorithm 1 for ``iters`` iterations (or until residual <= tol).
 
     With ``normalise`` the pair is rescaled by :func:`normalise_pair` first and
     the returned path is scaled back.  Returns (state, infos, scale) where the
     state is in solver units and ``scale`` maps its m, f and energy back.
+    ``with_dual`` adds the dual value of every iterate (info.dual).
     """
     if normalise:
         g0, g1, scale = normalise_pair(g, f0, f1)
     else:
         g0, g1, scale = np.asarray(f0, float), np.asarray(f1, float), 1.0
     st = State.zeros(g) if state is None else state.copy()
+    x0 = min_norm_path(g, g0, g1) if with_dual else None
     infos = []
     for r in range(iters):
-        st, info = pdhg_step(g, st, g0, g1, sigma, tau)
+        st, info = pdhg_step(g, st, g0, g1, sigma, tau, x0=x0)
         info.u = info.v = None
         infos.append(info)
         if callback is not None:

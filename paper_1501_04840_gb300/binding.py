@@ -37,7 +37,7 @@ class Grid(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", c_int), ("residual", c_double), ("energy", c_double), ("mass_drift", c_double),
-                ("elapsed_ms", c_double)]
+                ("elapsed_ms", c_double), ("dual_value", c_double), ("gap", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -344,6 +344,8 @@ ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* cons
         stats[i].residual = c.residual;
         stats[i].energy = c.energy;
         stats[i].mass_drift = c.drift;
+        stats[i].dual_value = c.dual;
+        stats[i].gap = c.gap;
         stats[i].elapsed_ms = ms;
       }
     }

@@ -131,6 +131,21 @@ struct Arrays {
   const T* f0;     // boundary densities (solver units), [b][s]
   const T* f1;
   v4<T>* x;        // optional output: x^{r+1} (faces), nullptr when not wanted
+  const v4<T>* w;  // K x0 + (0, f_b^+) at the cells (x0 the least-norm feasible path): the dual value
+                   // of a check is sigma <b^{r+1}, w>
+};
+
+// Compensated (Kahan) sum in the working precision: the per-thread partial sums of a residual check keep
+// about two units in the last place whatever their length; the sums across threads are in FP64.
+template <typename T>
+struct KSum {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
 };
 
 }  // namespace dynot

@@ -225,6 +225,32 @@ __global__ void k_dual_init(Geo<T> g, const v4<T>* __restrict__ x, const T* __re
   }
 }
 
+// w = K x0 + (0, f_b^+) at the cells (S_M m0 and S_F f0 + f_b^+ of section 2) for the least-norm feasible
+// path x0 = (m0, f0): the dual value of a check is sigma <b, w> (the dual function of the problem at
+// p = sigma b, with the infimum over C_d taken at x0).
+template <typename T>
+__global__ void k_dual_weights(Geo<T> g, const v4<T>* __restrict__ x, const T* __restrict__ f0,
+                               const T* __restrict__ f1, v4<T>* __restrict__ w) {
+  const long long tot = (long long)g.B * g.N;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    const int ix = r % g.n1; r /= g.n1;
+    const int iy = r % g.n2; r /= g.n2;
+    const int ic = r % g.C; r /= g.C;
+    const int t = r % g.P;
+    const int b = (int)(r / g.P);
+    T left[3];
+    left[0] = ix > 0 ? comp<T>(x, cidx(g, b, t, ix - 1, iy, ic), 0) : (g.per1 ? comp<T>(x, cidx(g, b, t, g.n1 - 1, iy, ic), 0) : T(0));
+    left[1] = iy > 0 ? comp<T>(x, cidx(g, b, t, ix, iy - 1, ic), 1) : (g.per2 ? comp<T>(x, cidx(g, b, t, ix, g.n2 - 1, ic), 1) : T(0));
+    left[2] = ic > 0 ? comp<T>(x, cidx(g, b, t, ix, iy, ic - 1), 2) : (g.perc ? comp<T>(x, cidx(g, b, t, ix, iy, g.C - 1), 2) : T(0));
+    const size_t s = (size_t)b * g.S + ix + (size_t)g.n1 * (iy + (size_t)g.n2 * ic);
+    const T fl = t == 0 ? f0[s] : comp<T>(x, cidx(g, b, t - 1, ix, iy, ic), 3);
+    const T fr = t == g.P - 1 ? f1[s] : comp<T>(x, id, 3);
+    w[id] = mk4<T>(T(0.5) * (left[0] + comp<T>(x, id, 0)), T(0.5) * (left[1] + comp<T>(x, id, 1)),
+                   T(0.5) * (left[2] + comp<T>(x, id, 2)), T(0.5) * (fl + fr));
+  }
+}
+
 // x = a - A^T phi at the right faces (the correction of the projection).
 template <typename T>
 __global__ void k_correct(Geo<T> g, Arrays<T> A) {

@@ -1,8 +1,12 @@
 // Templated plan: workspace, transform tables, kernel selection and the
 // iteration driver, instantiated for float (plan_f32.cu) and double (plan_f64.cu).
 #pragma once
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -14,6 +18,7 @@
 #include "misc_kernels.cuh"
 #include "plan_base.h"
 #include "rgb_kernels.cuh"
+#include "rgb_update_tma.cuh"
 
 namespace dynot {
 
@@ -128,6 +133,47 @@ KD<T> pick_kd(int C, bool check, bool wx, bool per_xy) {
   return per_xy ? pick_kd_p<T, true>(C, check, wx) : pick_kd_p<T, false>(C, check, wx);
 }
 
+// the update kernel with tensor-memory-accelerator staging (FP32, Neumann x and y)
+using KDT = void (*)(Geo<float>, Arrays<float>, int, double*, int*, const CUtensorMap, const CUtensorMap,
+                     const CUtensorMap);
+template <int C>
+KDT pick_kdt_c(bool check, bool wx) {
+  if (check) return wx ? k_update_tma<C, true, true> : k_update_tma<C, true, false>;
+  return wx ? k_update_tma<C, false, true> : k_update_tma<C, false, false>;
+}
+inline KDT pick_kdt(int C, bool check, bool wx) {
+  switch (C) {
+    case 1: return pick_kdt_c<1>(check, wx);
+    case 2: return pick_kdt_c<2>(check, wx);
+    case 3: return pick_kdt_c<3>(check, wx);
+    default: return pick_kdt_c<4>(check, wx);
+  }
+}
+inline size_t tma_smem(int C) {
+  switch (C) {
+    case 1: return TmaTiles<1>::total;
+    case 2: return TmaTiles<2>::total;
+    case 3: return TmaTiles<3>::total;
+    default: return TmaTiles<4>::total;
+  }
+}
+#ifndef DYNOT_UPD_TMA
+#define DYNOT_UPD_TMA 1   // 0: the plain-load update kernel everywhere
+#endif
+
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }();
+  return fn;
+}
+
 template <typename T>
 KH<T> pick_kh(int pm) {
   return pm == 16 ? k_hue_t<T, 16> : (pm == 32 ? k_hue_t<T, 32> : k_hue_t<T, 64>);
@@ -142,6 +188,7 @@ struct Plan final : PlanBase {
   T* phi = nullptr;
   T* hat = nullptr;
   v4<T>* x = nullptr;   // primal output x of the last check
+  v4<T>* w = nullptr;   // K x0 + (0, f_b^+) at the cells (dual value of a check)
   T* f0n = nullptr;
   T* f1n = nullptr;
   float* stage = nullptr;   // float staging: 2*B*S inputs, then path packing
@@ -151,6 +198,8 @@ struct Plan final : PlanBase {
   double* chk = nullptr;    // [B][kChk]
   double* scl = nullptr;    // [B][2]
   double* part = nullptr;   // per-block partial sums of the residual check
+  int* err = nullptr;       // set by a kernel whose bounded device wait ran out (sticky until the next start)
+  int* h_err = nullptr;     // pinned host copy, read with the residuals
   double* h_acc = nullptr;  // pinned host copies of acc and mass
   double* h_mass = nullptr;
   // transform tables
@@ -166,6 +215,8 @@ struct Plan final : PlanBase {
   KB<T> kb = nullptr;
   KH<T> kh = nullptr;
   bool tiled = false;       // tiled update kernel (up to four colour channels)
+  bool use_tma = false;     // the tiled update stages its planes with bulk tensor copies
+  CUtensorMap tmA[2]{}, tmB[2]{}, tmP{};   // a[p], b[p] and phi for k_update_tma
   int tc = 0;               // time-chunk length of the tiled update (autotuned)
   int par = 0;              // buffer holding the current state
   bool have_x = false;
@@ -184,6 +235,7 @@ struct Plan final : PlanBase {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     if (h_acc) cudaFreeHost(h_acc);
+    if (h_err) cudaFreeHost(h_err);
     if (h_mass) cudaFreeHost(h_mass);
   }
 
@@ -215,13 +267,13 @@ struct Plan final : PlanBase {
 
     // ---- workspace
     const size_t cells = (size_t)B * N;
-    const size_t narr = 2 * 4 + 2 * 4 + 2 + 4;
+    const size_t narr = 2 * 4 + 2 * 4 + 2 + 4 + 4;
     // staging holds the inputs (2 B S), a packed path (B total) or a packed dual (B (d+1) N)
     stage_floats = std::max<size_t>({2 * (size_t)B * S, (size_t)B * cp.total, (size_t)B * (d + 1) * (size_t)N});
     size_t bytes = narr * rnd16(cells * sizeof(T)) + 2 * rnd16((size_t)B * S * sizeof(T)) +
                    rnd16(stage_floats * sizeof(float)) + rnd16(sizeof(double) * B * kAcc) +
                    rnd16(sizeof(double) * (size_t)B * P) + rnd16(sizeof(double) * B * kChk) +
-                   rnd16(sizeof(double) * B * 2) + rnd16(part_bytes());
+                   rnd16(sizeof(double) * B * 2) + rnd16(part_bytes()) + 16;
     CUDA_OK(cudaMalloc(&mem.p, bytes));
     char* q = (char*)mem.p;
     auto take = [&](size_t nb) { char* r = q; q += rnd16(nb); return r; };
@@ -230,6 +282,7 @@ struct Plan final : PlanBase {
     phi = (T*)take(cells * sizeof(T));
     hat = (T*)take(cells * sizeof(T));
     x = (v4<T>*)take(cells * sizeof(v4<T>));
+    w = (v4<T>*)take(cells * sizeof(v4<T>));
     f0n = (T*)take((size_t)B * S * sizeof(T));
     f1n = (T*)take((size_t)B * S * sizeof(T));
     stage = (float*)take(stage_floats * sizeof(float));
@@ -238,15 +291,63 @@ struct Plan final : PlanBase {
     chk = (double*)take(sizeof(double) * B * kChk);
     scl = (double*)take(sizeof(double) * B * 2);
     part = (double*)take(part_bytes());
+    err = (int*)take(sizeof(int));
     CUDA_OK(cudaMemsetAsync(mem.p, 0, bytes, st));
 
     OT_TRY(build_tables());
     for (auto& e : ev) CUDA_OK(cudaEventCreate(&e));
     CUDA_OK(cudaMallocHost(&h_acc, sizeof(double) * B * kAcc));
+    CUDA_OK(cudaMallocHost(&h_err, sizeof(int)));
+    *h_err = 0;
     CUDA_OK(cudaMallocHost(&h_mass, sizeof(double) * (size_t)B * P));
     out_scale.assign(B, 1.0);
     tiled = !hue && C <= 4;
+    if constexpr (std::is_same<T, float>::value) {
+      // DYNOT_UPDATE_KERNEL=plain selects the plain-load update kernel (same arithmetic; for comparisons)
+      const char* kind = std::getenv("DYNOT_UPDATE_KERNEL");
+      const bool plain = kind && std::strcmp(kind, "plain") == 0;
+      if (tiled && DYNOT_UPD_TMA && !plain && !g.per1 && !g.per2 && n1 % 4 == 0 && n1 >= kTX && n2 >= kTY)
+        OT_TRY(make_tensor_maps());
+    }
     if (tiled) OT_TRY(tune_update());
+    return OT_OK;
+  }
+
+  // Tensor maps of the TMA-staged update: a and b as [B P][C][n2][n1][4] (the four components innermost),
+  // boxes of 33 x 9 cells (a, with the column left and the row below the 32 x 8 tile) and 32 x 8 cells (b);
+  // phi as [B P][C][n2][n1], boxes of 40 x 10 cells.  Out-of-range cells read as zero.
+  ot_status make_tensor_maps() {
+    auto enc = tensor_map_encoder();
+    if (!enc) return OT_OK;   // no driver entry point: keep the plain-load update
+    const cuuint64_t BP = (cuuint64_t)B * P;
+    const cuuint64_t dim5[5] = {4, (cuuint64_t)n1, (cuuint64_t)n2, (cuuint64_t)C, BP};
+    const cuuint64_t str5[4] = {16, 16ull * n1, 16ull * n1 * n2, 16ull * S};
+    const cuuint32_t boxA[5] = {4, kTX + 1, kTY + 1, (cuuint32_t)C, 1};
+    const cuuint32_t boxB[5] = {4, kTX, kTY, (cuuint32_t)C, 1};
+    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+    for (int i = 0; i < 2; ++i) {
+      CUresult r = enc(&tmA[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)a[i], dim5, str5, boxA, one,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return OT_OK;   // the driver cannot describe this tensor: keep the plain-load update
+      r = enc(&tmB[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)b[i], dim5, str5, boxB, one,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return OT_OK;
+    }
+    const cuuint64_t dim4[4] = {(cuuint64_t)n1, (cuuint64_t)n2, (cuuint64_t)C, BP};
+    const cuuint64_t str4[3] = {4ull * n1, 4ull * n1 * n2, 4ull * S};
+    const cuuint32_t boxP[4] = {kTX + 8, kTY + 2, (cuuint32_t)C, 1};
+    CUresult r = enc(&tmP, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)phi, dim4, str4, boxP, one,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return OT_OK;
+    const size_t smem = tma_smem(C);
+    for (int ck = 0; ck < 2; ++ck)
+      for (int wx = 0; wx < 2; ++wx)
+        CUDA_OK(cudaFuncSetAttribute((const void*)pick_kdt(C, ck, wx), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    use_tma = true;
     return OT_OK;
   }
 
@@ -501,6 +602,7 @@ struct Plan final : PlanBase {
     A.an = a[1 - p];
     A.bn = b[1 - p];
     A.x = wx ? x : nullptr;
+    A.w = w;
     A.phi = phi;
     A.f0 = f0n;
     A.f1 = f1n;
@@ -509,10 +611,11 @@ struct Plan final : PlanBase {
   const v4<T>* aptr(int p) const { return a[p]; }
 
   // ---- the Poisson solve phi = (A A^T)^+ (A a - f_b^-) for a in buffer p
-  void enqueue_poisson(int p, cudaEvent_t* evs) {
+  void enqueue_poisson(int p, cudaEvent_t* evs) { enqueue_poisson_src(aptr(p), evs); }
+  void enqueue_poisson_src(const v4<T>* asrc, cudaEvent_t* evs) {
     if (!hue) {
       if (evs) cudaEventRecord(evs[0], st);
-      launch_pdl(ka, dim3(n2, C, B), dim3(kThreadsXt), smA, st, g, aptr(p), (const T*)f0n, (const T*)f1n, hat, xt,
+      launch_pdl(ka, dim3(n2, C, B), dim3(kThreadsXt), smA, st, g, asrc, (const T*)f0n, (const T*)f1n, hat, xt,
                  scrA);
       if (evs) cudaEventRecord(evs[1], st);
       launch_pdl(kb, dim3((n1 + kW - 1) / kW, P, B), dim3(yc_threads(y_fft() ? n2 : 0)), smB, st, g, hat, yc, scrB);
@@ -521,7 +624,7 @@ struct Plan final : PlanBase {
       if (evs) cudaEventRecord(evs[3], st);
     } else {
       if (evs) cudaEventRecord(evs[0], st);
-      k_hue_fwd<T><<<dim3(P, B), 256, smH, st>>>(g, aptr(p), f0n, f1n, hat, ht);
+      k_hue_fwd<T><<<dim3(P, B), 256, smH, st>>>(g, asrc, f0n, f1n, hat, ht);
       if (evs) cudaEventRecord(evs[1], st);
       kh<<<dim3((n1 + 256 / pmax - 1) / (256 / pmax), B), 256, smHt, st>>>(g, hat, ht);
       if (evs) cudaEventRecord(evs[2], st);
@@ -548,7 +651,15 @@ struct Plan final : PlanBase {
     const Arrays<T> A = arrays(p, wx);
     if (tiled) {
       const dim3 grd = tiled_grid(tc);
-      launch_pdl(pick_kd<T>(C, check, wx, g.per1 || g.per2), grd, dim3(kTX, kTY), 0, st, g, A, tc, part);
+      bool done = false;
+      if constexpr (std::is_same<T, float>::value) {
+        if (use_tma) {
+          launch_pdl(pick_kdt(C, check, wx), grd, dim3(kTX, kTY), tma_smem(C), st, g, A, tc, part, err, tmA[p], tmB[p],
+                     tmP);
+          done = true;
+        }
+      }
+      if (!done) launch_pdl(pick_kd<T>(C, check, wx, g.per1 || g.per2), grd, dim3(kTX, kTY), 0, st, g, A, tc, part);
       if (check) k_reduce_check<<<B, 256, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass);
       return;
     }
@@ -603,7 +714,7 @@ struct Plan final : PlanBase {
   }
 
   struct Check {
-    double residual = 0, energy = 0, drift = 0;
+    double residual = 0, energy = 0, drift = 0, dual = 0, gap = 0;
   };
 
   // one iteration with residuals (and x output); results land in pinned host memory
@@ -616,6 +727,7 @@ struct Plan final : PlanBase {
     if (wx) have_x = true;
     CUDA_OK(cudaMemcpyAsync(h_acc, acc, sizeof(double) * B * kAcc, cudaMemcpyDeviceToHost, st));
     CUDA_OK(cudaMemcpyAsync(h_mass, mass, sizeof(double) * (size_t)B * P, cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaMemcpyAsync(h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     return OT_OK;
   }
 
@@ -623,18 +735,24 @@ struct Plan final : PlanBase {
   ot_status collect_check(std::vector<ProblemCheck>& per, Check& out) {
     per.assign(B, ProblemCheck{});
     out = Check{};
+    if (*h_err) return seterr(OT_ETIMEOUT, "a bounded device wait of the update kernel ran out of its limit");
     for (int bi = 0; bi < B; ++bi) {
       const double* q = &h_acc[(size_t)bi * kAcc];
       const double res = std::sqrt(q[0]) / std::max(std::sqrt(q[1]), 1e-300);
-      if (!std::isfinite(res) || !std::isfinite(q[2]))
+      if (!std::isfinite(res) || !std::isfinite(q[2]) || !std::isfinite(q[3]))
         return seterr(OT_ENUMERIC, "non-finite residual in problem %d", bi);
       double M = 0;
       for (int t = 0; t + 1 < P; ++t) M = std::max(M, std::fabs(h_mass[(size_t)bi * P + t] - (double)S));
       per[bi].residual = res;
       per[bi].energy = q[2] / (double)N * out_scale[bi];
+      per[bi].dual = (double)g.sigma * q[3] / (double)N * out_scale[bi];
+      per[bi].gap = std::fabs(per[bi].energy - per[bi].dual) /
+                    std::max(std::max(std::fabs(per[bi].energy), std::fabs(per[bi].dual)), 1e-300);
       per[bi].drift = M / (double)S;
       out.residual = std::max(out.residual, res);
       out.energy += per[bi].energy / B;
+      out.dual += per[bi].dual / B;
+      out.gap = std::max(out.gap, per[bi].gap);
       out.drift = std::max(out.drift, per[bi].drift);
     }
     return OT_OK;
@@ -651,6 +769,7 @@ struct Plan final : PlanBase {
     enqueue_iteration(lead ? 1 - p : p, true, true);
     cudaMemcpyAsync(h_acc, acc, sizeof(double) * B * kAcc, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(h_mass, mass, sizeof(double) * (size_t)B * P, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
     const cudaError_t le = cudaGetLastError();
     cudaError_t e = cudaStreamEndCapture(st, &gr);
     if (le != cudaSuccess) {
@@ -721,6 +840,8 @@ struct Plan final : PlanBase {
       stats->energy = ck.energy;
       stats->mass_drift = ck.drift;
       stats->elapsed_ms = ms;
+      stats->dual_value = ck.dual;
+      stats->gap = ck.gap;
     }
     if (tol > 0 && !converged) return seterr(OT_ENOTCONV, "residual %.3e > tol %.3e after %d iterations",
                                              ck.residual, tol, done);
@@ -746,7 +867,8 @@ struct Plan final : PlanBase {
 
   ot_status prepare_staged() override {
     OT_TRY(validate_scale(true));
-    return cold_start();
+    OT_TRY(cold_start());
+    return make_dual_weights();
   }
 
   // validate the staged densities (section 2: f >= 0, equal masses) and rescale (reading of section 4)
@@ -797,10 +919,31 @@ struct Plan final : PlanBase {
     return OT_OK;
   }
 
+  // w = K x0 + (0, f_b^+) for the boundary densities in f0n, f1n, with x0 = Pi_{C_d}(0) the least-norm feasible
+  // path (the projection of step 1 applied to a = 0); x serves as the work array.
+  ot_status make_dual_weights() {
+    const long long cells = (long long)B * N;
+    CUDA_OK(cudaMemsetAsync(x, 0, cells * sizeof(v4<T>), st));
+    enqueue_poisson_src(x, nullptr);
+    Arrays<T> A{};
+    A.a = x;
+    A.x = x;   // in place: every cell reads only its own a
+    A.phi = phi;
+    A.f0 = f0n;
+    A.f1 = f1n;
+    k_correct<T><<<grid1d(cells), 256, 0, st>>>(g, A);
+    k_dual_weights<T><<<grid1d(cells), 256, 0, st>>>(g, x, f0n, f1n, w);
+    CUDA_OK(cudaGetLastError());
+    have_x = false;
+    return OT_OK;
+  }
+
   ot_status cold_start() {
     CUDA_OK(cudaMemsetAsync(a[0], 0, (size_t)B * N * sizeof(v4<T>), st));
     CUDA_OK(cudaMemsetAsync(b[0], 0, (size_t)B * N * sizeof(v4<T>), st));
     CUDA_OK(cudaMemsetAsync(b[1], 0, (size_t)B * N * sizeof(v4<T>), st));
+    CUDA_OK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    *h_err = 0;
     par = 0;
     have_x = false;
     return OT_OK;
@@ -813,6 +956,7 @@ struct Plan final : PlanBase {
     if (used_cold) *used_cold = 0;
     OT_TRY(load_boundary(f0, f1, true));
     OT_TRY(cold_start());
+    OT_TRY(make_dual_weights());
     if (init) {
       // x0 = init (scaled to solver units per problem) into x, then b = bbar = 0 or the fixed-point dual
       const size_t n = (size_t)B * cp.total;
@@ -914,8 +1058,11 @@ struct Plan final : PlanBase {
                       const float* bbp) override {
     if (!f0 || !f1 || !xp || !bp) return seterr(OT_EINVAL, "f0, f1, x and b are required");
     OT_TRY(load_boundary(f0, f1, false));
+    OT_TRY(make_dual_weights());
     OT_TRY(unpack_x(xp));
     const long long cells = (long long)B * N;
+    CUDA_OK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    *h_err = 0;
     // b -> b[0]; bbar -> b[1] temporarily
     CUDA_OK(cudaMemsetAsync(b[0], 0, cells * sizeof(v4<T>), st));
     CUDA_OK(cudaMemsetAsync(b[1], 0, cells * sizeof(v4<T>), st));

@@ -45,7 +45,7 @@ struct DevMem {
 // --------------------------------------------------------------------------
 // residual, energy (caller units) and mass drift of one problem at a check
 struct ProblemCheck {
-  double residual = 0, energy = 0, drift = 0;
+  double residual = 0, energy = 0, drift = 0, dual = 0, gap = 0;
 };
 
 struct PlanBase {

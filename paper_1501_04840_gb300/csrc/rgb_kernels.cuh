@@ -225,7 +225,7 @@ struct CellCtx {
 
 // Residual accumulators (FP64, one set per problem):
 //   0: sum |b^{r+1} - b^r|^2   1: sum |K x + (0, f_b^+)|^2   2: sum J(u, v)
-//   3: sum |x^{r+1} - x^r|^2 is not formed here; 4..: unused
+//   3: sum <b^{r+1}, w> (the dual value over sigma; w = K x0 + (0, f_b^+))
 //   mass[b*P + t]: sum over space of f at time (t+1)/P
 constexpr int kAcc = 4;
 
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(128) k_update(Geo<T> g, Arrays<T> A, double* _
   const int t = z % g.P;
   const int b = z / g.P;
   const bool live = x < g.n1;
-  double r_db = 0, r_kx = 0, r_J = 0, r_m = 0;
+  double r_db = 0, r_kx = 0, r_J = 0, r_m = 0, r_w = 0;
   if (live) {
     CellCtx<T> cc{g, A, b};
     T bb[4], bn[4], xrr[4], kx[4], U0, U1, U2, V;
@@ -294,26 +294,31 @@ __global__ void __launch_bounds__(128) k_update(Geo<T> g, Arrays<T> A, double* _
       const double uu = (double)U0 * U0 + (double)U1 * U1 + (double)U2 * U2;
       if (V > T(0)) r_J = uu / (2.0 * (double)V);
       r_m = (double)xrr[3];
+      const v4<T> wv = A.w[i0];
+      r_w = (double)bn[0] * wv.x + (double)bn[1] * wv.y + (double)bn[2] * wv.z + (double)bn[3] * wv.w;
     }
   }
   if (CHECK) {
-    __shared__ double red[4][4];
+    __shared__ double red[4][5];
     r_db = warp_sum<T>(r_db);
     r_kx = warp_sum<T>(r_kx);
     r_J = warp_sum<T>(r_J);
     r_m = warp_sum<T>(r_m);
+    r_w = warp_sum<T>(r_w);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
       red[w][0] = r_db;
       red[w][1] = r_kx;
       red[w][2] = r_J;
       red[w][3] = r_m;
+      red[w][4] = r_w;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 5) {
       double s = 0;
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i][threadIdx.x];
       if (threadIdx.x < 3) atomicAdd(&acc[(size_t)b * kAcc + threadIdx.x], s);
+      else if (threadIdx.x == 4) atomicAdd(&acc[(size_t)b * kAcc + 3], s);
       else if (t < g.P - 1) atomicAdd(&mass[(size_t)b * g.P + t], s);
     }
   }
@@ -699,8 +704,40 @@ constexpr int kTX = 32, kTY = 8;
 #endif
 
 // Per-block partial sums of the residual check: [problem][block][kPart] with
-// 0: |b+ - b|^2, 1: |K x + (0, f_b^+)|^2, 2: J(u, v), 3 + t: mass of the time slice t.
+// 0: |b+ - b|^2, 1: |K x + (0, f_b^+)|^2, 2: J(u, v), 3 + t: mass of the time slice t (t < 64),
+// kPartW = 67: <b+, w> (the dual value over sigma).
 constexpr int kPart = 68;
+constexpr int kPartW = 67;
+
+// Per-block partial sums of a check (called by every thread of a 32 x 8 block after its plane loop):
+// FP64 sums of the threads' compensated partials, written to part[problem][block][...].
+template <typename T>
+__device__ __forceinline__ void block_check_partials(const KSum<T>& r_db, const KSum<T>& r_kx, const KSum<T>& r_J,
+                                                     const KSum<T>& r_w, int lane, int row, int nch, int b, int t0,
+                                                     int tend, int P, double* __restrict__ part,
+                                                     const double (&smass)[64]) {
+  __shared__ double red[kTY][4];
+  double d[4] = {(double)r_db.s - (double)r_db.c, (double)r_kx.s - (double)r_kx.c, (double)r_J.s - (double)r_J.c,
+                 (double)r_w.s - (double)r_w.c};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[row][q] = d[q];
+  __syncthreads();
+  const int tid = lane + kTX * row;
+  const int nblk = gridDim.x * gridDim.y * nch;    // blocks of one problem
+  const int jb = ((blockIdx.z % nch) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  double* pp = part + ((size_t)b * nblk + jb) * kPart;
+  if (tid < 4) {
+    double sum = 0;
+    for (int i = 0; i < kTY; ++i) sum += red[i][tid];
+    pp[tid < 3 ? tid : kPartW] = sum;
+  }
+  for (int t = tid; t < 64; t += kTX * kTY) pp[3 + t] = (t >= t0 && t < tend && t < P - 1) ? smass[t] : 0.0;
+}
 
 // The body of the tiled update.  INTERIOR: every thread of the block has both x and y neighbours
 // inside the grid, so the boundary tests fold away (about three quarters of the blocks at 256^2).
@@ -751,9 +788,9 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   if (CHECK) {
     for (int i = threadIdx.x + kTX * threadIdx.y; i < 64; i += kTX * kTY) smass[i] = 0.0;
   }
-  // residual and energy terms: per-thread partial sums in the working precision (at most 3 P terms),
+  // residual, energy and dual terms: per-thread compensated partial sums in the working precision,
   // every sum across threads in FP64
-  T r_db = 0, r_kx = 0, r_J = 0;
+  KSum<T> r_db, r_kx, r_J, r_w;
   pdl_wait();   // phi (inverse x/t pass) and the state are read from here on
 
   T phic[C], xfp[C], bbfp[C];
@@ -838,16 +875,18 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
 #pragma unroll
       for (int k = 0; k < 4; ++k) bb[c][k] = T(2) * bn[c][k] - lb[c][k];
       if (CHECK && out && write_plane) {
-        // per-cell terms in the working precision, sums in FP64
+        // per-cell terms in the working precision, sums compensated, then in FP64
         T db2 = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const T db = bn[c][k] - lb[c][k];
           db2 = fma(db, db, db2);
         }
-        r_db += db2;
-        r_kx += k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3;
-        if (V > T(0)) r_J += fdiv_fast(U0 * U0 + U1 * U1 + U2 * U2, T(2) * V);
+        r_db.add(db2);
+        r_kx.add(k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3);
+        if (V > T(0)) r_J.add(fdiv_fast(U0 * U0 + U1 * U1 + U2 * U2, T(2) * V));
+        const v4<T> wv = A.w[col + pt + c * sc];
+        r_w.add(bn[c][0] * wv.x + bn[c][1] * wv.y + bn[c][2] * wv.z + bn[c][3] * wv.w);
       }
     }
     // neighbours' bbar: x+1 by shuffle, y+1 through shared memory
@@ -903,32 +942,7 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
     for (int c = 0; c < C; ++c) qa[tlast * S + c * sc] = mk4<T>(cax[c], cay[c], cac[c], T(0));
   }
   pdl_trigger();
-  if (CHECK) {
-    __shared__ double red[kTY][3];
-    double d_db = (double)r_db, d_kx = (double)r_kx, d_J = (double)r_J;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      d_db += __shfl_xor_sync(0xffffffffu, d_db, o);
-      d_kx += __shfl_xor_sync(0xffffffffu, d_kx, o);
-      d_J += __shfl_xor_sync(0xffffffffu, d_J, o);
-    }
-    if (lane == 0) {
-      red[row][0] = d_db;
-      red[row][1] = d_kx;
-      red[row][2] = d_J;
-    }
-    __syncthreads();
-    const int tid = threadIdx.x + kTX * threadIdx.y;
-    const int nblk = gridDim.x * gridDim.y * nch;    // blocks of one problem
-    const int jb = ((blockIdx.z % nch) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    double* pp = part + ((size_t)b * nblk + jb) * kPart;
-    if (tid < 3) {
-      double sum = 0;
-      for (int i = 0; i < kTY; ++i) sum += red[i][tid];
-      pp[tid] = sum;
-    }
-    for (int t = tid; t < 64; t += kTX * kTY) pp[3 + t] = (t >= t0 && t < tend && t < g.P - 1) ? smass[t] : 0.0;
-  }
+  if (CHECK) block_check_partials<T>(r_db, r_kx, r_J, r_w, lane, row, nch, b, t0, tend, g.P, part, smass);
 }
 
 // PXY: the edge blocks handle periodic x / y (a separate instance, so that the Neumann kernel keeps its
@@ -951,7 +965,8 @@ static __global__ void k_reduce_check(const double* __restrict__ part, int nblk,
   const int b = blockIdx.x;
   const double* pb = part + (size_t)b * nblk * kPart;
   __shared__ double red[32];
-  for (int q = 0; q < 3 + P; ++q) {
+  for (int qi = 0; qi < 4 + P; ++qi) {
+    const int q = qi < 3 + P ? qi : kPartW;
     double s = 0;
     for (int j = threadIdx.x; j < nblk; j += blockDim.x) s += pb[(size_t)j * kPart + q];
 #pragma unroll
@@ -962,6 +977,7 @@ static __global__ void k_reduce_check(const double* __restrict__ part, int nblk,
       double t = 0;
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
       if (q < 3) acc[(size_t)b * kAcc + q] = t;
+      else if (q == kPartW) acc[(size_t)b * kAcc + 3] = t;
       else if (q - 3 < P) mass[(size_t)b * P + (q - 3)] = t;
     }
     __syncthreads();

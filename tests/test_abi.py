@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version_and_error_string_without_gpu(lib):
     lib.ot_abi_version.restype = ctypes.c_int
-    assert lib.ot_abi_version() == 1
+    assert lib.ot_abi_version() == 2
     lib.ot_last_error.restype = ctypes.c_char_p
     assert lib.ot_last_error() == b""
 
@@ -113,7 +113,7 @@ def test_header_and_library_from_plain_c(lib, tmp_path):
 int main(void) {
   ot_grid g;
   ot_plan_t p = 0;
-  if (ot_abi_version() != 1) return 1;
+  if (ot_abi_version() != OT_ABI_VERSION) return 1;
   ot_grid_rgb(&g, 64, 48, 16);
   if (g.ndim != 3 || g.n[0] != 64 || g.n[1] != 48 || g.n[2] != 3 || g.P != 16) return 2;
   g.P = 1;                                   /* below the supported range */

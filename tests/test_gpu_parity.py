@@ -208,8 +208,17 @@ def _solve_both(ot, n, bc, P, iters, f0, f1):
     plan, g = make_plan(ot, n, bc, P)
     stats = plan.solve(f32(f0), f32(f1), iters)
     path = plan.path()
-    st, infos, scale = o.solve(g, f0.astype(np.float64), f1.astype(np.float64), iters, SIG, TAU)
+    st, infos, scale = o.solve(g, f0.astype(np.float64), f1.astype(np.float64), iters, SIG, TAU, with_dual=True)
     return plan, g, stats, path, st, infos, scale
+
+
+def _check_dual(stats, info, scale):
+    """The dual value of the last check (FP64 sums of compensated per-thread partials) against the
+    oracle's, and the primal-dual gap formed from both sides' energy and dual value."""
+    D = info.dual * scale
+    assert abs(stats.dual_value - D) <= 1e-3 * abs(D)
+    gap = abs(info.energy - info.dual) / max(abs(info.energy), abs(info.dual))
+    assert abs(stats.gap - gap) <= 2e-3 + 1e-2 * gap
 
 
 def test_full_solve_rgb_32x32x3x16_500_iterations(ot):
@@ -223,6 +232,7 @@ def test_full_solve_rgb_32x32x3x16_500_iterations(ot):
     assert abs(stats.energy - infos[-1].energy * scale) <= 1e-3 * infos[-1].energy * scale
     assert abs(stats.residual - infos[-1].residual) <= 1e-2 * infos[-1].residual + 1e-7
     assert stats.mass_drift <= 1e-5
+    _check_dual(stats, infos[-1], scale)
 
 
 def test_full_solve_periodic_xy_24x20x3x8(ot):
@@ -274,6 +284,7 @@ def test_full_solve_hue_360x64(ot):
     u_gpu = o.S_M(g, [path["m"][0][0].astype(np.float64)])[0]
     assert rel(u_gpu, o.S_M(g, st.m)[0] * scale) <= 1e-3
     assert stats.mass_drift <= 1e-5
+    _check_dual(stats, infos[-1], scale)
 
 
 def test_batch_equals_single_problems(ot):
@@ -313,6 +324,32 @@ def test_input_validation(ot):
     # the plan still works afterwards
     st = plan.solve(f32(f0), f32(f1), 5)
     assert st.iterations == 5
+
+
+@pytest.mark.parametrize("n,P", [((64, 64, 3), 16), ((128, 96, 3), 17), ((64, 48), 8)])
+def test_staged_and_plain_update_kernels_agree(ot, n, P, monkeypatch):
+    """The update kernel that stages its planes with bulk tensor copies does the same arithmetic as the
+    plain-load one (DYNOT_UPDATE_KERNEL=plain); the compiler may contract a few products into fused
+    multiply-adds differently, so seven iterations from the same random state agree to float32 rounding,
+    amplified by the projection's correction A^T phi as in the parity bound (1e-5 relative), not bit for
+    bit."""
+    bc = RGB if len(n) == 3 else ("neumann", "neumann")
+    g = oracle_grid(n, bc, P)
+    f0, f1 = random_pair(g, 21)
+    st = _random_state(g, 22, smooth=True)
+    args = (f32(f0), f32(f1), f32(pack_path(g, st.m, st.f)), f32(pack_dual(g, st.bm, st.bf)),
+            f32(pack_dual(g, st.bbm, st.bbf)))
+    out = []
+    for kind in ("staged", "plain"):
+        if kind == "plain":
+            monkeypatch.setenv("DYNOT_UPDATE_KERNEL", "plain")
+        plan = ot.Plan(ot.grid(n, bc, P, sigma=SIG, tau=TAU))
+        plan.state_set(*args)
+        plan.iterate(7)
+        out.append(plan.state_get())
+        plan.close()
+    for a, b in zip(out[0], out[1]):
+        assert rel(a, b) <= 1e-5
 
 
 @pytest.mark.parametrize("where", ["dual", "path"])

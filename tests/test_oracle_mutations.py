@@ -45,6 +45,9 @@ MUTANTS = [
     ("pdhg_step", "a_f = sf + fbp + st.bf", "a_f = sf + st.bf"),
     ("pdhg_step", "bf = a_f - v", "bf = a_f + v"),
     ("pdhg_step", "bbf = bf + theta * (bf - st.bf)", "bbf = bf + theta * (st.bf - bf)"),
+    ("dual_value", "np.sum(bf * (sf + fbp))", "np.sum(bf * sf)"),
+    ("dual_value", "return sigma * tot / g.ncells", "return tot / g.ncells"),
+    ("min_norm_path", "m, f, _ = project(g, zm, np.zeros(g.f_shape), f0, f1)", "m, f = zm, np.zeros(g.f_shape)"),
 ]
 
 
@@ -106,6 +109,7 @@ def _pins():
     slv.test_remark1_nonunique_zero_energy()
     slv.test_equal_endpoints_give_zero_energy()
     slv.test_quantile_closed_form_1d_neumann()
+    slv.test_primal_dual_gap_vanishes_at_convergence()
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=["%s:%d" % (m[0], i) for i, m in enumerate(MUTANTS)])

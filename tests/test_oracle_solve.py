@@ -1,8 +1,9 @@
 """Pins of the oracle's full iteration (Algorithm 1) against facts the paper
 and the mathematics fix: mass conservation per time slice (from C_d), the
 zero-energy cases f0 = f1 and Remark 1, equivariance under a cyclic colour
-shift and under time reversal, translation of a blob, and the 1D quantile
-closed form of optimal transport on the line (section 1)."""
+shift and under time reversal, translation of a blob, the 1D quantile
+closed form of optimal transport on the line (section 1), and the vanishing of
+the primal-dual gap at the saddle point."""
 import numpy as np
 
 import oracle as o
@@ -39,6 +40,49 @@ def test_equal_endpoints_give_zero_energy():
     for k in range(g.P - 1):
         np.testing.assert_allclose(st.f[k], g0, rtol=0, atol=1e-4)
     assert max(np.abs(m).max() for m in st.m) < 1e-4
+
+
+def test_primal_dual_gap_vanishes_at_convergence():
+    """At a saddle point the energy of the prox output equals the dual value: J is 1-homogeneous, so
+    J(y) = <p, y> for p = sigma b in its subdifferential (step 2), y = K x + (0, f_b^+) (step 3 at a
+    fixed point), and K^T p lies in the range of A^T (optimality over C_d), where <K^T p, x> = <K^T p, x0>.
+    Solved to a splitting residual of 1e-11 the gap is below 1e-8 of the energy; early iterates have a
+    gap of order one or more."""
+    g = o.rgb_grid(6, 5, 4)
+    f0, f1 = _pair(g, 3, floor=0.3)
+    st, infos, _ = o.solve(g, f0, f1, 6000, SIG, 0.99 / SIG, with_dual=True, tol=1e-11, check_every=10)
+    last = infos[-1]
+    assert last.residual <= 1e-11
+    assert abs(last.energy - last.dual) <= 1e-8 * last.energy
+    assert abs(infos[0].energy - infos[0].dual) > 0.5 * infos[0].energy
+
+
+def test_primal_dual_gap_with_equal_endpoints():
+    """f0 = f1: the optimal energy is zero, and so is the dual value of the converged dual."""
+    g = o.rgb_grid(6, 6, 5)
+    f0, _ = _pair(g, 1)
+    _, infos, _ = o.solve(g, f0, f0.copy(), 1600, SIG, 0.99 / SIG, with_dual=True)
+    assert infos[-1].energy < 1e-12 and abs(infos[-1].dual) < 1e-10
+
+
+def test_min_norm_path_is_the_nearest_feasible_path():
+    """x0 = Pi_{C_d}(0) meets the continuity constraint and is orthogonal to ker A (so no feasible path is
+    shorter): every other feasible path x0 + w (w in ker A) is longer, with <x0, w> = 0."""
+    g = o.rgb_grid(5, 4, 4)
+    f0, f1 = _pair(g, 8)
+    g0, g1, _ = o.normalise_pair(g, f0, f1)
+    m0, fz = o.min_norm_path(g, g0, g1)
+    fbm = o.f_b_minus(g, g0, g1)
+    assert np.abs(o.A(g, m0, fz) - fbm).max() < 1e-12
+    n0 = sum(float(np.sum(a * a)) for a in m0) + float(np.sum(fz * fz))
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        zm = [rng.standard_normal(g.m_shape(k)) for k in range(g.d)]
+        zf = rng.standard_normal(g.f_shape)
+        pm, pf, _ = o.project(g, [a + b for a, b in zip(m0, zm)], fz + zf, g0, g1)   # another feasible path
+        n1 = sum(float(np.sum(a * a)) for a in pm) + float(np.sum(pf * pf))
+        inner = sum(float(np.sum(a * (b - a))) for a, b in zip(m0, pm)) + float(np.sum(fz * (pf - fz)))
+        assert n1 > n0 and abs(inner) < 1e-9 * n0
 
 
 def test_remark1_nonunique_zero_energy():
@@ -120,6 +164,10 @@ def test_quantile_closed_form_1d_neumann():
     W2sq = np.mean((Q1 - Q0) ** 2)
     E = infos[-1].energy
     assert abs(E - 0.5 * W2sq) < 0.03 * 0.5 * W2sq
+    # the dual value of the final dual iterate approaches the same optimal value
+    x0 = o.min_norm_path(g, f0, f1)
+    D = o.dual_value(g, st.bm, st.bf, x0, f0, f1, SIG)
+    assert abs(D - 0.5 * W2sq) < 0.03 * 0.5 * W2sq
     # CDF of the discrete f at t = k/P against the closed-form CDF
     for k in [P // 4, P // 2, 3 * P // 4]:
         t = k / P
