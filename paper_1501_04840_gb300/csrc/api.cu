@@ -267,6 +267,7 @@ ot_status ot_batch_create(const ot_grid* grids, int count, void* cuda_stream, ot
     for (size_t j = 0; j < keys.size(); ++j) {
       std::unique_ptr<PlanBase> p;
       OT_TRY(make_plan(keys[j], counts[j], nullptr, p));   // each group on a stream of its own
+      OT_TRY(p->enable_retirement());                      // converged problems stop iterating
       b->groups.push_back(std::move(p));
     }
     if (cuda_stream) {
@@ -300,12 +301,20 @@ ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* cons
       CUDA_OK(cudaEventRecord(b->join[i], b->groups[i]->st));
       CUDA_OK(cudaStreamWaitEvent(b->main, b->join[i], 0));
     }
+    // every problem starts active; one that meets tol at a check is retired: its kernels return at once
+    // from then on, so its state and path stay those of that check
+    std::vector<std::vector<int>> act(b->groups.size());
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+      act[i].assign(b->groups[i]->B, 1);
+      OT_TRY(b->groups[i]->set_active(act[i], b->main));
+    }
+    std::vector<int> its(count, 0);
+    int live = count;
     CUDA_OK(cudaEventRecord(b->t0, b->main));
     const int K = check_every > 0 ? check_every : iters;
     int done = 0;
-    bool converged = false;
     std::vector<std::vector<ProblemCheck>> per(b->groups.size());
-    while (done < iters) {
+    while (done < iters && live > 0) {
       const int chunk = std::min(K, iters - done);
       const int plain = chunk - 1;
       const int par = b->groups[0]->parity();
@@ -323,16 +332,22 @@ ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* cons
       }
       CUDA_OK(cudaStreamSynchronize(b->main));
       done += chunk;
-      double worst = 0;
-      for (size_t i = 0; i < b->groups.size(); ++i) {
-        OT_TRY(b->groups[i]->collect(per[i]));
-        for (const ProblemCheck& c : per[i]) worst = std::max(worst, c.residual);
+      for (size_t i = 0; i < b->groups.size(); ++i) OT_TRY(b->groups[i]->collect(per[i]));
+      std::vector<char> changed(b->groups.size(), 0);
+      for (int i = 0; i < count; ++i) {
+        const int gi = b->grp[i], k = b->idx[i];
+        if (!act[gi][k]) continue;
+        its[i] = done;
+        if (tol > 0 && per[gi][k].residual <= tol) {
+          act[gi][k] = 0;
+          changed[gi] = 1;
+          --live;
+        }
       }
-      if (tol > 0 && worst <= tol) {
-        converged = true;
-        break;
-      }
+      for (size_t i = 0; i < b->groups.size(); ++i)
+        if (changed[i]) OT_TRY(b->groups[i]->set_active(act[i], b->main));
     }
+    const bool converged = live == 0;
     CUDA_OK(cudaEventRecord(b->t1, b->main));
     CUDA_OK(cudaEventSynchronize(b->t1));
     float ms = 0;
@@ -340,7 +355,7 @@ ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* cons
     if (stats) {
       for (int i = 0; i < count; ++i) {
         const ProblemCheck& c = per[b->grp[i]][b->idx[i]];
-        stats[i].iterations = done;
+        stats[i].iterations = its[i];
         stats[i].residual = c.residual;
         stats[i].energy = c.energy;
         stats[i].mass_drift = c.drift;
@@ -349,7 +364,8 @@ ot_status ot_batch_solve(ot_batch_t b, const float* const* f0, const float* cons
         stats[i].elapsed_ms = ms;
       }
     }
-    if (tol > 0 && !converged) return seterr(OT_ENOTCONV, "batch: tolerance not reached after %d iterations", done);
+    if (tol > 0 && !converged)
+      return seterr(OT_ENOTCONV, "batch: %d problems above the tolerance after %d iterations", live, done);
     return OT_OK;
   });
 }

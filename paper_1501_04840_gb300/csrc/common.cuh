@@ -93,7 +93,15 @@ struct Geo {
   T sp;                 // P, factor of D_F
   T ts;                 // tau*sigma (step 1 of Algorithm 1)
   T sigma;              // step 2 of Algorithm 1
+  const int* active;    // per problem: 0 = retired (its blocks return at once); nullptr = all active
 };
+
+// A problem of a mixed-size batch that has met its tolerance is retired: every kernel of the iteration
+// returns at once for its blocks, so its state stays as it was at the check that retired it.
+template <typename T>
+__device__ __forceinline__ bool retired(const Geo<T>& g, int b) {
+  return g.active != nullptr && g.active[b] == 0;
+}
 
 // Four components of one cell, one aligned vector: float4 in FP32, 32-byte aligned in FP64.
 struct __align__(32) dvec4 {

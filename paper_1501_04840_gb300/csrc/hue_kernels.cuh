@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) k_hue_fwd(Geo<T> g, const v4<T>* __restri
                                                  const T* __restrict__ f1, T* __restrict__ hat, HueTables tb) {
   extern __shared__ __align__(16) char smraw[];
   const int t = blockIdx.x, b = blockIdx.y;
+  if (retired(g, b)) return;
   const int n = g.n1, P = g.P;
   T* row = (T*)smraw;
   c2<T>* cs = (c2<T>*)(smraw + ((sizeof(T) * n + 15) & ~size_t(15)));
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(256) k_hue_t(Geo<T> g, T* __restrict__ hat, Hu
   extern __shared__ __align__(16) char smraw[];
   constexpr int SL = 256 / PMAX, LD = PMAX + 1;
   const int P = g.P, n = g.n1, b = blockIdx.y;
+  if (retired(g, b)) return;
   T* Mf = (T*)smraw;            // [k][t], row stride LD
   T* Mi = Mf + PMAX * LD;       // [t][k]
   T* v = Mi + PMAX * LD;        // [SL][PMAX] input columns
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(256) k_hue_inv(Geo<T> g, const T* __restrict__
                                                  HueTables tb) {
   extern __shared__ __align__(16) char smraw[];
   const int t = blockIdx.x, b = blockIdx.y;
+  if (retired(g, b)) return;
   const int n = g.n1, P = g.P;
   T* row = (T*)smraw;
   c2<T>* cs = (c2<T>*)(smraw + ((sizeof(T) * n + 15) & ~size_t(15)));

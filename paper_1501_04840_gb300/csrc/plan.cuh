@@ -8,7 +8,9 @@
 #include <type_traits>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -34,7 +36,10 @@ inline int pmax_for(int P) { return P <= 16 ? 16 : (P <= 32 ? 32 : 64); }
 inline bool fft_len(int n) { return n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512; }
 inline int fft_n1(int n) { return n == 64 ? 8 : (n == 128 ? 8 : 16); }
 // threads per block of the y/colour pass (matches pick_kb)
-inline int yc_threads(int n2) { return fft_len(n2) ? 12 * fft_n1(n2) : 256; }
+// threads of the y/colour pass for strips of W columns: 3 W / 2 row pairs of length n2 per FFT chunk
+// (NT = 12 N1 at W = 8), 256 on the dense path
+constexpr int yc_nt(int m1, int w) { return w == 4 ? 6 * m1 : (w == 8 ? 12 * m1 : 24 * m1); }
+inline int yc_threads(int n2, int w = kW) { return fft_len(n2) ? yc_nt(fft_n1(n2), w) : 256; }
 
 inline size_t rnd16(size_t b) { return (b + 15) & ~size_t(15); }
 
@@ -100,17 +105,44 @@ template <typename T>
 KC<T> pick_kc(int n, int pm) {
   return pm == 16 ? pick_kc_p<T, 16>(n) : (pm == 32 ? pick_kc_p<T, 32>(n) : pick_kc_p<T, 64>(n));
 }
-template <typename T>
-KB<T> pick_kb(int n) {
+template <typename T> using KRX = void (*)(Geo<T>, const T*, T*, XtTables, int);
+template <typename T> using KCT = void (*)(Geo<T>, T*, const T*);
+template <typename T, bool INV>
+KRX<T> pick_krx(int n) {
   switch (n) {
-    case 64: return k_solve_yc<T, 8, 8, kW, 12 * 8>;
-    case 96: return k_solve_yc<T, 16, 6, kW, 12 * 16>;
-    case 128: return k_solve_yc<T, 8, 16, kW, 12 * 8>;
-    case 192: return k_solve_yc<T, 16, 12, kW, 12 * 16>;
-    case 256: return k_solve_yc<T, 16, 16, kW, 12 * 16>;
-    case 512: return k_solve_yc<T, 16, 32, kW, 12 * 16>;
+    case 64: return k_rows_x<T, 8, 8, INV>;
+    case 96: return k_rows_x<T, 16, 6, INV>;
+    case 128: return k_rows_x<T, 8, 16, INV>;
+    case 192: return k_rows_x<T, 16, 12, INV>;
+    case 256: return k_rows_x<T, 16, 16, INV>;
+    case 512: return k_rows_x<T, 16, 32, INV>;
+    default: return k_rows_x<T, 0, 0, INV>;
+  }
+}
+template <typename T>
+KCT<T> pick_kct(int pm) {
+  return pm == 16 ? k_cols_t<T, 16> : (pm == 32 ? k_cols_t<T, 32> : k_cols_t<T, 64>);
+}
+template <typename T, int W>
+KB<T> pick_kb_w(int n) {
+  switch (n) {
+    case 64: return k_solve_yc<T, 8, 8, W, yc_nt(8, W)>;
+    case 96: return k_solve_yc<T, 16, 6, W, yc_nt(16, W)>;
+    case 128: return k_solve_yc<T, 8, 16, W, yc_nt(8, W)>;
+    case 192: return k_solve_yc<T, 16, 12, W, yc_nt(16, W)>;
+    case 256: return k_solve_yc<T, 16, 16, W, yc_nt(16, W)>;
+    case 512: return k_solve_yc<T, 16, 32, W, yc_nt(16, W)>;
     default: return k_solve_yc<T, 0, 0, kW, 256>;
   }
+}
+// strips of 4, 8 or 16 columns on the FFT lengths (FP32; the FP64 plan keeps 8)
+template <typename T>
+KB<T> pick_kb(int n, int w = kW) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (fft_len(n) && w == 4) return pick_kb_w<T, 4>(n);
+    if (fft_len(n) && w == 16) return pick_kb_w<T, 16>(n);
+  }
+  return pick_kb_w<T, kW>(n);
 }
 template <typename T> using KD = void (*)(Geo<T>, Arrays<T>, int, double*);
 
@@ -199,6 +231,8 @@ struct Plan final : PlanBase {
   double* scl = nullptr;    // [B][2]
   double* part = nullptr;   // per-block partial sums of the residual check
   int* err = nullptr;       // set by a kernel whose bounded device wait ran out (sticky until the next start)
+  int* active = nullptr;    // [B] per-problem flags of a retiring batch (g.active points here once enabled)
+  std::vector<int> h_active;
   int* h_err = nullptr;     // pinned host copy, read with the residuals
   double* h_acc = nullptr;  // pinned host copies of acc and mass
   double* h_mass = nullptr;
@@ -209,9 +243,15 @@ struct Plan final : PlanBase {
   HueTables ht{};
   int pmax = 32;
   int scrA = 0, scrB = 0;
+  int yw = kW;              // column-strip width of the y/colour pass (autotuned on the FFT lengths)
   size_t smA = 0, smB = 0, smH = 0, smHt = 0;
   KA<T> ka = nullptr;
   KC<T> kc = nullptr;
+  bool split_xt = false;    // separate r, x and t launches (the (t, x) plane exceeds shared memory)
+  KRX<T> krx_f = nullptr, krx_i = nullptr;
+  KCT<T> kct = nullptr;
+  int scrS = 0;
+  size_t smR = 0, smT = 0;
   KB<T> kb = nullptr;
   KH<T> kh = nullptr;
   bool tiled = false;       // tiled update kernel (up to four colour channels)
@@ -247,7 +287,7 @@ struct Plan final : PlanBase {
   size_t yc_smem() const {
     T *t0, *t1, *t2, *t3;
     c2<T> *c0, *c1, *c3;
-    return yc_layout<T>(nullptr, C, n2, kW, scrB, !y_fft(), &t0, &c0, &c1, &c3, &t1, &t2, &t3);
+    return yc_layout<T>(nullptr, C, n2, yw, scrB, !y_fft(), &t0, &c0, &c1, &c3, &t1, &t2, &t3);
   }
 
   ot_status init() override {
@@ -273,7 +313,7 @@ struct Plan final : PlanBase {
     size_t bytes = narr * rnd16(cells * sizeof(T)) + 2 * rnd16((size_t)B * S * sizeof(T)) +
                    rnd16(stage_floats * sizeof(float)) + rnd16(sizeof(double) * B * kAcc) +
                    rnd16(sizeof(double) * (size_t)B * P) + rnd16(sizeof(double) * B * kChk) +
-                   rnd16(sizeof(double) * B * 2) + rnd16(part_bytes()) + 16;
+                   rnd16(sizeof(double) * B * 2) + rnd16(part_bytes()) + 16 + rnd16(sizeof(int) * B);
     CUDA_OK(cudaMalloc(&mem.p, bytes));
     char* q = (char*)mem.p;
     auto take = [&](size_t nb) { char* r = q; q += rnd16(nb); return r; };
@@ -292,6 +332,7 @@ struct Plan final : PlanBase {
     scl = (double*)take(sizeof(double) * B * 2);
     part = (double*)take(part_bytes());
     err = (int*)take(sizeof(int));
+    active = (int*)take(sizeof(int) * B);
     CUDA_OK(cudaMemsetAsync(mem.p, 0, bytes, st));
 
     OT_TRY(build_tables());
@@ -309,28 +350,29 @@ struct Plan final : PlanBase {
       if (tiled && DYNOT_UPD_TMA && !plain && !g.per1 && !g.per2 && n1 % 4 == 0 && n1 >= kTX && n2 >= kTY)
         OT_TRY(make_tensor_maps());
     }
-    if (tiled) OT_TRY(tune_update());
+    OT_TRY(tune());
     return OT_OK;
   }
 
-  // Tensor maps of the TMA-staged update: a and b as [B P][C][n2][n1][4] (the four components innermost),
-  // boxes of 33 x 9 cells (a, with the column left and the row below the 32 x 8 tile) and 32 x 8 cells (b);
-  // phi as [B P][C][n2][n1], boxes of 40 x 10 cells.  Out-of-range cells read as zero.
+  // Tensor maps of the TMA-staged update: a and b as float tensors [B P][C][n2][4 n1] (a cell's four components
+  // are consecutive, so one box row is one run of 16-byte cells), boxes of 33 x 9 cells (a, with the column left
+  // and the row below the 32 x 8 tile) and 32 x 8 cells (b); phi as [B P][C][n2][n1], boxes of 40 x 10 cells.
+  // Out-of-range cells read as zero.
   ot_status make_tensor_maps() {
     auto enc = tensor_map_encoder();
     if (!enc) return OT_OK;   // no driver entry point: keep the plain-load update
     const cuuint64_t BP = (cuuint64_t)B * P;
-    const cuuint64_t dim5[5] = {4, (cuuint64_t)n1, (cuuint64_t)n2, (cuuint64_t)C, BP};
-    const cuuint64_t str5[4] = {16, 16ull * n1, 16ull * n1 * n2, 16ull * S};
-    const cuuint32_t boxA[5] = {4, kTX + 1, kTY + 1, (cuuint32_t)C, 1};
-    const cuuint32_t boxB[5] = {4, kTX, kTY, (cuuint32_t)C, 1};
-    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+    const cuuint64_t dimS[4] = {4ull * n1, (cuuint64_t)n2, (cuuint64_t)C, BP};
+    const cuuint64_t strS[3] = {16ull * n1, 16ull * n1 * n2, 16ull * S};
+    const cuuint32_t boxA[4] = {4 * (kTX + 1), kTY + 1, (cuuint32_t)C, 1};
+    const cuuint32_t boxB[4] = {4 * kTX, kTY, (cuuint32_t)C, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
     for (int i = 0; i < 2; ++i) {
-      CUresult r = enc(&tmA[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)a[i], dim5, str5, boxA, one,
+      CUresult r = enc(&tmA[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a[i], dimS, strS, boxA, one,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return OT_OK;   // the driver cannot describe this tensor: keep the plain-load update
-      r = enc(&tmB[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)b[i], dim5, str5, boxB, one,
+      r = enc(&tmB[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)b[i], dimS, strS, boxB, one,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return OT_OK;
@@ -344,16 +386,75 @@ struct Plan final : PlanBase {
     if (r != CUDA_SUCCESS) return OT_OK;
     const size_t smem = tma_smem(C);
     for (int ck = 0; ck < 2; ++ck)
-      for (int wx = 0; wx < 2; ++wx)
-        CUDA_OK(cudaFuncSetAttribute((const void*)pick_kdt(C, ck, wx), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    use_tma = true;
+      for (int wx = 0; wx < 2; ++wx) {
+        const void* fn = (const void*)pick_kdt(C, ck, wx);
+        CUDA_OK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // the operands come from shared memory: take the largest shared-memory carve-out of the unified L1
+        CUDA_OK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+      }
+    tma_ok = use_tma = true;
     return OT_OK;
   }
 
-  // Autotuner of the tiled update: time chunk lengths P, P/2, P/4, P/8 on the
-  // zeroed workspace and keep the fastest (ties go to the longer chunk).
-  ot_status tune_update() {
+  // Autotuner, run once per shape and device (the choice is cached for later plans of the shape):
+  //  - the y/colour pass: column strips of 4, 8 or 16 (FFT lengths, FP32) with 6, 12 or 24 row pairs per
+  //    FFT chunk;
+  //  - the tiled update: staged by bulk tensor copies or with plain loads (where both exist), and time chunks
+  //    of P, P/2, P/4 or P/8 planes.
+  // Each candidate is timed over three launches on the zeroed workspace (b set so that the prox takes its
+  // Newton branch); a later candidate must beat the best by 3 % (ties keep the earlier, simpler one).
+  struct Tuned {
+    int yw = kW, tc = 0;
+    bool tma = false;
+  };
+  static std::mutex& tune_mu() {
+    static std::mutex m;
+    return m;
+  }
+  static std::map<std::string, Tuned>& tune_cache() {
+    static std::map<std::string, Tuned> c;
+    return c;
+  }
+  std::string shape_key() const {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d:%d:%d%d%d:%d:%d", (int)sizeof(T), n1, n2, C, P, B, g.per1, g.per2,
+                  g.perc, device, (int)tma_ok);
+    return buf;
+  }
+  bool tma_ok = false;      // tensor maps exist: the staged update is a candidate
+
+  // y/colour pass with strips of w columns; false when its shared memory does not fit
+  bool set_yw(int w) {
+    if (hue) return false;
+    const int old = yw;
+    yw = w;
+    scrB = y_fft() ? (yc_threads(n2, yw) / fft_n1(n2)) * n2 : 4 * n2;
+    const size_t need = yc_smem();
+    int maxsm = 0;
+    if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        (int)need > maxsm) {
+      yw = old;
+      scrB = y_fft() ? (yc_threads(n2, yw) / fft_n1(n2)) * n2 : 4 * n2;
+      return false;
+    }
+    smB = need;
+    kb = pick_kb<T>(y_fft() ? n2 : 0, yw);
+    return cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm) == cudaSuccess;
+  }
+
+  template <class F>
+  ot_status time3(F&& launch, float& ms) {
+    launch();   // warm
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaEventRecord(ev[10], st));
+    for (int r = 0; r < 3; ++r) launch();
+    CUDA_OK(cudaEventRecord(ev[11], st));
+    CUDA_OK(cudaEventSynchronize(ev[11]));
+    CUDA_OK(cudaEventElapsedTime(&ms, ev[10], ev[11]));
+    return OT_OK;
+  }
+
+  ot_status tune() {
     std::vector<int> cands;
     for (int d = 1; d <= 8; d *= 2) {
       const int c = (P + d - 1) / d;
@@ -361,33 +462,65 @@ struct Plan final : PlanBase {
         if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
     }
     tc = cands[0];
-    if (cands.size() == 1) return OT_OK;
+    use_tma = tma_ok;
+    const std::string key = shape_key();
+    {
+      std::lock_guard<std::mutex> lk(tune_mu());
+      auto it = tune_cache().find(key);
+      if (it != tune_cache().end()) {
+        if (it->second.yw != yw) set_yw(it->second.yw);
+        tc = it->second.tc;
+        use_tma = it->second.tma;
+        return OT_OK;
+      }
+    }
     // a state on which the prox takes its Newton branch: b_f = 1, b_m = 0.5, a = phi = 0
     const long long cells = (long long)B * N;
     k_fill<v4<T>><<<grid1d(cells), 256, 0, st>>>(cells, mk4<T>(T(0.5), T(0.5), T(0.5), T(1)), b[0]);
     CUDA_OK(cudaGetLastError());
-    float best = 1e30f;
-    for (int c : cands) {
-      tc = c;
-      enqueue_update(0, false, false);  // warm
-      CUDA_OK(cudaGetLastError());
-      CUDA_OK(cudaEventRecord(ev[10], st));
-      for (int r = 0; r < 3; ++r) enqueue_update(0, false, false);
-      CUDA_OK(cudaEventRecord(ev[11], st));
-      CUDA_OK(cudaEventSynchronize(ev[11]));
-      float ms = 0;
-      CUDA_OK(cudaEventElapsedTime(&ms, ev[10], ev[11]));
-      if (ms < 0.97f * best) {
-        best = ms;
-        tune_tc = c;
+    if (!hue && y_fft() && std::is_same<T, float>::value) {
+      float best = 1e30f;
+      int bw = yw;
+      for (int w : {kW, 4, 16}) {
+        if (!set_yw(w)) continue;
+        float ms = 0;
+        OT_TRY(time3([&] {
+          launch_pdl(kb, dim3((n1 + yw - 1) / yw, P, B), dim3(yc_threads(n2, yw)), smB, st, g, hat, yc, scrB);
+        }, ms));
+        if (ms < 0.97f * best) {
+          best = ms;
+          bw = w;
+        }
       }
+      set_yw(bw);
     }
-    tc = tune_tc;
+    if (tiled) {
+      float best = 1e30f;
+      Tuned pick{yw, tc, use_tma};
+      for (int kind = 0; kind < (tma_ok ? 2 : 1); ++kind) {
+        use_tma = tma_ok && kind == 0;
+        for (int c : cands) {
+          tc = c;
+          float ms = 0;
+          OT_TRY(time3([&] { enqueue_update(0, false, false); }, ms));
+          if (ms < 0.97f * best) {
+            best = ms;
+            pick.tc = c;
+            pick.tma = use_tma;
+          }
+        }
+      }
+      tc = pick.tc;
+      use_tma = pick.tma;
+    }
+    tune_tc = tc;
     // clear both buffer sets again
     for (int i = 0; i < 2; ++i) {
       CUDA_OK(cudaMemsetAsync(a[i], 0, (size_t)B * N * sizeof(v4<T>), st));
       CUDA_OK(cudaMemsetAsync(b[i], 0, (size_t)B * N * sizeof(v4<T>), st));
     }
+    std::lock_guard<std::mutex> lk(tune_mu());
+    tune_cache()[key] = Tuned{yw, tc, use_tma};
     return OT_OK;
   }
   int tune_tc = 0;
@@ -559,7 +692,7 @@ struct Plan final : PlanBase {
       yc.Qc = base + o_Q; yc.lamc = base + o_lc; yc.lamcd = (const double*)(base + o_lcd);
       yc.lam_fp64 = thr;
       scrA = x_fft() ? (kThreadsXt / fft_n1(n1)) * n1 : 4 * n1;
-      scrB = y_fft() ? (yc_threads(n2) / fft_n1(n2)) * n2 : 4 * n2;
+      scrB = y_fft() ? (yc_threads(n2, yw) / fft_n1(n2)) * n2 : 4 * n2;
       ka = pick_ka<T>(x_fft() ? n1 : 0, pmax);
       kc = pick_kc<T>(x_fft() ? n1 : 0, pmax);
       kb = pick_kb<T>(y_fft() ? n2 : 0);
@@ -567,13 +700,33 @@ struct Plan final : PlanBase {
       smB = yc_smem();
       int maxsm = 0;
       CUDA_OK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
-      if ((int)smA > maxsm || (int)smB > maxsm)
-        return seterr(OT_EUNSUPPORTED, "grid needs %zu / %zu bytes of shared memory per block (max %d)", smA, smB,
-                      maxsm);
+      // a (t, x) plane too large for one block's shared memory takes the split x/t passes
+      // (DYNOT_SPLIT_XT=1 selects them for any grid, for comparisons)
+      const char* sx = std::getenv("DYNOT_SPLIT_XT");
+      split_xt = (int)smA > maxsm || (sx && std::strcmp(sx, "1") == 0);
+      if (split_xt) {
+        scrS = x_fft() ? (256 / fft_n1(n1)) * n1 : (kRowsX * n1 + 1) / 2;
+        T *t0p, *t1p;
+        c2<T> *c0p, *c1p, *c2p;
+        smR = rows_x_layout<T>(nullptr, n1, scrS, !x_fft(), &t0p, &c0p, &c1p, &c2p, &t1p);
+        smT = sizeof(T) * ((size_t)P * pmax + (size_t)P * kColsT);
+        krx_f = pick_krx<T, false>(x_fft() ? n1 : 0);
+        krx_i = pick_krx<T, true>(x_fft() ? n1 : 0);
+        kct = pick_kct<T>(pmax);
+      }
+      if ((!split_xt && (int)smA > maxsm) || (int)smB > maxsm || (split_xt && ((int)smR > maxsm || (int)smT > maxsm)))
+        return seterr(OT_EUNSUPPORTED, "grid needs %zu / %zu bytes of shared memory per block (max %d)",
+                      split_xt ? std::max(smR, smT) : smA, smB, maxsm);
       // The limit is a property of the kernel, shared by every plan that uses it:
       // raise it to the device maximum instead of this plan's size.
-      CUDA_OK(cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-      CUDA_OK(cudaFuncSetAttribute((const void*)kc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+      if (split_xt) {
+        CUDA_OK(cudaFuncSetAttribute((const void*)krx_f, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+        CUDA_OK(cudaFuncSetAttribute((const void*)krx_i, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+        CUDA_OK(cudaFuncSetAttribute((const void*)kct, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+      } else {
+        CUDA_OK(cudaFuncSetAttribute((const void*)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+        CUDA_OK(cudaFuncSetAttribute((const void*)kc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+      }
       CUDA_OK(cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     } else {
       ht.cs = base + o_cs; ht.lam = base + o_hl; ht.lamd = (const double*)(base + o_hld);
@@ -615,12 +768,28 @@ struct Plan final : PlanBase {
   void enqueue_poisson_src(const v4<T>* asrc, cudaEvent_t* evs) {
     if (!hue) {
       if (evs) cudaEventRecord(evs[0], st);
-      launch_pdl(ka, dim3(n2, C, B), dim3(kThreadsXt), smA, st, g, asrc, (const T*)f0n, (const T*)f1n, hat, xt,
-                 scrA);
+      if (split_xt) {
+        k_rhs_cells<T><<<grid1d((long long)B * N), 256, 0, st>>>(g, asrc, (const T*)f0n, (const T*)f1n, hat);
+        launch_pdl(krx_f, dim3((P + kRowsX - 1) / kRowsX, n2 * C, B), dim3(256), smR, st, g, (const T*)hat, hat, xt,
+                   scrS);
+        launch_pdl(kct, dim3((n1 + kColsT - 1) / kColsT, n2 * C, B), dim3(kColsT), smT, st, g, hat,
+                   (const T*)xt.Mt_f);
+      } else {
+        launch_pdl(ka, dim3(n2, C, B), dim3(kThreadsXt), smA, st, g, asrc, (const T*)f0n, (const T*)f1n, hat, xt,
+                   scrA);
+      }
       if (evs) cudaEventRecord(evs[1], st);
-      launch_pdl(kb, dim3((n1 + kW - 1) / kW, P, B), dim3(yc_threads(y_fft() ? n2 : 0)), smB, st, g, hat, yc, scrB);
+      launch_pdl(kb, dim3((n1 + yw - 1) / yw, P, B), dim3(yc_threads(y_fft() ? n2 : 0, yw)), smB, st, g, hat, yc,
+                 scrB);
       if (evs) cudaEventRecord(evs[2], st);
-      launch_pdl(kc, dim3(n2, C, B), dim3(kThreadsXt), smA, st, g, (const T*)hat, phi, xt, scrA);
+      if (split_xt) {
+        launch_pdl(kct, dim3((n1 + kColsT - 1) / kColsT, n2 * C, B), dim3(kColsT), smT, st, g, hat,
+                   (const T*)xt.Mt_i);
+        launch_pdl(krx_i, dim3((P + kRowsX - 1) / kRowsX, n2 * C, B), dim3(256), smR, st, g, (const T*)hat, phi, xt,
+                   scrS);
+      } else {
+        launch_pdl(kc, dim3(n2, C, B), dim3(kThreadsXt), smA, st, g, (const T*)hat, phi, xt, scrA);
+      }
       if (evs) cudaEventRecord(evs[3], st);
     } else {
       if (evs) cudaEventRecord(evs[0], st);
@@ -660,7 +829,7 @@ struct Plan final : PlanBase {
         }
       }
       if (!done) launch_pdl(pick_kd<T>(C, check, wx, g.per1 || g.per2), grd, dim3(kTX, kTY), 0, st, g, A, tc, part);
-      if (check) k_reduce_check<<<B, 256, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass);
+      if (check) k_reduce_check<<<B, 256, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass, g.active);
       return;
     }
     const dim3 grd((n1 + kThreadsUpd - 1) / kThreadsUpd, n2, C * P * B);
@@ -733,10 +902,11 @@ struct Plan final : PlanBase {
 
   // per-problem residual, energy (caller units) and mass drift of the last check (after a sync)
   ot_status collect_check(std::vector<ProblemCheck>& per, Check& out) {
-    per.assign(B, ProblemCheck{});
+    per.resize(B);
     out = Check{};
     if (*h_err) return seterr(OT_ETIMEOUT, "a bounded device wait of the update kernel ran out of its limit");
     for (int bi = 0; bi < B; ++bi) {
+      if (g.active && !h_active[bi]) continue;   // retired: its entry keeps the check that retired it
       const double* q = &h_acc[(size_t)bi * kAcc];
       const double res = std::sqrt(q[0]) / std::max(std::sqrt(q[1]), 1e-300);
       if (!std::isfinite(res) || !std::isfinite(q[2]) || !std::isfinite(q[3]))
@@ -1011,6 +1181,22 @@ struct Plan final : PlanBase {
     return collect_check(per, ck);
   }
   int parity() const override { return par; }
+
+  ot_status enable_retirement() override {
+    if (gexec[0] || gexec[1]) return seterr(OT_EINVAL, "retirement must be enabled before graphs are captured");
+    h_active.assign(B, 1);
+    CUDA_OK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    CUDA_OK(cudaStreamSynchronize(st));
+    g.active = active;
+    return OT_OK;
+  }
+  ot_status set_active(const std::vector<int>& act, cudaStream_t s) override {
+    if (!g.active || (int)act.size() != B) return seterr(OT_EINVAL, "retirement is not enabled for this plan");
+    h_active = act;
+    CUDA_OK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    return OT_OK;
+  }
 
   ot_status path_one(int bi, float* f, float* m0, float* m1, float* m2) override {
     if (!have_x) return seterr(OT_EINVAL, "no path: run a solve first");

@@ -85,6 +85,11 @@ struct PlanBase {
   virtual ot_status enqueue_check_async() = 0;
   virtual ot_status collect(std::vector<ProblemCheck>& per) = 0;
   virtual int parity() const = 0;
+  // per-problem retirement (mixed-size batches): enable_retirement() before any graph is captured makes
+  // every kernel skip the problems whose flag is 0; set_active uploads the flags on stream s, and collect
+  // leaves the entries of retired problems as they were
+  virtual ot_status enable_retirement() = 0;
+  virtual ot_status set_active(const std::vector<int>& act, cudaStream_t s) = 0;
   virtual ot_status path_one(int bi, float* f, float* m0, float* m1, float* m2) = 0;
 };
 

@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(128) k_update(Geo<T> g, Arrays<T> A, double* _
   z /= g.C;
   const int t = z % g.P;
   const int b = z / g.P;
+  if (retired(g, b)) return;
   const bool live = x < g.n1;
   double r_db = 0, r_kx = 0, r_J = 0, r_m = 0, r_w = 0;
   if (live) {
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, con
                                                     T* __restrict__ rhat, XtTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int y = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
+  if (retired(g, b)) return;
   const int n1 = g.n1, P = g.P;
   XtSmem<T> s;
   xt_layout<T>(&s, smraw, P, n1, PMAX, scr_elems, N1 == 0);
@@ -463,12 +465,132 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, con
     for (int x = threadIdx.x; x < n1; x += blockDim.x) rhat[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
 }
 
+// ---------------------------------------------------------------------------
+// Split x/t passes, for grids whose whole (t, x) plane of one (y, c) does not fit shared memory (the FP64
+// plan at n1 = 512, P = 64).  The same transforms as K_A and K_C in separate launches:
+//   k_rhs_cells : r = A a - f_b^- into hat, one cell per thread;
+//   k_rows_x    : the DCT-II along x (or its inverse) of kRowsX rows [t][x] of one (y, c) per block, from
+//                 src into dst (in place when they are the same array);
+//   k_cols_t    : the DCT-II along t (or its inverse) of kColsT columns of one (y, c) per block, in place,
+//                 as the dense product with the transform matrix.
+// ---------------------------------------------------------------------------
+constexpr int kRowsX = 16, kColsT = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rhs_cells(Geo<T> g, const v4<T>* __restrict__ ap, const T* __restrict__ f0,
+                                                   const T* __restrict__ f1, T* __restrict__ r) {
+  const long long tot = (long long)g.B * g.N;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    long long q = id;
+    const int x = q % g.n1; q /= g.n1;
+    const int y = q % g.n2; q /= g.n2;
+    const int c = q % g.C; q /= g.C;
+    const int t = q % g.P;
+    const int b = (int)(q / g.P);
+    if (retired(g, b)) continue;
+    const v4<T> av = ap[id];
+    const int xm = x > 0 ? x - 1 : (g.per1 ? g.n1 - 1 : -1);
+    const int ym = y > 0 ? y - 1 : (g.per2 ? g.n2 - 1 : -1);
+    const int cm = c > 0 ? c - 1 : (g.perc ? g.C - 1 : -1);
+    const size_t sb = (size_t)b * g.S + x + (size_t)g.n1 * (y + (size_t)g.n2 * c);
+    T v = g.s1 * (av.x - (xm >= 0 ? comp<T>(ap, cidx(g, b, t, xm, y, c), 0) : T(0)));
+    v += g.s2 * (av.y - (ym >= 0 ? comp<T>(ap, cidx(g, b, t, x, ym, c), 1) : T(0)));
+    v += g.sc * (av.z - (cm >= 0 ? comp<T>(ap, cidx(g, b, t, x, y, cm), 2) : T(0)));
+    const T fnext = (t == g.P - 1) ? f1[sb] : av.w;
+    const T fprev = (t == 0) ? f0[sb] : comp<T>(ap, id - g.S, 3);
+    v += g.sp * (fnext - fprev);
+    r[id] = v;
+  }
+}
+
+// Shared memory of k_rows_x: the row tile, the FFT scratch (or the dense scratch) and the tables.
+template <typename T>
+__host__ __device__ __forceinline__ size_t rows_x_layout(char* sm, int n1, int scr_elems, bool dense, T** tile,
+                                                         c2<T>** scr, c2<T>** tw, c2<T>** hw, T** cos4) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = sm + off; off += (bytes + 15) & ~size_t(15); return p; };
+  *tile = (T*)take(sizeof(T) * (size_t)kRowsX * n1);
+  *scr = (c2<T>*)take(sizeof(c2<T>) * (size_t)scr_elems);
+  *tw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n1);
+  *hw = dense ? nullptr : (c2<T>*)take(sizeof(c2<T>) * n1);
+  *cos4 = dense ? (T*)take(sizeof(T) * 4 * n1) : nullptr;
+  return off;
+}
+
+template <typename T, int N1, int N2, bool INV>
+__global__ void __launch_bounds__(256) k_rows_x(Geo<T> g, const T* __restrict__ src, T* __restrict__ dst,
+                                                XtTables tb, int scr_elems) {
+  extern __shared__ __align__(16) char smraw[];
+  const int t0 = blockIdx.x * kRowsX, yc = blockIdx.y, b = blockIdx.z;
+  if (retired(g, b)) return;
+  const int n1 = g.n1, P = g.P;
+  const int nr = min(kRowsX, P - t0), nre = nr + (nr & 1);   // rows of this block, even for the pairs
+  T *tile, *cos4;
+  c2<T> *scr, *tw, *hw;
+  rows_x_layout<T>(smraw, n1, scr_elems, N1 == 0, &tile, &scr, &tw, &hw, &cos4);
+  if (N1) load_tables<T>(tw, hw, (const c2<T>*)tb.tw, (const c2<T>*)tb.hw, n1);
+  else for (int j = threadIdx.x; j < 4 * n1; j += blockDim.x) cos4[j] = ((const T*)tb.cos4)[j];
+  pdl_wait();
+  const size_t base = ((size_t)b * P + t0) * g.S + (size_t)yc * n1;   // row t0 of (y, c) = yc
+  for (int i = threadIdx.x; i < nre * n1; i += blockDim.x) {
+    const int r = i / n1, x = i - r * n1;
+    tile[i] = r < nr ? src[base + (size_t)r * g.S + x] : T(0);
+  }
+  __syncthreads();
+  Rows<T, 1, 1> rows{tile, n1, 0};
+  if constexpr (N1 > 0) {
+    if (g.per1) {
+      if (INV) DctPow2<T, N1, N2, false, 256, true>::inverse(rows, nre, scr, tw, hw);
+      else DctPow2<T, N1, N2, false, 256, true>::forward(rows, nre, scr, tw, hw);
+    } else {
+      if (INV) DctPow2<T, N1, N2, false, 256>::inverse(rows, nre, scr, tw, hw);
+      else DctPow2<T, N1, N2, false, 256>::forward(rows, nre, scr, tw, hw);
+    }
+  } else {
+    if (g.per1) rdft_dense_rows<T, false>(rows, nr, n1, INV, (T*)scr, 2 * scr_elems, (const c2<T>*)cos4);
+    else dct_dense_rows<T, false>(rows, nr, n1, INV, (T*)scr, 2 * scr_elems, cos4);
+  }
+  __syncthreads();
+  pdl_trigger();
+  for (int i = threadIdx.x; i < nr * n1; i += blockDim.x) {
+    const int r = i / n1, x = i - r * n1;
+    dst[base + (size_t)r * g.S + x] = tile[i];
+  }
+}
+
+template <typename T, int PMAX>
+__global__ void __launch_bounds__(kColsT) k_cols_t(Geo<T> g, T* __restrict__ hat, const T* __restrict__ Mt_g) {
+  extern __shared__ __align__(16) char smraw[];
+  const int x0 = blockIdx.x * kColsT, yc = blockIdx.y, b = blockIdx.z;
+  if (retired(g, b)) return;
+  const int n1 = g.n1, P = g.P;
+  const int w = min(kColsT, n1 - x0);
+  T* Mt = (T*)smraw;                  // [P][PMAX]
+  T* tile = Mt + (size_t)P * PMAX;    // [P][kColsT]
+  for (int j = threadIdx.x; j < P * PMAX; j += blockDim.x) Mt[j] = Mt_g[j];
+  pdl_wait();
+  const size_t base = (size_t)b * P * g.S + (size_t)yc * n1 + x0;
+  for (int i = threadIdx.x; i < P * kColsT; i += blockDim.x) {
+    const int t = i / kColsT, x = i - t * kColsT;
+    tile[i] = x < w ? hat[base + (size_t)t * g.S + x] : T(0);
+  }
+  __syncthreads();
+  dct_cols<T, PMAX>(tile, kColsT, w, P, Mt);
+  __syncthreads();
+  pdl_trigger();
+  for (int i = threadIdx.x; i < P * kColsT; i += blockDim.x) {
+    const int t = i / kColsT, x = i - t * kColsT;
+    if (x < w) hat[base + (size_t)t * g.S + x] = tile[i];
+  }
+}
+
 // K_C: inverse DCT along t and x -> phi
 template <typename T, int N1, int N2, int PMAX>
 __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const T* __restrict__ phihat, T* __restrict__ phi,
                                                 XtTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int y = blockIdx.x, c = blockIdx.y, b = blockIdx.z;
+  if (retired(g, b)) return;
   const int n1 = g.n1, P = g.P;
   XtSmem<T> s;
   xt_layout<T>(&s, smraw, P, n1, PMAX, scr_elems, N1 == 0);
@@ -567,6 +689,7 @@ template <typename T, int M1, int M2, int W, int NT>
 __global__ void __launch_bounds__(NT, 768 / NT) k_solve_yc(Geo<T> g, T* __restrict__ hat, YcTables tb, int scr_elems) {
   extern __shared__ __align__(16) char smraw[];
   const int x0 = blockIdx.x * W, kt = blockIdx.y, b = blockIdx.z;
+  if (retired(g, b)) return;
   const int n1 = g.n1, n2 = g.n2, C = g.C;
   const int w_act = min(W, n1 - x0);
   const int cst = yc_cstride(n2, W);
@@ -750,6 +873,7 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   const int y = blockIdx.y * (kTY - 1) + row;
   const int nch = (g.P + TC - 1) / TC;
   const int b = blockIdx.z / nch;
+  if (retired(g, b)) return;
   const int t0 = (blockIdx.z % nch) * TC;
   const int tend = min(t0 + TC, g.P);           // planes [t0, tend) are written
   const int tlast = min(tend, g.P - 1);          // planes [t0, tlast] are computed
@@ -961,8 +1085,9 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
 
 // Sum the per-block partials of each problem (one block per problem) into acc and mass.
 static __global__ void k_reduce_check(const double* __restrict__ part, int nblk, int P, double* __restrict__ acc,
-                               double* __restrict__ mass) {
+                               double* __restrict__ mass, const int* __restrict__ active) {
   const int b = blockIdx.x;
+  if (active != nullptr && active[b] == 0) return;
   const double* pb = part + (size_t)b * nblk * kPart;
   __shared__ double red[32];
   for (int qi = 0; qi < 4 + P; ++qi) {

@@ -98,6 +98,7 @@ __device__ __forceinline__ void update_tma_body(const Geo<float>& g, const Array
   const int x = x0 + lane, y = y0 + row;
   const int nch = (g.P + TC - 1) / TC;
   const int b = blockIdx.z / nch;
+  if (retired(g, b)) return;
   const int t0 = (blockIdx.z % nch) * TC;
   const int tend = min(t0 + TC, g.P);
   const int tlast = min(tend, g.P - 1);
@@ -126,9 +127,9 @@ __device__ __forceinline__ void update_tma_body(const Geo<float>& g, const Array
     mbar_expect_tx(bar(slot), bytes);
     const int bp = b * g.P + p;
     char* base = sm + slot * L::slot_bytes;
-    if (full) {
-      tma_load_5d(smem_u32(base + L::a_off), tmA, 0, x0 - 1, y0 - 1, 0, bp, bar(slot));
-      tma_load_5d(smem_u32(base + L::b_off), tmB, 0, x0, y0, 0, bp, bar(slot));
+    if (full) {   // rows of a and b are (cell, component) runs: 16 bytes per cell
+      tma_load_4d(smem_u32(base + L::a_off), tmA, 4 * (x0 - 1), y0 - 1, 0, bp, bar(slot));
+      tma_load_4d(smem_u32(base + L::b_off), tmB, 4 * x0, y0, 0, bp, bar(slot));
     }
     tma_load_4d(smem_u32(base + L::p_off), tmP, xa, y0 - 1, 0, bp, bar(slot));
   };

@@ -62,12 +62,31 @@ def test_batch_matches_oracle_and_stops_at_tolerance(ot):
     stats = batch.solve([f32(p[3][0]) for p in probs], [f32(p[3][1]) for p in probs], 3000, tol=1e-4,
                         check_every=10)
     assert all(s.converged and s.residual <= 1e-4 for s in stats)
-    iters = stats[0].iterations
     for i, (n, bc, P, (f0, f1)) in enumerate(probs):
         g = oracle_grid(n, bc, P)
-        st, infos, scale = o.solve(g, f0.astype(np.float64), f1.astype(np.float64), iters, SIG, TAU)
+        st, infos, scale = o.solve(g, f0.astype(np.float64), f1.astype(np.float64), stats[i].iterations, SIG, TAU)
         assert rel(batch.path(i)["f"], st.f * scale) <= 1e-3
         assert stats[i].mass_drift <= 1e-5
+
+
+def test_converged_problems_retire(ot):
+    """Each problem stops at the first check where its own residual meets tol: its iteration count, its
+    path and its residual equal those of a single plan solved to the same tolerance, so the batch does no
+    more cell-iterations than the problems solved one by one."""
+    probs = _problems()
+    grids = [ot.grid(n, bc, P, sigma=SIG, tau=TAU) for n, bc, P, _ in probs]
+    batch = ot.Batch(grids)
+    stats = batch.solve([f32(p[3][0]) for p in probs], [f32(p[3][1]) for p in probs], 3000, tol=1e-4,
+                        check_every=10)
+    its = [s.iterations for s in stats]
+    assert len(set(its)) > 1      # the problems converge at different checks
+    for i, (n, bc, P, (f0, f1)) in enumerate(probs):
+        plan = ot.Plan(ot.grid(n, bc, P, sigma=SIG, tau=TAU))
+        st = plan.solve(f32(f0), f32(f1), 3000, tol=1e-4, check_every=10)
+        assert st.converged and stats[i].iterations == st.iterations
+        assert stats[i].residual == pytest.approx(st.residual, rel=1e-6)
+        ps, pb = plan.path(), batch.path(i)
+        assert rel(pb["f"], ps["f"][0]) <= 1e-6
 
 
 def test_plans_sharing_kernels_coexist(ot):

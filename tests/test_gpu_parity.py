@@ -352,6 +352,29 @@ def test_staged_and_plain_update_kernels_agree(ot, n, P, monkeypatch):
         assert rel(a, b) <= 1e-5
 
 
+@pytest.mark.parametrize("n,bc,P,precision", [((64, 64, 3), RGB, 16, 0), ((96, 64, 3), RGB, 12, 0),
+                                                ((48, 40, 3), ("periodic", "neumann", "periodic"), 9, 0),
+                                                ((64, 64, 3), RGB, 16, 2)])
+def test_split_xt_passes_match_oracle(ot, n, bc, P, precision, monkeypatch):
+    """The split x/t passes (r, the x transform of row blocks and the t transform of column strips in
+    separate launches), which grids whose (t, x) plane exceeds shared memory take (the FP64 plan at
+    512 x 512 x 3 x 64), selected here with DYNOT_SPLIT_XT=1: one iteration against the oracle with the
+    bound of the fused passes (FP32), and to 1e-9 in FP64."""
+    monkeypatch.setenv("DYNOT_SPLIT_XT", "1")
+    g = oracle_grid(n, bc, P)
+    plan = ot.Plan(ot.grid(n, bc, P, sigma=SIG, tau=TAU, precision=precision))
+    f0, f1 = random_pair(g, 31)
+    st = _random_state(g, 32, smooth=True)
+    plan.state_set(f32(f0), f32(f1), f32(pack_path(g, st.m, st.f)), f32(pack_dual(g, st.bm, st.bf)),
+                   f32(pack_dual(g, st.bbm, st.bbf)))
+    plan.iterate(1)
+    x, b, _ = plan.state_get()
+    new, _ = o.pdhg_step(g, st, f0, f1, SIG, TAU)
+    xo, bo = pack_path(g, new.m, new.f), pack_dual(g, new.bm, new.bf)
+    tol = 1e-6 if precision == 2 else _step_tolerance(g, st, f0, f1)
+    assert rel(x, xo) <= tol and rel(b, bo) <= tol
+
+
 @pytest.mark.parametrize("where", ["dual", "path"])
 def test_non_finite_state_is_reported(ot, where):
     """The detector of non-finite residuals: a NaN planted on the host in the dual (or an Inf in the
