@@ -29,11 +29,30 @@ __device__ __forceinline__ size_t cidx(const Geo<T>& g, int b, int t, int ix, in
   return ((size_t)(b * g.P + t) * g.S) + (size_t)ix + (size_t)g.n1 * ((size_t)iy + (size_t)g.n2 * ic);
 }
 
-__device__ __forceinline__ float fdiv_fast(float a, float b) { return __fdividef(a, b); }
+// FP32 quotients, roots and the cube root of Newton's starting point from the hardware's approximate
+// instructions (PTX rcp.approx, sqrt.approx, lg2.approx, ex2.approx; about one unit in the last place, with
+// subnormal operands flushed to zero).  Newton's method corrects its own rounding, and the quotients of
+// the results are a few units off at most.  FP64 uses the correctly rounded operations.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fdiv_fast(float a, float b) { return a * rcp_approx(b); }
 __device__ __forceinline__ double fdiv_fast(double a, double b) { return a / b; }
-// d^(1/3) for Newton's starting point: in FP32 the fast power intrinsic (a few ulp off,
-// which Newton corrects), in FP64 the library cube root.
-__device__ __forceinline__ float cbrt_start(float d) { return d > 0.f ? __powf(d, 1.f / 3.f) : 0.f; }
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
+// d^(1/3) = 2^(log2(d) / 3) for d > 0 (0 otherwise)
+__device__ __forceinline__ float cbrt_start(float d) {
+  float l, r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(d));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(l * (1.f / 3.f)));
+  return d > 0.f ? r : 0.f;
+}
 __device__ __forceinline__ double cbrt_start(double d) { return cbrt(d); }
 
 // Per-cell proximal map of J (section 3, step 2):
@@ -56,7 +75,7 @@ __device__ __forceinline__ void prox_J(T am0, T am1, T am2, T af, T sigma, T inv
   const T cbd = cbrt_start(d);
   // both starts are computed and one is selected, so that the three channels of a cell interleave
   const T zpos = e + min(cbd, fdiv_fast(d, c * c));                  // c > 0
-  const T zneg = min(cbd, sqrt(fdiv_fast(d, fabs(c)))) - T(1);        // c <= 0
+  const T zneg = min(cbd, sqrt_fast(fdiv_fast(d, fabs(c)))) - T(1);   // c <= 0
   T z = live ? max(c > T(0) ? zpos : zneg, T(0)) : T(0);
   // Stop when the step is below a few units in the last place of the data
   // scale |e| + d + z: near e + d = 0 the root cannot be resolved more finely
