@@ -70,6 +70,9 @@ def parse():
                     help="U-Net weights to evaluate ('default': the package's trained weights; '' trains new ones)")
     ap.add_argument("--hue-pipeline", action="store_true",
                     help="section 5's hue image morph on a synthetic 512x512 flower pair (360 bins, 16 steps)")
+    ap.add_argument("--conv", action="store_true",
+                    help="3x3x3 convolution layers of the warm-start network at 128x128x32 (batch 4): tcgen05 "
+                         "against the mma.sync kernels, TFLOP/s against the measured bf16 peak")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the kernel profile, time-to-tolerance and end-to-end legs (for profiler runs)")
     return ap.parse_args()
@@ -550,6 +553,54 @@ def batch_bench(tol: float = 1e-4, check_every: int = 10):
 
 
 # ---------------------------------------------------------------------------
+# convolution layers of the warm-start network (not part of the default run)
+# ---------------------------------------------------------------------------
+
+def conv_bench(reps: int = 20):
+    import torch
+    from paper_1501_04840_gb300 import _build, nn
+    _build.build()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    vol = (4, 32, 128, 128)
+    vox = vol[0] * vol[1] * vol[2] * vol[3]
+    out = {"metric": "3x3x3 convolution forward, TFLOP/s", "unit": "TFLOP/s", "peak_bf16_tflops": peak,
+           "peak_kind": kind, "volume": list(vol), "layers": {}}
+    g = torch.Generator().manual_seed(0)
+    for cin, cout in ((16, 16), (32, 32), (48, 48), (64, 64)):
+        x = (torch.randn(*vol, cin, generator=g)).to(torch.bfloat16).cuda()
+        w = (0.1 * torch.randn(cout, 27, cin, generator=g)).to(torch.bfloat16).cuda()
+        b = torch.zeros(cout, device="cuda")
+        y = torch.empty(*vol, cout, dtype=torch.bfloat16, device="cuda")
+        flops = 2.0 * vox * 27 * cin * cout
+        row = {}
+        for impl in ("tcgen05", "mma"):
+            if impl == "mma":
+                os.environ["DYNOT_CONV"] = "mma"
+            else:
+                os.environ.pop("DYNOT_CONV", None)
+            for _ in range(3):
+                nn.conv3d(vol, nn.whole(x), w, b, nn.whole(y), relu=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                nn.conv3d(vol, nn.whole(x), w, b, nn.whole(y), relu=True)
+            e1.record()
+            torch.cuda.synchronize()
+            nn.check()
+            ms = e0.elapsed_time(e1) / reps
+            tf = flops / (ms / 1e3) / 1e12
+            row[impl] = {"ms": ms, "tflops": tf, "frac": tf / peak}
+        os.environ.pop("DYNOT_CONV", None)
+        out["layers"]["%d->%d" % (cin, cout)] = row
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # learned warm start (not part of the default run)
 # ---------------------------------------------------------------------------
 
@@ -634,6 +685,9 @@ def main():
         return
     if args.warmstart:
         warmstart_bench(args)
+        return
+    if args.conv:
+        conv_bench()
         return
     if args.precision_study:
         precision_study(args.iters if args.iters != 1000 else 2000)

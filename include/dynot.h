@@ -286,7 +286,12 @@ void ot_batch_destroy(ot_batch_t b);
  * 9 (dt+1) + 3 (dy+1) + (dx+1)), bias fp32.
  *
  * ot_nn_conv3d: y = relu?(conv3x3x3(x, w) + bias), zero padding; cin % 16 == 0,
- *   cout % 8 == 0; out_f32 selects an fp32 output.  Tensor cores (bf16, fp32 accumulate).
+ *   cout % 8 == 0; out_f32 selects an fp32 output.  Tensor cores (bf16, fp32 accumulate):
+ *   tcgen05 with the accumulator in tensor memory and operands staged by bulk tensor copies
+ *   where cout % 16 == 0 (<= 256), the input slice starts on 16 bytes, the output rows hold
+ *   16-byte vectors and X divides 128 (or 128 divides X); mma.sync otherwise.
+ * ot_nn_check: waits for `stream` and returns OT_ETIMEOUT (once) if a bounded device wait of
+ *   the tcgen05 convolution ran out since the last check (that launch wrote NaN), else OT_OK.
  * ot_nn_conv3d_wgrad: dw (fp32 [cout][27][cin]) += sum_v dy[v] x[v + tap]; db (fp32,
  *   may be NULL) += sum_v dy[v]; cin, cout % 16 == 0.  The data gradient is
  *   ot_nn_conv3d with ot_nn_rotate_weights(w) (wr[ci][tap][co] = w[co][26-tap][ci]).
@@ -314,6 +319,7 @@ void ot_batch_destroy(ot_batch_t b);
  */
 ot_status ot_nn_conv3d(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo, const void* w,
                        const float* bias, void* y, int ys, int yo, int relu, int out_f32, void* stream);
+ot_status ot_nn_check(void* stream);
 ot_status ot_nn_conv3d_wgrad(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo,
                              const void* dy, int dys, int dyo, float* dw, float* db, void* stream);
 ot_status ot_nn_rotate_weights(int Cin, int Cout, const void* w, void* wr, void* stream);

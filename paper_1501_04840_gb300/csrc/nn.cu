@@ -19,7 +19,13 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cudaTypedefs.h>
+
+#include <cstdlib>
+#include <cstring>
+
 #include "common.cuh"
+#include "nn_tcgen05.cuh"
 #include "plan_base.h"
 
 namespace dynot {
@@ -670,6 +676,72 @@ using namespace dynot;
 
 extern "C" {
 
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime
+static PFN_cuTensorMapEncodeTiled_v12000 nn_tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }();
+  return fn;
+}
+
+// The tcgen05 form of the convolution where its layout rules hold: 16-channel input slices at 16-byte
+// offsets, Cout a multiple of 16 up to 256, 16-byte output vectors, and tiles of 128 voxels along x (and y).
+// Returns false (nothing launched) where they do not; DYNOT_CONV=mma forces the mma.sync kernels.
+static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo,
+                           const void* w, const float* bias, void* y, int ys, int yo, int relu, int out_f32,
+                           cudaStream_t st, ot_status* status) {
+  const char* sel = std::getenv("DYNOT_CONV");
+  if (sel && std::strcmp(sel, "mma") == 0) return false;
+  const int vec = out_f32 ? 4 : 8;
+  const bool xok = X >= 128 ? X % 128 == 0 : (X >= 1 && 128 % X == 0);
+  if (Cin % 16 || Cout % 16 || Cout > 256 || xs % 8 || xo % 8 || ys % vec || yo % vec || !xok ||
+      ((uintptr_t)x & 15) || ((uintptr_t)w & 15) || ((uintptr_t)y & 15) || (long long)N * T >= 65536)
+    return false;
+  auto enc = nn_tensor_map_encoder();
+  if (!enc) return false;
+  tc::Geom g{N, T, Y, X, 0, 0, 0};
+  g.BX = X >= 128 ? 128 : X;
+  g.BY = 128 / g.BX;
+  g.nxb = X / g.BX;
+  const int nyb = (Y + g.BY - 1) / g.BY;
+  CUtensorMap tmX, tmW;
+  {
+    const cuuint64_t dim[5] = {(cuuint64_t)xs, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)T, (cuuint64_t)N};
+    const cuuint64_t str[4] = {2ull * xs, 2ull * xs * X, 2ull * xs * X * Y, 2ull * xs * X * Y * T};
+    const cuuint32_t box[5] = {16, (cuuint32_t)g.BX, (cuuint32_t)g.BY, 1, 1};
+    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+    if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dim, str, box, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  {
+    const cuuint64_t dim[3] = {(cuuint64_t)Cin, 27, (cuuint64_t)Cout};
+    const cuuint64_t str[2] = {2ull * Cin, 2ull * 27 * Cin};
+    const cuuint32_t box[3] = {16, 1, (cuuint32_t)Cout};
+    const cuuint32_t one[3] = {1, 1, 1};
+    if (enc(&tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(w), dim, str, box, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  const size_t smem = tc::smem_bytes(Cout);
+  cudaError_t e = cudaFuncSetAttribute((const void*)tc::k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess) {
+    tc::k_conv3d_tc<<<dim3((unsigned)(g.nxb * nyb), (unsigned)(N * T)), 128, smem, st>>>(
+        g, Cin, Cout, xo, bias, y, ys, yo, relu, out_f32, tmX, tmW);
+    e = cudaGetLastError();
+  }
+  *status = e == cudaSuccess ? OT_OK : seterr(OT_ECUDA, "conv3d (tcgen05): %s", cudaGetErrorString(e));
+  return true;
+}
+
 ot_status ot_nn_conv3d(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo, const void* w,
                        const float* bias, void* y, int ys, int yo, int relu, int out_f32, void* stream) {
   if (Cin % 16 || Cout % 8 || xs % 2 || xo % 2 || ys % 2 || yo % 2 || xo < 0 || yo < 0 || Cin + xo > xs ||
@@ -679,6 +751,8 @@ ot_status ot_nn_conv3d(int N, int T, int Y, int X, int Cin, int Cout, const void
   const long long M = (long long)N * T * Y * X;
   const dim3 blk(128);
   cudaStream_t st = (cudaStream_t)stream;
+  ot_status tcs = OT_OK;
+  if (conv3d_tcgen05(N, T, Y, X, Cin, Cout, x, xs, xo, w, bias, y, ys, yo, relu, out_f32, st, &tcs)) return tcs;
   if (xs % 8 == 0 && xo % 8 == 0 && ((uintptr_t)x & 15) == 0 && (long long)N * T < 65536) {
     // shared-memory tiled form (16-byte input pieces)
     const int nxb = (X + kCT_TX - 1) / kCT_TX, nyb = (Y + kCT_TY - 1) / kCT_TY;
@@ -700,6 +774,20 @@ ot_status ot_nn_conv3d(int N, int T, int Y, int X, int Cin, int Cout, const void
         v, Cin, Cout, (const bf16*)x, xs, xo, (const bf16*)w, bias, y, ys, yo, relu, out_f32);
   }
   NN_LAUNCH_CHECK();
+  return OT_OK;
+}
+
+ot_status ot_nn_check(void* stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return seterr(OT_ECUDA, "nn: %s", cudaGetErrorString(e));
+  int flag = 0;
+  e = cudaMemcpyFromSymbol(&flag, tc::g_tc_err, sizeof(int));
+  if (e != cudaSuccess) return seterr(OT_ECUDA, "nn: %s", cudaGetErrorString(e));
+  if (flag) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(tc::g_tc_err, &zero, sizeof(int));
+    return seterr(OT_ETIMEOUT, "a bounded device wait of the tensor-core convolution ran out of its limit");
+  }
   return OT_OK;
 }
 

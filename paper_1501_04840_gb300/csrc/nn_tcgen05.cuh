@@ -1,0 +1,221 @@
+// 3x3x3 convolution on the fifth-generation tensor cores (tcgen05), bf16 in, fp32 accumulate in TMEM.
+//
+// The implicit GEMM of k_conv3d (M = voxels, N = output channels, K = 27 taps x input channels) with a
+// CTA tile of M = 128 voxels (BX x BY of one (n, t) slice, BX * BY = 128) and all N = Cout channels.
+// The K loop runs over (tap, 16-channel chunk) pairs.  For each pair a bulk tensor copy brings
+//   A: the 128 voxels shifted by the tap, 16 channels each (32-byte rows, 32-byte swizzle; the copy
+//      reads zeros outside the volume, which is the convolution's zero padding), and
+//   B: the tap's 16-channel slice of every output channel's weights (Cout rows of 32 bytes),
+// into one of kTcStages shared-memory stages.  One thread issues the copies, one thread issues one
+// tcgen05.mma (M = 128, N = Cout, K = 16) per stage and releases the stage with tcgen05.commit; the
+// accumulator lives in tensor memory (Cout columns of 128 lanes).  After the last MMA the four warps
+// read their 32 lanes with tcgen05.ld, add the bias, apply ReLU and store bf16 or fp32.
+//
+// Every mbarrier wait has a time limit; a wait that runs out sets g_tc_err, the kernel writes NaN
+// instead of its results, frees its tensor memory and returns.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+namespace dynot {
+namespace tc {
+
+constexpr int kStages = 4;
+constexpr int kM = 128;
+constexpr unsigned long long kWaitNs = 20000000ull;   // 20 ms
+
+__device__ int g_tc_err = 0;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void bar_init(uint32_t b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(b), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity) {
+  unsigned long long start = 0;
+#pragma unroll 1
+  for (int i = 0;; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (i == 0) start = now_ns();
+    else if ((i & 63) == 0 && now_ns() - start > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* m, int c0, int c1, int c2, int c3, int c4,
+                                       uint32_t b) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];\n" ::"r"(dst),
+      "l"((unsigned long long)m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(b)
+      : "memory");
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* m, int c0, int c1, int c2, uint32_t b) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(dst),
+      "l"((unsigned long long)m), "r"(c0), "r"(c1), "r"(c2), "r"(b)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 32-byte swizzled layout: rows of 32 bytes
+// (16 bf16 of K), groups of 8 rows 256 bytes apart (stride byte offset), one swizzle atom across K (the
+// leading byte offset is not used), descriptor version 1, layout type 6 (32-byte swizzle).
+__device__ __forceinline__ uint64_t desc_k32(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
+  return d;
+}
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__host__ __device__ constexpr uint32_t b_bytes(int cout) { return (uint32_t)((cout * 32 + 1023) & ~1023); }
+__host__ __device__ constexpr uint32_t stage_bytes(int cout) { return 4096u + b_bytes(cout); }
+__host__ __device__ constexpr int tmem_cols(int cout) { return cout <= 32 ? 32 : (cout <= 64 ? 64 : (cout <= 128 ? 128 : 256)); }
+inline size_t smem_bytes(int cout) { return (size_t)kStages * stage_bytes(cout) + 128 + 1024; }
+
+struct Geom {
+  int N, T, Y, X;
+  int BX, BY, nxb;   // tile of BX x BY voxels (BX * BY = 128); nxb tiles along x
+};
+
+__global__ void __launch_bounds__(128) k_conv3d_tc(Geom v, int Cin, int Cout, int xo, const float* __restrict__ bias,
+                                                   void* __restrict__ y, int ys, int yo, int relu, int out_f32,
+                                                   const __grid_constant__ CUtensorMap tmX,
+                                                   const __grid_constant__ CUtensorMap tmW) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x0 = (blockIdx.x % v.nxb) * v.BX, y0 = (blockIdx.x / v.nxb) * v.BY;
+  const int t = blockIdx.y % v.T, n = blockIdx.y / v.T;
+  const uint32_t sb = stage_bytes(Cout);
+  const uint32_t base = saddr(sm);
+  const uint32_t bars = base + kStages * sb;   // full[kStages], empty[kStages], done
+  auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return bars + 8u * (uint32_t)(kStages + s); };
+  const uint32_t done = bars + 8u * (2 * kStages);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kStages * sb + 8 * (2 * kStages + 1));
+  const int ncols = tmem_cols(Cout);
+  const int chunks = Cin / 16, nk = 27 * chunks;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(full(s), 1);
+      bar_init(empty(s), 1);
+    }
+    bar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  if (warp == 0 && lane == 0) {
+    // producer: the shifted input tile and the weight slice of every (tap, chunk)
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages;
+      if (i >= kStages && ok) ok = bar_wait(empty(s), ((i / kStages) & 1) ^ 1);
+      const int tap = i / chunks, cc = i - tap * chunks;
+      const int dt = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+      bar_expect_tx(full(s), 4096u + 32u * (uint32_t)Cout);
+      tma_5d(base + s * sb, &tmX, xo + 16 * cc, x0 + dx, y0 + dy, t + dt, n, full(s));
+      tma_3d(base + s * sb + 4096u, &tmW, 16 * cc, tap, 0, full(s));
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issue: D (tensor memory) += A (128 x 16) B^T (16 x Cout) per stage
+    const uint32_t idesc = idesc_bf16(kM, Cout);
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages;
+      if (ok) ok = bar_wait(full(s), (i / kStages) & 1);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint64_t ad = desc_k32(base + s * sb), bd = desc_k32(base + s * sb + 4096u);
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(i > 0 ? 1 : 0)
+          : "memory");
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(s))
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(done)
+                 : "memory");
+  }
+  __syncwarp();
+  // epilogue: warp w owns accumulator rows (tensor-memory lanes) 32 w .. 32 w + 31
+  if (ok) ok = bar_wait(done, 0);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const int m = 32 * warp + lane;
+  const int xx = x0 + m % v.BX, yy = y0 + m / v.BX;
+  const bool store = xx < v.X && yy < v.Y;
+  const long long vox = (((long long)n * v.T + t) * v.Y + yy) * v.X + xx;
+  const float nanv = __int_as_float(0x7fc00000);
+  for (int c0 = 0; c0 < Cout; c0 += 16) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    if (!store) continue;
+    float u[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      u[j] = __uint_as_float(r[j]) + (bias ? bias[c0 + j] : 0.f);
+      if (relu) u[j] = fmaxf(u[j], 0.f);
+      if (!ok) u[j] = nanv;
+    }
+    const long long o = vox * ys + yo + c0;
+    if (out_f32) {
+      float4* yp = reinterpret_cast<float4*>((float*)y + o);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) yp[q] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
+    } else {
+      uint4* yp = reinterpret_cast<uint4*>((__nv_bfloat16*)y + o);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        uint32_t p[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const __nv_bfloat16 lo = __float2bfloat16(u[8 * q + 2 * j]), hi = __float2bfloat16(u[8 * q + 2 * j + 1]);
+          p[j] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        yp[q] = make_uint4(p[0], p[1], p[2], p[3]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+  if (!ok) atomicExch(&g_tc_err, 1);
+}
+
+}  // namespace tc
+}  // namespace dynot

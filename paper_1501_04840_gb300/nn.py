@@ -37,6 +37,7 @@ def lib():
         "ot_nn_make_input": [i, i, i, i, i, vp, vp, vp, vp, vp],
         "ot_nn_path_channels": [i, i, i, i, i, vp, vp, vp, vp, vp, i, vp],
         "ot_nn_dual_channels": [i, i, i, i, i, vp, vp, i, i, vp],
+        "ot_nn_check": [vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -143,3 +144,9 @@ def path_channels(N, Y, X, P, to_channels: bool, packed, ch, f0=None, f1=None, s
 def dual_channels(N, Y, X, P, to_channels: bool, packed, ch, co: int, stream=None):
     _check(lib().ot_nn_dual_channels(N, Y, X, P, int(to_channels), _p(packed), _p(ch), ch.shape[-1], co,
                                      _s(stream)))
+
+
+def check(stream=None):
+    """ot_nn_check: wait for the stream and raise if a bounded device wait of the tcgen05 convolution ran
+    out since the last check."""
+    _check(lib().ot_nn_check(_s(stream)))
