@@ -578,10 +578,7 @@ def conv_bench(reps: int = 20):
         flops = 2.0 * vox * 27 * cin * cout
         row = {}
         for impl in ("tcgen05", "mma"):
-            if impl == "mma":
-                os.environ["DYNOT_CONV"] = "mma"
-            else:
-                os.environ.pop("DYNOT_CONV", None)
+            os.environ["DYNOT_CONV"] = impl
             for _ in range(3):
                 nn.conv3d(vol, nn.whole(x), w, b, nn.whole(y), relu=True)
             torch.cuda.synchronize()

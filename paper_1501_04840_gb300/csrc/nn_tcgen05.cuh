@@ -11,6 +11,12 @@
 // accumulator lives in tensor memory (Cout columns of 128 lanes).  After the last MMA the four warps
 // read their 32 lanes with tcgen05.ld, add the bias, apply ReLU and store bf16 or fp32.
 //
+// Rows of 128 voxels along x (X a multiple of 128) take the halo form (HALO = true): a stage holds the
+// input row of 130 voxels (x0 - 1 .. x0 + 128) of one (dt, dy) and one 16-channel chunk, stored without
+// swizzle as two planes of 8 channels (16-byte rows), and the weights of the three taps dx = -1, 0, 1;
+// the three MMAs read the row through descriptors that start 0, 1 and 2 rows in, so each input row is
+// copied once per (dt, dy) instead of once per tap.
+//
 // Every mbarrier wait has a time limit; a wait that runs out sets g_tc_err, the kernel writes NaN
 // instead of its results, frees its tensor memory and returns.
 #pragma once
@@ -80,21 +86,35 @@ __device__ __forceinline__ uint64_t desc_k32(uint32_t addr) {
   d |= (uint64_t)6 << 61;
   return d;
 }
+// The same for the layout without swizzle: 8-row core matrices of 16-byte rows (stride byte offset 128 between
+// 8-row groups), the two 8-channel halves of K `lbo` bytes apart (leading byte offset), layout type 0.
+__device__ __forceinline__ uint64_t desc_k_plain(uint32_t addr, uint32_t lbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(128u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
 // Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both K-major, N >> 3 and M >> 4.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __host__ __device__ constexpr uint32_t b_bytes(int cout) { return (uint32_t)((cout * 32 + 1023) & ~1023); }
-__host__ __device__ constexpr uint32_t stage_bytes(int cout) { return 4096u + b_bytes(cout); }
+constexpr uint32_t kHaloRows = 130, kPlane = 2176;   // 130 rows of 16 bytes, padded to 128-byte multiples
+constexpr uint32_t kHaloA = 5120;                    // two planes, padded to 1024 bytes
+__host__ __device__ constexpr uint32_t stage_bytes(int cout, bool halo) {
+  return halo ? kHaloA + 3u * b_bytes(cout) : 4096u + b_bytes(cout);
+}
 __host__ __device__ constexpr int tmem_cols(int cout) { return cout <= 32 ? 32 : (cout <= 64 ? 64 : (cout <= 128 ? 128 : 256)); }
-inline size_t smem_bytes(int cout) { return (size_t)kStages * stage_bytes(cout) + 128 + 1024; }
+inline size_t smem_bytes(int cout, bool halo) { return (size_t)kStages * stage_bytes(cout, halo) + 128 + 1024; }
 
 struct Geom {
   int N, T, Y, X;
   int BX, BY, nxb;   // tile of BX x BY voxels (BX * BY = 128); nxb tiles along x
 };
 
+template <bool HALO>
 __global__ void __launch_bounds__(128) k_conv3d_tc(Geom v, int Cin, int Cout, int xo, const float* __restrict__ bias,
                                                    void* __restrict__ y, int ys, int yo, int relu, int out_f32,
                                                    const __grid_constant__ CUtensorMap tmX,
@@ -104,7 +124,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(Geom v, int Cin, int Cout, in
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int x0 = (blockIdx.x % v.nxb) * v.BX, y0 = (blockIdx.x / v.nxb) * v.BY;
   const int t = blockIdx.y % v.T, n = blockIdx.y / v.T;
-  const uint32_t sb = stage_bytes(Cout);
+  const uint32_t sb = stage_bytes(Cout, HALO), bb = b_bytes(Cout);
   const uint32_t base = saddr(sm);
   const uint32_t bars = base + kStages * sb;   // full[kStages], empty[kStages], done
   auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
@@ -112,7 +132,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(Geom v, int Cin, int Cout, in
   const uint32_t done = bars + 8u * (2 * kStages);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kStages * sb + 8 * (2 * kStages + 1));
   const int ncols = tmem_cols(Cout);
-  const int chunks = Cin / 16, nk = 27 * chunks;
+  const int chunks = Cin / 16, nk = (HALO ? 9 : 27) * chunks;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       bar_init(full(s), 1);
@@ -137,11 +157,20 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(Geom v, int Cin, int Cout, in
     for (int i = 0; i < nk; ++i) {
       const int s = i % kStages;
       if (i >= kStages && ok) ok = bar_wait(empty(s), ((i / kStages) & 1) ^ 1);
-      const int tap = i / chunks, cc = i - tap * chunks;
-      const int dt = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-      bar_expect_tx(full(s), 4096u + 32u * (uint32_t)Cout);
-      tma_5d(base + s * sb, &tmX, xo + 16 * cc, x0 + dx, y0 + dy, t + dt, n, full(s));
-      tma_3d(base + s * sb + 4096u, &tmW, 16 * cc, tap, 0, full(s));
+      if constexpr (HALO) {
+        const int ty = i / chunks, cc = i - ty * chunks;   // ty = 3 (dt + 1) + (dy + 1)
+        const int dt = ty / 3 - 1, dy = ty % 3 - 1;
+        bar_expect_tx(full(s), 2u * 16u * kHaloRows + 3u * 32u * (uint32_t)Cout);
+        for (int h = 0; h < 2; ++h)
+          tma_5d(base + s * sb + h * kPlane, &tmX, xo + 16 * cc + 8 * h, x0 - 1, y0 + dy, t + dt, n, full(s));
+        for (int q = 0; q < 3; ++q) tma_3d(base + s * sb + kHaloA + q * bb, &tmW, 16 * cc, 3 * ty + q, 0, full(s));
+      } else {
+        const int tap = i / chunks, cc = i - tap * chunks;
+        const int dt = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        bar_expect_tx(full(s), 4096u + 32u * (uint32_t)Cout);
+        tma_5d(base + s * sb, &tmX, xo + 16 * cc, x0 + dx, y0 + dy, t + dt, n, full(s));
+        tma_3d(base + s * sb + 4096u, &tmW, 16 * cc, tap, 0, full(s));
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issue: D (tensor memory) += A (128 x 16) B^T (16 x Cout) per stage
@@ -150,12 +179,16 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(Geom v, int Cin, int Cout, in
       const int s = i % kStages;
       if (ok) ok = bar_wait(full(s), (i / kStages) & 1);
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint64_t ad = desc_k32(base + s * sb), bd = desc_k32(base + s * sb + 4096u);
-      asm volatile(
-          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(ad), "l"(bd), "r"(idesc), "r"(i > 0 ? 1 : 0)
-          : "memory");
+      for (int q = 0; q < (HALO ? 3 : 1); ++q) {
+        // halo: the tap dx = q - 1 reads the row from its (q)-th voxel on
+        const uint64_t ad = HALO ? desc_k_plain(base + s * sb + 16u * q, kPlane) : desc_k32(base + s * sb);
+        const uint64_t bd = desc_k32(base + s * sb + (HALO ? kHaloA + q * bb : 4096u));
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(i > 0 || q > 0 ? 1 : 0)
+            : "memory");
+      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(s))
                    : "memory");
     }
