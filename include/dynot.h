@@ -288,8 +288,9 @@ void ot_batch_destroy(ot_batch_t b);
  * ot_nn_conv3d: y = relu?(conv3x3x3(x, w) + bias), zero padding; cin % 16 == 0,
  *   cout % 8 == 0; out_f32 selects an fp32 output.  Tensor cores (bf16, fp32 accumulate):
  *   tcgen05 with the accumulator in tensor memory and operands staged by bulk tensor copies
- *   where 32 <= cout <= 256, cout % 16 == 0, the input slice starts on 16 bytes, the output
- *   rows hold 16-byte vectors and X divides 128 (or 128 divides X); mma.sync otherwise.
+ *   where cout % 16 == 0 (16 <= cout <= 256; 32 or more when X < 128), the input slice starts
+ *   on 16 bytes, the output rows hold 16-byte vectors and X divides 128 (or 128 divides X);
+ *   mma.sync otherwise.
  * ot_nn_check: waits for `stream` and returns OT_ETIMEOUT (once) if a bounded device wait of
  *   the tcgen05 convolution ran out since the last check (that launch wrote NaN), else OT_OK.
  * ot_nn_conv3d_wgrad: dw (fp32 [cout][27][cin]) += sum_v dy[v] x[v + tap]; db (fp32,

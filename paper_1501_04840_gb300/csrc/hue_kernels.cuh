@@ -190,4 +190,161 @@ __global__ void __launch_bounds__(256) k_hue_inv(Geo<T> g, const T* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// The real DFT along the bins as a dense matrix product (FP32 plans with at most kHueGemmMax bins and at
+// least kHueGemmRows rows, where the product fills the GPU; single pairs keep the per-row kernels): the
+// transform of all B P rows at once is C = R W^T with W[slot][i] the basis of the real Fourier slots
+// (forward) or its inverse with the weights 1, 2, ..., 2, (1) / n (inverse, stored transposed).
+//   H_R  hue_rhs  : r = A a - f_b^- per cell (one thread per cell) into a row array;
+//   H_G  gemm_nt  : C[M][N] = sum_k A[m][k] B[n][k], 64 x 64 tiles of 4 x 4 outputs per thread, K in steps
+//                   of 16 through shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kHueGemmMax = 1024, kHueGemmRows = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_hue_rhs(Geo<T> g, const v4<T>* __restrict__ ap, const T* __restrict__ f0,
+                                                 const T* __restrict__ f1, T* __restrict__ r) {
+  const int n = g.n1, P = g.P;
+  const long long tot = (long long)g.B * P * n;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % n);
+    const long long row = id / n;
+    const int t = (int)(row % P), b = (int)(row / P);
+    if (retired(g, b)) continue;
+    const int im = i > 0 ? i - 1 : n - 1;   // periodic
+    const v4<T> av = ap[id];
+    T v = g.s1 * (av.x - comp<T>(ap, id - i + im, 0));
+    const T fnext = (t == P - 1) ? f1[(size_t)b * n + i] : av.w;
+    const T fprev = (t == 0) ? f0[(size_t)b * n + i] : comp<T>(ap, id - n, 3);
+    v += g.sp * (fnext - fprev);
+    r[id] = v;
+  }
+}
+
+static __global__ void __launch_bounds__(256) k_gemm_nt(int M, int N, int K, const float* __restrict__ A,
+                                                 const float* __restrict__ Bm, float* __restrict__ C) {
+  __shared__ __align__(16) float As[16][68];
+  __shared__ __align__(16) float Bs[16][68];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = threadIdx.x + 256 * q;   // row idx / 16 of the tile, k idx % 16
+      const int r = idx >> 4, kk = idx & 15;
+      const bool kin = k0 + kk < K;
+      As[kk][r] = (m0 + r < M && kin) ? A[(size_t)(m0 + r) * K + k0 + kk] : 0.f;
+      Bs[kk][r] = (n0 + r < N && kin) ? Bm[(size_t)(n0 + r) * K + k0 + kk] : 0.f;
+    }
+    __syncthreads();
+    // the 16 terms of this K step are summed on their own and then added to the total, which keeps the
+    // rounding error of a sum over K terms near that of 16 + K / 16 additions
+    float part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + 4 * ty + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nn = n0 + 4 * tx + j;
+      if (nn < N) C[(size_t)m * N + nn] = acc[i][j];
+    }
+  }
+}
+
+// C[z][m][n] = sum_k A[m][k] B[z][k][n] for every batch z (A row-major [M][K]; B, C row-major [K][N], [M][N]
+// per batch, batch stride `bs`), the time transforms of all slot columns of the hue rows at once, with the
+// per-step partial sums of k_gemm_nt.  DIV divides every output by its eigenvalue lamt[m] + lam[n] (zero
+// mode -> 0; below lam_fp64 in double), as k_hue_t does between its two products.
+template <bool DIV>
+__global__ void __launch_bounds__(256) k_gemm_tn(int M, int N, int K, const float* __restrict__ A,
+                                                 const float* __restrict__ Bm, float* __restrict__ C, long long bs,
+                                                 HueTables tb) {
+  __shared__ __align__(16) float As[16][68];
+  __shared__ __align__(16) float Bs[16][68];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const float* Bz = Bm + (size_t)blockIdx.z * bs;
+  float* Cz = C + (size_t)blockIdx.z * bs;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = threadIdx.x + 256 * q;
+      const int r = idx >> 4, kk = idx & 15;         // A: row r of the tile, k kk
+      As[kk][r] = (m0 + r < M && k0 + kk < K) ? A[(size_t)(m0 + r) * K + k0 + kk] : 0.f;
+      const int kb = idx >> 6, c = idx & 63;         // B: k kb of the tile, column c
+      Bs[kb][c] = (k0 + kb < K && n0 + c < N) ? Bz[(size_t)(k0 + kb) * N + n0 + c] : 0.f;
+    }
+    __syncthreads();
+    float part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + 4 * ty + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nn = n0 + 4 * tx + j;
+      if (nn >= N) continue;
+      float v = acc[i][j];
+      if (DIV) {
+        const float lam = ((const float*)tb.lam)[nn] + ((const float*)tb.lamt)[m];
+        if (!(lam > 0.f)) v = 0.f;
+        else if ((double)lam < tb.lam_fp64) v = (float)((double)v / (tb.lamd[nn] + tb.lamtd[m]));
+        else v = v / lam;
+      }
+      Cz[(size_t)m * N + nn] = v;
+    }
+  }
+}
+
 }  // namespace dynot

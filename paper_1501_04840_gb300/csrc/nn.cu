@@ -691,18 +691,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 nn_tensor_map_encoder() {
 
 // The tcgen05 form of the convolution where its layout rules hold: 16-channel input slices at 16-byte
 // offsets, Cout a multiple of 16 up to 256, 16-byte output vectors, and tiles of 128 voxels along x (and y).
-// Returns false (nothing launched) where they do not, and for fewer than 32 output channels;
-// DYNOT_CONV=mma forces the mma.sync kernels, DYNOT_CONV=tcgen05 the tcgen05 form wherever its rules
-// hold, DYNOT_CONV=tap its per-tap form on rows of 128 voxels.
+// Returns false (nothing launched) where they do not, and for fewer than 32 output channels on rows shorter
+// than 128 voxels;
+// DYNOT_CONV=mma forces the mma.sync kernels, DYNOT_CONV=tcgen05 the tcgen05 forms wherever their rules
+// hold, DYNOT_CONV=tap and =halo the per-tap and the halo-row forms on rows of 128 voxels.
 static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo,
                            const void* w, const float* bias, void* y, int ys, int yo, int relu, int out_f32,
                            cudaStream_t st, ot_status* status) {
   const char* sel = std::getenv("DYNOT_CONV");
   if (sel && std::strcmp(sel, "mma") == 0) return false;
-  const bool forced = sel && (std::strcmp(sel, "tcgen05") == 0 || std::strcmp(sel, "tap") == 0);
-  // with 16 output channels an MMA of N = 16 per tap does too little per copy: the mma.sync kernel, which
-  // stages one input halo per 16-channel slice, is faster there (bench.py --conv)
-  if (!forced && Cout < 32) return false;
+  const bool forced = sel && (std::strcmp(sel, "tcgen05") == 0 || std::strcmp(sel, "tap") == 0 ||
+                              std::strcmp(sel, "halo") == 0);
+  // with 16 output channels and rows shorter than 128 voxels (per-tap form) an MMA of N = 16 per tap does
+  // too little per copy: the mma.sync kernel, which stages one input halo per 16-channel slice, is faster
+  // there; rows of 128 voxels take the four-row block form, faster at every width (bench.py --conv)
+  if (!forced && Cout < 32 && X % 128 != 0) return false;
   const int vec = out_f32 ? 4 : 8;
   const bool xok = X >= 128 ? X % 128 == 0 : (X >= 1 && 128 % X == 0);
   if (Cin % 16 || Cout % 16 || Cout > 256 || xs % 8 || xo % 8 || ys % vec || yo % vec || !xok ||
@@ -715,8 +718,39 @@ static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const 
   g.BY = 128 / g.BX;
   g.nxb = X / g.BX;
   const int nyb = (Y + g.BY - 1) / g.BY;
-  // rows of 128 voxels along x take the halo form (one input row per (dt, dy), three taps per stage)
-  const bool halo = g.BX == 128 && !(sel && std::strcmp(sel, "tap") == 0);
+  // rows of 128 voxels along x take the row-block form (Cout <= 64: four output rows per CTA, six input rows
+  // per (dt, chunk)) or the halo form (one input row per (dt, dy), three taps per stage)
+  const bool tapf = sel && std::strcmp(sel, "tap") == 0, halof = sel && std::strcmp(sel, "halo") == 0;
+  const bool rows = g.BX == 128 && Cout <= 64 && !tapf && !halof;
+  const bool halo = g.BX == 128 && !tapf && !rows;
+  if (rows) {
+    CUtensorMap tmR, tmW;
+    const cuuint64_t dim[5] = {(cuuint64_t)xs, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)T, (cuuint64_t)N};
+    const cuuint64_t str[4] = {2ull * xs, 2ull * xs * X, 2ull * xs * X * Y, 2ull * xs * X * Y * T};
+    const cuuint32_t box[5] = {8, tc::kHaloRows, (cuuint32_t)tc::kRBin, 1, 1};
+    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+    const cuuint64_t wdim[3] = {(cuuint64_t)Cin, 27, (cuuint64_t)Cout};
+    const cuuint64_t wstr[2] = {2ull * Cin, 2ull * 27 * Cin};
+    const cuuint32_t wbox[3] = {16, 1, (cuuint32_t)Cout};
+    if (enc(&tmR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dim, str, box, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(w), wdim, wstr, wbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    const size_t smem = tc::rows_smem_bytes(Cout);
+    cudaError_t e = cudaFuncSetAttribute((const void*)tc::k_conv3d_tc_rows,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      const int nrb = (Y + tc::kRB - 1) / tc::kRB;
+      tc::k_conv3d_tc_rows<<<dim3((unsigned)(g.nxb * nrb), (unsigned)(N * T)), 128, smem, st>>>(
+          g, Cin, Cout, xo, bias, y, ys, yo, relu, out_f32, tmR, tmW);
+      e = cudaGetLastError();
+    }
+    *status = e == cudaSuccess ? OT_OK : seterr(OT_ECUDA, "conv3d (tcgen05 rows): %s", cudaGetErrorString(e));
+    return true;
+  }
   CUtensorMap tmX, tmW;
   {
     const cuuint64_t dim[5] = {(cuuint64_t)xs, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)T, (cuuint64_t)N};

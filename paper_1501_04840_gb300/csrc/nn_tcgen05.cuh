@@ -250,5 +250,147 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(Geom v, int Cin, int Cout, in
   if (!ok) atomicExch(&g_tc_err, 1);
 }
 
+// Blocks of kRB = 4 output rows of 128 voxels (X a multiple of 128, Cout <= 64).  One stage holds the six input
+// rows y0 - 1 .. y0 + 4 (130 voxels each, two unswizzled 8-channel planes) of one dt and 16-channel chunk, and
+// the weights of its nine (dy, dx) taps.  Each stage issues 36 MMAs (4 output rows x 9 taps) into four
+// accumulators of Cout columns: every input row is copied once per (dt, chunk) for four output rows and every
+// weight slice once per four rows, which cuts the copies per MMA about threefold against the halo row form.
+constexpr int kRB = 4, kRBin = kRB + 2;
+constexpr uint32_t kRowPlane = 12544;                    // 6 rows x 130 voxels x 16 bytes = 12480, padded to 128
+constexpr uint32_t kRowsA = 25600;                       // two planes, padded to 1024 bytes
+constexpr int kRowStages = 2;
+__host__ __device__ constexpr uint32_t rows_stage_bytes(int cout) { return kRowsA + 9u * b_bytes(cout); }
+__host__ __device__ constexpr int rows_col_stride(int cout) { return cout <= 16 ? 16 : (cout <= 32 ? 32 : 64); }
+inline size_t rows_smem_bytes(int cout) { return (size_t)kRowStages * rows_stage_bytes(cout) + 128 + 1024; }
+
+__global__ void __launch_bounds__(128) k_conv3d_tc_rows(Geom v, int Cin, int Cout, int xo, const float* __restrict__ bias,
+                                                        void* __restrict__ y, int ys, int yo, int relu, int out_f32,
+                                                        const __grid_constant__ CUtensorMap tmX,
+                                                        const __grid_constant__ CUtensorMap tmW) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x0 = (blockIdx.x % v.nxb) * 128, y0 = (blockIdx.x / v.nxb) * kRB;
+  const int t = blockIdx.y % v.T, n = blockIdx.y / v.T;
+  const uint32_t sb = rows_stage_bytes(Cout), bb = b_bytes(Cout);
+  const uint32_t base = saddr(sm);
+  const uint32_t bars = base + kRowStages * sb;   // full[kRowStages], empty[kRowStages], done
+  auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return bars + 8u * (uint32_t)(kRowStages + s); };
+  const uint32_t done = bars + 8u * (2 * kRowStages);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kRowStages * sb + 8 * (2 * kRowStages + 1));
+  const int cs = rows_col_stride(Cout);
+  const int ncols = tmem_cols(kRB * cs);
+  const int chunks = Cin / 16, nk = 3 * chunks;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kRowStages; ++s) {
+      bar_init(full(s), 1);
+      bar_init(empty(s), 1);
+    }
+    bar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  if (warp == 0 && lane == 0) {
+    // producer: six input rows of one dt and chunk, and the weights of its nine taps
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kRowStages;
+      if (i >= kRowStages && ok) ok = bar_wait(empty(s), ((i / kRowStages) & 1) ^ 1);
+      const int dt = i / chunks - 1, cc = i % chunks;
+      bar_expect_tx(full(s), 2u * kRBin * kHaloRows * 16u + 9u * 32u * (uint32_t)Cout);
+      for (int h = 0; h < 2; ++h)
+        tma_5d(base + s * sb + h * kRowPlane, &tmX, xo + 16 * cc + 8 * h, x0 - 1, y0 - 1, t + dt, n, full(s));
+      for (int q = 0; q < 9; ++q) tma_3d(base + s * sb + kRowsA + q * bb, &tmW, 16 * cc, 9 * (dt + 1) + q, 0, full(s));
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16(kM, Cout);
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kRowStages;
+      if (ok) ok = bar_wait(full(s), (i / kRowStages) & 1);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      for (int r = 0; r < kRB; ++r)
+        for (int q = 0; q < 9; ++q) {
+          // output row r, tap (dy, dx) = (q / 3 - 1, q % 3 - 1): input row r + dy + 1 of the stage, from voxel dx + 1
+          const int arow = r + q / 3, ax = q % 3;
+          const uint64_t ad = desc_k_plain(base + s * sb + (uint32_t)(arow * (int)kHaloRows + ax) * 16u, kRowPlane);
+          const uint64_t bd = desc_k32(base + s * sb + kRowsA + q * bb);
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(r * cs)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(i > 0 || q > 0 ? 1 : 0)
+              : "memory");
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(s))
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(done)
+                 : "memory");
+  }
+  __syncwarp();
+  if (ok) ok = bar_wait(done, 0);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const int xx = x0 + 32 * warp + lane;
+  const float nanv = __int_as_float(0x7fc00000);
+  for (int r = 0; r < kRB; ++r) {
+    const int yy = y0 + r;
+    const bool store = xx < v.X && yy < v.Y;
+    const long long vox = (((long long)n * v.T + t) * v.Y + yy) * v.X + xx;
+    for (int c0 = 0; c0 < Cout; c0 += 16) {
+      uint32_t rr[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];\n"
+          : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+            "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+          : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(r * cs + c0)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (!store) continue;
+      float u[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        u[j] = __uint_as_float(rr[j]) + (bias ? bias[c0 + j] : 0.f);
+        if (relu) u[j] = fmaxf(u[j], 0.f);
+        if (!ok) u[j] = nanv;
+      }
+      const long long o = vox * ys + yo + c0;
+      if (out_f32) {
+        float4* yp = reinterpret_cast<float4*>((float*)y + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) yp[q] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
+      } else {
+        uint4* yp = reinterpret_cast<uint4*>((__nv_bfloat16*)y + o);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          uint32_t pk[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat16 lo = __float2bfloat16(u[8 * q + 2 * j]), hi = __float2bfloat16(u[8 * q + 2 * j + 1]);
+            pk[j] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+          }
+          yp[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+  if (!ok) atomicExch(&g_tc_err, 1);
+}
+
 }  // namespace tc
 }  // namespace dynot

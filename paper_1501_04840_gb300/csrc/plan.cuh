@@ -144,7 +144,7 @@ KB<T> pick_kb(int n, int w = kW) {
   }
   return pick_kb_w<T, kW>(n);
 }
-template <typename T> using KD = void (*)(Geo<T>, Arrays<T>, int, double*);
+template <typename T> using KD = void (*)(Geo<T>, Arrays<T>, int, TileLayout, double*);
 
 template <typename T, int C, bool PXY>
 KD<T> pick_kd_c(bool check, bool wx) {
@@ -254,6 +254,11 @@ struct Plan final : PlanBase {
   size_t smR = 0, smT = 0;
   KB<T> kb = nullptr;
   KH<T> kh = nullptr;
+  bool hue_gemm = false;    // the hue DFTs as dense matrix products (FP32, bins <= kHueGemmMax)
+  const T* hwf = nullptr;   // [slot][bin] forward basis
+  const T* hwi = nullptr;   // [bin][slot] inverse
+  const T* hmf = nullptr;   // [k][t] forward DCT along t (P x P)
+  const T* hmi = nullptr;   // [t][k] its inverse
   bool tiled = false;       // tiled update kernel (up to four colour channels)
   bool use_tma = false;     // the tiled update stages its planes with bulk tensor copies
   CUtensorMap tmA[2]{}, tmB[2]{}, tmP{};   // a[p], b[p] and phi for k_update_tma
@@ -343,10 +348,16 @@ struct Plan final : PlanBase {
     CUDA_OK(cudaMallocHost(&h_mass, sizeof(double) * (size_t)B * P));
     out_scale.assign(B, 1.0);
     tiled = !hue && C <= 4;
+    {
+      const char* kind = std::getenv("DYNOT_UPDATE_KERNEL");
+      plain_update = kind && std::strcmp(kind, "plain") == 0;
+    }
     if constexpr (std::is_same<T, float>::value) {
-      // DYNOT_UPDATE_KERNEL=plain selects the plain-load update kernel (same arithmetic; for comparisons)
+      // DYNOT_UPDATE_KERNEL=plain selects the plain-load update kernel, =staged the staged one wherever it
+      // applies (same arithmetic; for comparisons and profiles)
       const char* kind = std::getenv("DYNOT_UPDATE_KERNEL");
       const bool plain = kind && std::strcmp(kind, "plain") == 0;
+      force_staged = kind && std::strcmp(kind, "staged") == 0;
       if (tiled && DYNOT_UPD_TMA && !plain && !g.per1 && !g.per2 && n1 % 4 == 0 && n1 >= kTX && n2 >= kTY)
         OT_TRY(make_tensor_maps());
     }
@@ -417,11 +428,13 @@ struct Plan final : PlanBase {
   }
   std::string shape_key() const {
     char buf[160];
-    std::snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d:%d:%d%d%d:%d:%d", (int)sizeof(T), n1, n2, C, P, B, g.per1, g.per2,
-                  g.perc, device, (int)tma_ok);
+    std::snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d:%d:%d%d%d:%d:%d%d", (int)sizeof(T), n1, n2, C, P, B, g.per1, g.per2,
+                  g.perc, device, (int)tma_ok, (int)force_staged);
     return buf;
   }
   bool tma_ok = false;      // tensor maps exist: the staged update is a candidate
+  bool force_staged = false;
+  bool plain_update = false;  // DYNOT_UPDATE_KERNEL=plain: no staged kernel, and hue batches update cell by cell
 
   // y/colour pass with strips of w columns; false when its shared memory does not fit
   bool set_yw(int w) {
@@ -497,7 +510,7 @@ struct Plan final : PlanBase {
     if (tiled) {
       float best = 1e30f;
       Tuned pick{yw, tc, use_tma};
-      for (int kind = 0; kind < (tma_ok ? 2 : 1); ++kind) {
+      for (int kind = 0; kind < (tma_ok && !force_staged ? 2 : 1); ++kind) {
         use_tma = tma_ok && kind == 0;
         for (int c : cands) {
           tc = c;
@@ -608,7 +621,8 @@ struct Plan final : PlanBase {
     size_t o_ltd = put(lt.data(), P * sizeof(double));
 
     size_t o_tw1 = 0, o_hw1 = 0, o_c41 = 0, o_tw2 = 0, o_hw2 = 0, o_c42 = 0, o_l1 = 0, o_l1d = 0, o_l2 = 0,
-           o_l2d = 0, o_Q = 0, o_lc = 0, o_lcd = 0, o_cs = 0, o_hl = 0, o_hld = 0;
+           o_l2d = 0, o_Q = 0, o_lc = 0, o_lcd = 0, o_cs = 0, o_hl = 0, o_hld = 0, o_wf = 0, o_wi = 0, o_mf = 0,
+           o_mi = 0;
     if (!hue) {
       std::vector<T> tw, hw;
       twid(n1, tw, hw);
@@ -677,6 +691,39 @@ struct Plan final : PlanBase {
       o_cs = put(cs.data(), cs.size() * sizeof(T));
       o_hl = put(hlT.data(), n * sizeof(T));
       o_hld = put(hl.data(), n * sizeof(double));
+      hue_gemm = std::is_same<T, float>::value && n <= kHueGemmMax && B * P >= kHueGemmRows;
+      if (hue_gemm) {
+        // W[slot][i]: 1, cos / sin (2 pi i j / n) of frequency j = (slot + 1) / 2, (-1)^i (Nyquist slot of even n);
+        // the inverse, stored [i][slot], weighs the slots 1, 2, ..., 2, (1) and divides by n
+        std::vector<T> wf((size_t)n * n), wi((size_t)n * n);
+        for (int slot = 0; slot < n; ++slot) {
+          const bool nyq = n % 2 == 0 && slot == n - 1;
+          const int j = (slot + 1) / 2;
+          const double wgt = (slot == 0 || nyq) ? 1.0 : 2.0;
+          for (int i = 0; i < n; ++i) {
+            double v;
+            if (slot == 0) v = 1.0;
+            else if (nyq) v = (i & 1) ? -1.0 : 1.0;
+            else {
+              const double ang = 2 * kPi * (double)(((long long)i * j) % n) / n;
+              v = (slot & 1) ? std::cos(ang) : std::sin(ang);
+            }
+            wf[(size_t)slot * n + i] = (T)v;
+            wi[(size_t)i * n + slot] = (T)(wgt * v / n);
+          }
+        }
+        o_wf = put(wf.data(), wf.size() * sizeof(T));
+        o_wi = put(wi.data(), wi.size() * sizeof(T));
+        // the time DCT and its inverse as P x P matrices (rows of the padded tables above)
+        std::vector<T> mf((size_t)P * P), mi((size_t)P * P);
+        for (int r = 0; r < P; ++r)
+          for (int c = 0; c < P; ++c) {
+            mf[(size_t)r * P + c] = Mf[(size_t)r * pmax + c];
+            mi[(size_t)r * P + c] = Mi[(size_t)r * pmax + c];
+          }
+        o_mf = put(mf.data(), mf.size() * sizeof(T));
+        o_mi = put(mi.data(), mi.size() * sizeof(T));
+      }
     }
     CUDA_OK(cudaMalloc(&tabmem.p, h.size()));
     CUDA_OK(cudaMemcpy(tabmem.p, h.data(), h.size(), cudaMemcpyHostToDevice));
@@ -729,6 +776,12 @@ struct Plan final : PlanBase {
       }
       CUDA_OK(cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     } else {
+      if (hue_gemm) {
+        hwf = (const T*)(base + o_wf);
+        hwi = (const T*)(base + o_wi);
+        hmf = (const T*)(base + o_mf);
+        hmi = (const T*)(base + o_mi);
+      }
       ht.cs = base + o_cs; ht.lam = base + o_hl; ht.lamd = (const double*)(base + o_hld);
       ht.lamt = base + o_lt; ht.lamtd = (const double*)(base + o_ltd);
       ht.Mt_f = base + o_Mf; ht.Mt_i = base + o_Mi;
@@ -793,11 +846,30 @@ struct Plan final : PlanBase {
       if (evs) cudaEventRecord(evs[3], st);
     } else {
       if (evs) cudaEventRecord(evs[0], st);
-      k_hue_fwd<T><<<dim3(P, B), 256, smH, st>>>(g, asrc, f0n, f1n, hat, ht);
+      const dim3 gg((n1 + 63) / 64, (B * P + 63) / 64);
+      if constexpr (std::is_same<T, float>::value) {
+        if (hue_gemm) {   // r into phi (overwritten by the inverse below), then R W^T into hat
+          k_hue_rhs<T><<<grid1d((long long)B * N), 256, 0, st>>>(g, asrc, f0n, f1n, phi);
+          k_gemm_nt<<<gg, 256, 0, st>>>(B * P, n1, n1, phi, hwf, hat);
+        }
+      }
+      if (!hue_gemm) k_hue_fwd<T><<<dim3(P, B), 256, smH, st>>>(g, asrc, f0n, f1n, hat, ht);
       if (evs) cudaEventRecord(evs[1], st);
-      kh<<<dim3((n1 + 256 / pmax - 1) / (256 / pmax), B), 256, smHt, st>>>(g, hat, ht);
+      bool tdone = false;
+      if constexpr (std::is_same<T, float>::value) {
+        if (hue_gemm) {   // the time transforms of all slot columns: hat -> phi (with the divide) -> hat
+          const dim3 gt((n1 + 63) / 64, (P + 63) / 64, B);
+          k_gemm_tn<true><<<gt, 256, 0, st>>>(P, n1, P, (const float*)hmf, hat, phi, (long long)P * n1, ht);
+          k_gemm_tn<false><<<gt, 256, 0, st>>>(P, n1, P, (const float*)hmi, phi, hat, (long long)P * n1, ht);
+          tdone = true;
+        }
+      }
+      if (!tdone) kh<<<dim3((n1 + 256 / pmax - 1) / (256 / pmax), B), 256, smHt, st>>>(g, hat, ht);
       if (evs) cudaEventRecord(evs[2], st);
-      k_hue_inv<T><<<dim3(P, B), 256, smH, st>>>(g, hat, phi, ht);
+      if constexpr (std::is_same<T, float>::value) {
+        if (hue_gemm) k_gemm_nt<<<gg, 256, 0, st>>>(B * P, n1, n1, hat, hwi, phi);
+      }
+      if (!hue_gemm) k_hue_inv<T><<<dim3(P, B), 256, smH, st>>>(g, hat, phi, ht);
       if (evs) cudaEventRecord(evs[3], st);
     }
   }
@@ -828,8 +900,27 @@ struct Plan final : PlanBase {
           done = true;
         }
       }
-      if (!done) launch_pdl(pick_kd<T>(C, check, wx, g.per1 || g.per2), grd, dim3(kTX, kTY), 0, st, g, A, tc, part);
+      if (!done) {
+        const TileLayout Lt{S, n1, n1 * n2, (long long)P * S, n1, (long long)S};
+        launch_pdl(pick_kd<T>(C, check, wx, g.per1 || g.per2), grd, dim3(kTX, kTY), 0, st, g, A, tc, Lt, part);
+      }
       if (check) k_reduce_check<<<B, 256, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass, g.active);
+      return;
+    }
+    if (hue && !check && !wx && !g.active && B >= 8 && !plain_update) {
+      // a batch of hue problems: the tiled update with the problems as its rows (no coupling between rows,
+      // since the y difference factor is zero and the y components of the state stay zero); checks keep the
+      // per-problem kernel below, whose sums are per problem
+      Geo<T> gr = g;
+      gr.n2 = B;
+      gr.B = 1;
+      gr.per2 = 0;
+      gr.s2 = T(0);
+      gr.active = nullptr;
+      const TileLayout Lt{n1, P * n1, n1, 0, n1, 0};
+      const int tcr = std::max(4, (P + 3) / 4);
+      const dim3 grd((n1 + kTX - 2) / (kTX - 1), std::max(1, (B - 1 + kTY - 2) / (kTY - 1)), (P + tcr - 1) / tcr);
+      launch_pdl(pick_kd<T>(1, false, false, true), grd, dim3(kTX, kTY), 0, st, gr, A, tcr, Lt, part);
       return;
     }
     const dim3 grd((n1 + kThreadsUpd - 1) / kThreadsUpd, n2, C * P * B);

@@ -851,6 +851,17 @@ constexpr int kTX = 32, kTY = 8;
 constexpr int kPart = 68;
 constexpr int kPartW = 67;
 
+// Strides of the tiled update's arrays: a time plane, a row, a colour channel and a problem of the cell arrays,
+// and a row and a problem of the boundary densities.  Grids with rows along y: S, n1, n1 n2, P S; n1, S.  A
+// batch of hue problems runs with its problems as the rows (cell arrays [problem][t][bin], densities
+// [problem][bin]): n1, P n1, -, 0; n1, 0 -- with the y difference factor set to zero the rows do not couple.
+struct TileLayout {
+  int plane, row, chan;
+  long long prob;
+  int frow;
+  long long fprob;
+};
+
 // Per-block partial sums of a check (called by every thread of a 32 x 8 block after its plane loop):
 // FP64 sums of the threads' compensated partials, written to part[problem][block][...].
 template <typename T>
@@ -884,7 +895,7 @@ __device__ __forceinline__ void block_check_partials(const KSum<T>& r_db, const 
 // The body of the tiled update.  INTERIOR: every thread of the block has both x and y neighbours
 // inside the grid, so the boundary tests fold away (about three quarters of the blocks at 256^2).
 template <typename T, int C, bool CHECK, bool WRITE_X, bool INTERIOR, bool PXY>
-__device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<T>& A, int TC,
+__device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<T>& A, int TC, const TileLayout& Lt,
                                                   double* __restrict__ part, T (&sbb)[2][kTY][kTX][C],
                                                   double (&smass)[64]) {
   const int lane = threadIdx.x, row = threadIdx.y;
@@ -909,14 +920,14 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
   const bool hasR = INTERIOR || px || xs < g.n1 - 1, hasL = INTERIOR || px || xs > 0;
   const bool hasU = INTERIOR || py || ys < g.n2 - 1, hasD = INTERIOR || py || ys > 0;
   // offsets to the four neighbours in the plane (wrapped on a periodic axis)
+  // 32-bit offsets from per-thread column bases (problem sizes stay below 2^31 cells)
+  const int S = Lt.plane, sy = Lt.row, sc = Lt.chan;
   const int dxr = (px && xs == g.n1 - 1) ? 1 - g.n1 : 1;
   const int dxl = (px && xs == 0) ? g.n1 - 1 : -1;
-  const int dyu = (py && ys == g.n2 - 1) ? (1 - g.n2) * g.n1 : g.n1;
-  const int dyd = (py && ys == 0) ? (g.n2 - 1) * g.n1 : -g.n1;
-  // 32-bit offsets from per-thread column bases (problem sizes stay below 2^31 cells)
-  const int S = g.S, sy = g.n1, sc = g.n1 * g.n2;
-  const size_t col = (size_t)b * g.P * S + xs + (size_t)sy * ys;
-  const size_t col2 = (size_t)b * S + xs + (size_t)sy * ys;
+  const int dyu = (py && ys == g.n2 - 1) ? (1 - g.n2) * sy : sy;
+  const int dyd = (py && ys == 0) ? (g.n2 - 1) * sy : -sy;
+  const size_t col = (size_t)b * Lt.prob + xs + (size_t)sy * ys;
+  const size_t col2 = (size_t)b * Lt.fprob + xs + (size_t)Lt.frow * ys;
   const v4<T>* __restrict__ pa = A.a + col;
   const v4<T>* __restrict__ pb = A.b + col;
   const T* __restrict__ pas = reinterpret_cast<const T*>(pa);   // scalar component loads: pas[4 o + k]
@@ -1092,13 +1103,13 @@ __device__ __forceinline__ void update_tiled_body(const Geo<T>& g, const Arrays<
 // register allocation)
 template <typename T, int C, bool CHECK, bool WRITE_X, bool PXY>
 __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<T> g, Arrays<T> A, int TC,
-                                                                double* __restrict__ part) {
+                                                                TileLayout Lt, double* __restrict__ part) {
   __shared__ T sbb[2][kTY][kTX][C];   // bbar_y exchange, double-buffered by plane parity
   __shared__ double smass[64];
   const int x0 = blockIdx.x * (kTX - 1), y0 = blockIdx.y * (kTY - 1);
   const bool interior = x0 >= 1 && x0 + kTX < g.n1 && y0 >= 1 && y0 + kTY < g.n2;
-  if (interior) update_tiled_body<T, C, CHECK, WRITE_X, true, PXY>(g, A, TC, part, sbb, smass);
-  else update_tiled_body<T, C, CHECK, WRITE_X, false, PXY>(g, A, TC, part, sbb, smass);
+  if (interior) update_tiled_body<T, C, CHECK, WRITE_X, true, PXY>(g, A, TC, Lt, part, sbb, smass);
+  else update_tiled_body<T, C, CHECK, WRITE_X, false, PXY>(g, A, TC, Lt, part, sbb, smass);
 }
 
 

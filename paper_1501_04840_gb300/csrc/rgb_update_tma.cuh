@@ -6,11 +6,12 @@
 // march over a chunk of time planes.  What differs is how a plane reaches the
 // threads: one thread issues three bulk tensor copies per plane -- the tile of
 // a with the column left of it and the row below it, the tile of b, and the
-// tile of phi with a one-cell halo -- into one of two shared-memory slots, and
-// an mbarrier counts their bytes.  The copies of plane t + 2 are issued while
-// plane t + 1 is being computed, so the plane's loads never stall the warps on
-// memory; the threads read their operands from shared memory with constant
-// offsets.  Stores go straight from registers as 16-byte vectors.
+// tile of phi with a one-cell halo -- into shared-memory slots (two for a and
+// b, three for phi, which a plane also reads as the next plane of the plane
+// before it), and an mbarrier per slot counts their bytes.  While plane t is
+// computed, a and b of plane t + 1 and phi of planes t + 1 and t + 2 are
+// already on their way; the threads read their operands from shared memory
+// with constant offsets.  Stores go straight from registers as 16-byte vectors.
 //
 // Every wait on an mbarrier has a time limit.  A wait that runs out sets *err,
 // and the thread carries on without waiting again (its results are then
@@ -30,12 +31,14 @@ struct TmaTiles {
   static constexpr size_t b_bytes = sizeof(float4) * kTX * kTY * C;
   static constexpr size_t p_bytes = sizeof(float) * PX * PY * C;
   static constexpr size_t al(size_t n) { return (n + 127) & ~size_t(127); }
-  static constexpr size_t a_off = 0, b_off = al(a_bytes), p_off = b_off + al(b_bytes);
-  static constexpr size_t slot_bytes = p_off + al(p_bytes);
-  static constexpr size_t sbb_off = 2 * slot_bytes;
+  // two slots of (a, b) and three of phi: a plane's phi is read as the next plane of the plane before it
+  static constexpr size_t a_off = 0, b_off = al(a_bytes);
+  static constexpr size_t ab_bytes = b_off + al(b_bytes);
+  static constexpr size_t p_base = 2 * ab_bytes, p_stride = al(p_bytes);
+  static constexpr size_t sbb_off = p_base + 3 * p_stride;
   static constexpr size_t sbb_bytes = sizeof(float) * 2 * kTY * kTX * C;
   static constexpr size_t mbar_off = sbb_off + al(sbb_bytes);
-  static constexpr size_t total = mbar_off + 64 + 128;   // two mbarriers, and slack to align the base to 128 bytes
+  static constexpr size_t total = mbar_off + 64 + 128;   // five mbarriers, and slack to align the base to 128 bytes
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -112,30 +115,33 @@ __device__ __forceinline__ void update_tma_body(const Geo<float>& g, const Array
   const int ox = x - xa;             // this cell's column in the phi tile
   float (*sbb)[kTY][kTX][C] = reinterpret_cast<float (*)[kTY][kTX][C]>(sm + L::sbb_off);
   const uint32_t bar0 = smem_u32(sm + L::mbar_off);
-  auto bar = [&](int slot) { return bar0 + 8u * (uint32_t)slot; };
-  auto sa = [&](int slot) { return reinterpret_cast<const float4*>(sm + slot * L::slot_bytes + L::a_off); };
-  auto sbv = [&](int slot) { return reinterpret_cast<const float4*>(sm + slot * L::slot_bytes + L::b_off); };
-  auto sp = [&](int slot) { return reinterpret_cast<const float*>(sm + slot * L::slot_bytes + L::p_off); };
-  // copies of the k-th plane of the chunk (plane t0 + k) into slot k & 1: a, b and phi for the computed planes,
-  // phi alone for the plane after the last computed one
-  auto issue = [&](int k) {
+  auto bar_ab = [&](int slot) { return bar0 + 8u * (uint32_t)slot; };        // slots 0, 1
+  auto bar_p = [&](int slot) { return bar0 + 8u * (uint32_t)(2 + slot); };   // slots 0, 1, 2
+  auto sa = [&](int slot) { return reinterpret_cast<const float4*>(sm + slot * L::ab_bytes + L::a_off); };
+  auto sbv = [&](int slot) { return reinterpret_cast<const float4*>(sm + slot * L::ab_bytes + L::b_off); };
+  auto sp = [&](int slot) { return reinterpret_cast<const float*>(sm + L::p_base + slot * L::p_stride); };
+  // copies of the k-th plane of the chunk (plane t0 + k): a and b into slot k % 2 (computed planes), phi into
+  // slot k % 3 (computed planes and the plane after the last one)
+  auto issue_ab = [&](int k) {
+    const int p = t0 + k;
+    if (p > tlast) return;
+    const int slot = k & 1;
+    mbar_expect_tx(bar_ab(slot), (uint32_t)(L::a_bytes + L::b_bytes));
+    const int bp = b * g.P + p;
+    char* base = sm + slot * L::ab_bytes;
+    // rows of a and b are (cell, component) runs: 16 bytes per cell
+    tma_load_4d(smem_u32(base + L::a_off), tmA, 4 * (x0 - 1), y0 - 1, 0, bp, bar_ab(slot));
+    tma_load_4d(smem_u32(base + L::b_off), tmB, 4 * x0, y0, 0, bp, bar_ab(slot));
+  };
+  auto issue_p = [&](int k) {
     const int p = t0 + k;
     if (p > tlast + 1 || p >= g.P) return;
-    const int slot = k & 1;
-    const bool full = p <= tlast;
-    const uint32_t bytes = (uint32_t)((full ? L::a_bytes + L::b_bytes : 0) + L::p_bytes);
-    mbar_expect_tx(bar(slot), bytes);
-    const int bp = b * g.P + p;
-    char* base = sm + slot * L::slot_bytes;
-    if (full) {   // rows of a and b are (cell, component) runs: 16 bytes per cell
-      tma_load_4d(smem_u32(base + L::a_off), tmA, 4 * (x0 - 1), y0 - 1, 0, bp, bar(slot));
-      tma_load_4d(smem_u32(base + L::b_off), tmB, 4 * x0, y0, 0, bp, bar(slot));
-    }
-    tma_load_4d(smem_u32(base + L::p_off), tmP, xa, y0 - 1, 0, bp, bar(slot));
+    const int slot = k % 3;
+    mbar_expect_tx(bar_p(slot), (uint32_t)L::p_bytes);
+    tma_load_4d(smem_u32(sm + L::p_base + slot * L::p_stride), tmP, xa, y0 - 1, 0, b * g.P + p, bar_p(slot));
   };
   if (tid == 0) {
-    mbar_init(bar(0), 1);
-    mbar_init(bar(1), 1);
+    for (int i = 0; i < 5; ++i) mbar_init(bar0 + 8u * (uint32_t)i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (CHECK)
@@ -143,8 +149,11 @@ __device__ __forceinline__ void update_tma_body(const Geo<float>& g, const Array
   __syncthreads();
   pdl_wait();   // phi (inverse x/t pass) and the state are read from here on
   if (tid == 0) {
-    issue(0);
-    issue(1);
+    issue_ab(0);
+    issue_ab(1);
+    issue_p(0);
+    issue_p(1);
+    issue_p(2);
   }
 
   const int S = g.S, sc = g.n1 * g.n2;
@@ -174,17 +183,18 @@ __device__ __forceinline__ void update_tma_body(const Geo<float>& g, const Array
 
 #pragma unroll 1
   for (int t = t0; t <= tlast; ++t) {
-    const int k = t - t0, slot = k & 1, nslot = slot ^ 1;
+    const int k = t - t0, slot = k & 1, ps = k % 3, pn = (k + 1) % 3;
     const int pt = t * S;
     const bool write_plane = t < tend;
     const bool tnext = t + 1 < g.P;
     // once a wait has run out, this thread stops waiting (the error is already recorded below)
-    if (ok) ok = mbar_wait(bar(slot), (k >> 1) & 1);
-    if (ok && tnext) ok = mbar_wait(bar(nslot), ((k + 1) >> 1) & 1);
+    if (ok) ok = mbar_wait(bar_ab(slot), (k >> 1) & 1);
+    if (ok) ok = mbar_wait(bar_p(ps), (k / 3) & 1);
+    if (ok && tnext) ok = mbar_wait(bar_p(pn), ((k + 1) / 3) & 1);
     const float4* ta = sa(slot);
     const float4* tb = sbv(slot);
-    const float* tp = sp(slot);
-    const float* tpn = sp(nslot);
+    const float* tp = sp(ps);
+    const float* tpn = sp(pn);
     float bb[C][4], bn[C][4], xr[C][4], phn[C];
     float4 la[C], lb[C];
     float phy[C], phd[C], la1d[C], la0l[C], phl[C], phx[C];
@@ -257,8 +267,11 @@ __device__ __forceinline__ void update_tma_body(const Geo<float>& g, const Array
     const int par = t & 1;
 #pragma unroll
     for (int c = 0; c < C; ++c) sbb[par][row][lane][c] = bb[c][1];
-    __syncthreads();   // every thread is done with slot `slot`: refill it with plane t + 2
-    if (tid == 0) issue(k + 2);
+    __syncthreads();   // every thread is done with a, b of plane t and phi of plane t: refill their slots
+    if (tid == 0) {
+      issue_ab(k + 2);
+      issue_p(k + 3);
+    }
     if (out && t > t0) {
 #pragma unroll
       for (int c = 0; c < C; ++c)

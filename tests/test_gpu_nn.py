@@ -57,12 +57,14 @@ def test_conv3d_forward_fp32(K, cin, cout, vol):
 
 @pytest.mark.parametrize("cin,cout,vol,out_f32", [(16, 16, (1, 3, 8, 16), True), (32, 64, (2, 2, 5, 32), True),
                                                   (64, 48, (1, 2, 3, 128), False), (16, 32, (1, 4, 9, 64), False),
-                                                  (48, 16, (2, 3, 4, 8), True), (16, 16, (2, 2, 3, 256), True)])
+                                                  (48, 16, (2, 3, 4, 8), True), (16, 16, (2, 2, 3, 256), True),
+                                                  (32, 64, (1, 2, 9, 128), False)])
 def test_conv3d_tcgen05_tiles(K, cin, cout, vol, out_f32, monkeypatch):
     """Shapes the tcgen05 convolution takes (cout % 16 == 0, X dividing 128 or a multiple of it): tiles of
-    128 voxels over one or several rows, partial tiles at the y edge, rows of 128 voxels in the halo form
-    (X = 128, 256) and in the per-tap form (DYNOT_CONV=tap), fp32 and bf16 outputs with ReLU, against the
-    oracle; the mma.sync kernels (DYNOT_CONV=mma) give the same outputs within the same bound."""
+    128 voxels over one or several rows, partial tiles at the y edge, rows of 128 voxels (X = 128, 256) in
+    the four-row block form (the default up to 64 output channels), the halo-row form (DYNOT_CONV=halo) and
+    the per-tap form (DYNOT_CONV=tap), fp32 and bf16 outputs with ReLU, against the oracle; the mma.sync
+    kernels (DYNOT_CONV=mma) give the same outputs within the same bound."""
     import torch
     x = _bf(vol + (cin,), 11)
     w = _bf((cout, 27, cin), 12, 0.2)
@@ -70,7 +72,7 @@ def test_conv3d_tcgen05_tiles(K, cin, cout, vol, out_f32, monkeypatch):
     ref = unet.conv3d(_np(x), _np(w), b.double().numpy(), relu=True)
     bound = unet.conv3d(np.abs(_np(x)), np.abs(_np(w))) + np.abs(b.double().numpy())
     outs = []
-    for kind in ("tcgen05", "tap", "mma"):
+    for kind in ("tcgen05", "halo", "tap", "mma"):
         monkeypatch.setenv("DYNOT_CONV", kind)
         dt = torch.float32 if out_f32 else torch.bfloat16
         y = torch.full(vol + (cout,), float("nan"), dtype=dt, device="cuda")

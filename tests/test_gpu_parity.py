@@ -375,6 +375,53 @@ def test_split_xt_passes_match_oracle(ot, n, bc, P, precision, monkeypatch):
     assert rel(x, xo) <= tol and rel(b, bo) <= tol
 
 
+@pytest.mark.parametrize("bins,P,batch,smooth", [(360, 64, 8, False), (101, 32, 16, True), (720, 16, 40, False)])
+def test_hue_batch_dft_product_matches_oracle(ot, bins, P, batch, smooth):
+    """Hue plans of at least 512 rows (batch x P) run the real DFT along the bins as one dense matrix product
+    over all rows: one iteration of every problem from its own random state against the oracle, with the
+    bound of the single-problem tests."""
+    g = oracle_grid((bins,), ("periodic",), P)
+    plan = ot.Plan(ot.grid((bins,), ("periodic",), P, sigma=SIG, tau=TAU), batch=batch)
+    pairs = [random_pair(g, 40 + i) for i in range(batch)]
+    states = [_random_state(g, 60 + i, smooth) for i in range(batch)]
+    cat = lambda parts: f32(np.concatenate([np.asarray(p, np.float64).ravel() for p in parts]))
+    plan.state_set(cat([p[0] for p in pairs]), cat([p[1] for p in pairs]),
+                   cat([pack_path(g, st.m, st.f) for st in states]), cat([pack_dual(g, st.bm, st.bf) for st in states]),
+                   cat([pack_dual(g, st.bbm, st.bbf) for st in states]))
+    plan.iterate(1)
+    x, _, _ = plan.state_get()
+    x = x.reshape(batch, -1)
+    for i in range(batch):
+        f0, f1 = pairs[i]
+        new, _ = o.pdhg_step(g, states[i], f0, f1, SIG, TAU)
+        assert rel(x[i], pack_path(g, new.m, new.f)) <= _step_tolerance(g, states[i], f0, f1)
+
+
+def test_hue_batch_row_update_matches_cell_update(ot, monkeypatch):
+    """A hue plan of 8 or more problems updates its plain iterations with the tiled kernel, the problems as
+    its rows; DYNOT_UPDATE_KERNEL=plain keeps the cell-by-cell kernel.  Seven iterations (six plain, one
+    check) from the same random states agree to float32 rounding (1e-5, as for the RGB update kernels)."""
+    bins, P, batch = 101, 20, 12
+    g = oracle_grid((bins,), ("periodic",), P)
+    pairs = [random_pair(g, 80 + i) for i in range(batch)]
+    states = [_random_state(g, 90 + i, True) for i in range(batch)]
+    cat = lambda parts: f32(np.concatenate([np.asarray(p, np.float64).ravel() for p in parts]))
+    args = (cat([p[0] for p in pairs]), cat([p[1] for p in pairs]),
+            cat([pack_path(g, st.m, st.f) for st in states]), cat([pack_dual(g, st.bm, st.bf) for st in states]),
+            cat([pack_dual(g, st.bbm, st.bbf) for st in states]))
+    out = []
+    for kind in ("rows", "plain"):
+        if kind == "plain":
+            monkeypatch.setenv("DYNOT_UPDATE_KERNEL", "plain")
+        plan = ot.Plan(ot.grid((bins,), ("periodic",), P, sigma=SIG, tau=TAU), batch=batch)
+        plan.state_set(*args)
+        plan.iterate(7)
+        out.append(plan.state_get())
+        plan.close()
+    for a, b in zip(out[0], out[1]):
+        assert rel(a, b) <= 1e-5
+
+
 @pytest.mark.parametrize("where", ["dual", "path"])
 def test_non_finite_state_is_reported(ot, where):
     """The detector of non-finite residuals: a NaN planted on the host in the dual (or an Inf in the
