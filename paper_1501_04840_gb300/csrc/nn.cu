@@ -727,7 +727,8 @@ static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const 
     CUtensorMap tmR, tmW;
     const cuuint64_t dim[5] = {(cuuint64_t)xs, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)T, (cuuint64_t)N};
     const cuuint64_t str[4] = {2ull * xs, 2ull * xs * X, 2ull * xs * X * Y, 2ull * xs * X * Y * T};
-    const cuuint32_t box[5] = {8, tc::kHaloRows, (cuuint32_t)tc::kRBin, 1, 1};
+    const int rb = Cout <= 32 ? 8 : tc::kRB;
+    const cuuint32_t box[5] = {8, tc::kHaloRows, (cuuint32_t)(rb + 2), 1, 1};
     const cuuint32_t one[5] = {1, 1, 1, 1, 1};
     const cuuint64_t wdim[3] = {(cuuint64_t)Cin, 27, (cuuint64_t)Cout};
     const cuuint64_t wstr[2] = {2ull * Cin, 2ull * 27 * Cin};
@@ -739,13 +740,13 @@ static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const 
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
-    const size_t smem = tc::rows_smem_bytes(Cout);
-    cudaError_t e = cudaFuncSetAttribute((const void*)tc::k_conv3d_tc_rows,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = rb == 8 ? tc::rows_smem_bytes<8>(Cout) : tc::rows_smem_bytes<tc::kRB>(Cout);
+    auto kern = rb == 8 ? tc::k_conv3d_tc_rows<8> : tc::k_conv3d_tc_rows<tc::kRB>;
+    cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-      const int nrb = (Y + tc::kRB - 1) / tc::kRB;
-      tc::k_conv3d_tc_rows<<<dim3((unsigned)(g.nxb * nrb), (unsigned)(N * T)), 128, smem, st>>>(
-          g, Cin, Cout, xo, bias, y, ys, yo, relu, out_f32, tmR, tmW);
+      const int nrb = (Y + rb - 1) / rb;
+      kern<<<dim3((unsigned)(g.nxb * nrb), (unsigned)(N * T)), 128, smem, st>>>(g, Cin, Cout, xo, bias, y, ys, yo,
+                                                                               relu, out_f32, tmR, tmW);
       e = cudaGetLastError();
     }
     *status = e == cudaSuccess ? OT_OK : seterr(OT_ECUDA, "conv3d (tcgen05 rows): %s", cudaGetErrorString(e));

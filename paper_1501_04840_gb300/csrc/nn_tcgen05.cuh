@@ -255,14 +255,23 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(Geom v, int Cin, int Cout, in
 // the weights of its nine (dy, dx) taps.  Each stage issues 36 MMAs (4 output rows x 9 taps) into four
 // accumulators of Cout columns: every input row is copied once per (dt, chunk) for four output rows and every
 // weight slice once per four rows, which cuts the copies per MMA about threefold against the halo row form.
-constexpr int kRB = 4, kRBin = kRB + 2;
-constexpr uint32_t kRowPlane = 12544;                    // 6 rows x 130 voxels x 16 bytes = 12480, padded to 128
-constexpr uint32_t kRowsA = 25600;                       // two planes, padded to 1024 bytes
+// RB output rows per CTA: 4 for up to 64 output channels, 8 for up to 32 (RB accumulators of at most 64 and 32
+// columns fill 256 of the 512 tensor-memory columns, so two CTAs share an SM).
+template <int RB>
+struct RowsForm {
+  static constexpr int in = RB + 2;                                                // input rows per stage
+  static constexpr uint32_t plane = ((uint32_t)in * 130u * 16u + 127u) & ~127u;   // one 8-channel plane
+  static constexpr uint32_t a_bytes = (2u * plane + 1023u) & ~1023u;
+};
 constexpr int kRowStages = 2;
-__host__ __device__ constexpr uint32_t rows_stage_bytes(int cout) { return kRowsA + 9u * b_bytes(cout); }
+template <int RB>
+__host__ __device__ constexpr uint32_t rows_stage_bytes(int cout) { return RowsForm<RB>::a_bytes + 9u * b_bytes(cout); }
 __host__ __device__ constexpr int rows_col_stride(int cout) { return cout <= 16 ? 16 : (cout <= 32 ? 32 : 64); }
-inline size_t rows_smem_bytes(int cout) { return (size_t)kRowStages * rows_stage_bytes(cout) + 128 + 1024; }
+template <int RB>
+inline size_t rows_smem_bytes(int cout) { return (size_t)kRowStages * rows_stage_bytes<RB>(cout) + 128 + 1024; }
+constexpr int kRB = 4;   // rows per CTA of the wider outputs (the host picks 8 up to 32 output channels)
 
+template <int RB>
 __global__ void __launch_bounds__(128) k_conv3d_tc_rows(Geom v, int Cin, int Cout, int xo, const float* __restrict__ bias,
                                                         void* __restrict__ y, int ys, int yo, int relu, int out_f32,
                                                         const __grid_constant__ CUtensorMap tmX,
@@ -270,9 +279,10 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_rows(Geom v, int Cin, int Cou
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x0 = (blockIdx.x % v.nxb) * 128, y0 = (blockIdx.x / v.nxb) * kRB;
+  using F = RowsForm<RB>;
+  const int x0 = (blockIdx.x % v.nxb) * 128, y0 = (blockIdx.x / v.nxb) * RB;
   const int t = blockIdx.y % v.T, n = blockIdx.y / v.T;
-  const uint32_t sb = rows_stage_bytes(Cout), bb = b_bytes(Cout);
+  const uint32_t sb = rows_stage_bytes<RB>(Cout), bb = b_bytes(Cout);
   const uint32_t base = saddr(sm);
   const uint32_t bars = base + kRowStages * sb;   // full[kRowStages], empty[kRowStages], done
   auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_rows(Geom v, int Cin, int Cou
   const uint32_t done = bars + 8u * (2 * kRowStages);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kRowStages * sb + 8 * (2 * kRowStages + 1));
   const int cs = rows_col_stride(Cout);
-  const int ncols = tmem_cols(kRB * cs);
+  const int ncols = tmem_cols(RB * cs);
   const int chunks = Cin / 16, nk = 3 * chunks;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kRowStages; ++s) {
@@ -307,10 +317,11 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_rows(Geom v, int Cin, int Cou
       const int s = i % kRowStages;
       if (i >= kRowStages && ok) ok = bar_wait(empty(s), ((i / kRowStages) & 1) ^ 1);
       const int dt = i / chunks - 1, cc = i % chunks;
-      bar_expect_tx(full(s), 2u * kRBin * kHaloRows * 16u + 9u * 32u * (uint32_t)Cout);
+      bar_expect_tx(full(s), 2u * F::in * kHaloRows * 16u + 9u * 32u * (uint32_t)Cout);
       for (int h = 0; h < 2; ++h)
-        tma_5d(base + s * sb + h * kRowPlane, &tmX, xo + 16 * cc + 8 * h, x0 - 1, y0 - 1, t + dt, n, full(s));
-      for (int q = 0; q < 9; ++q) tma_3d(base + s * sb + kRowsA + q * bb, &tmW, 16 * cc, 9 * (dt + 1) + q, 0, full(s));
+        tma_5d(base + s * sb + h * F::plane, &tmX, xo + 16 * cc + 8 * h, x0 - 1, y0 - 1, t + dt, n, full(s));
+      for (int q = 0; q < 9; ++q)
+        tma_3d(base + s * sb + F::a_bytes + q * bb, &tmW, 16 * cc, 9 * (dt + 1) + q, 0, full(s));
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = idesc_bf16(kM, Cout);
@@ -318,12 +329,16 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_rows(Geom v, int Cin, int Cou
       const int s = i % kRowStages;
       if (ok) ok = bar_wait(full(s), (i / kRowStages) & 1);
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      for (int r = 0; r < kRB; ++r)
+      // descriptors of the stage's first input voxel and first weight slice; the start-address field counts
+      // 16-byte units, so later rows, voxels and slices are added to it
+      const uint64_t ad0 = desc_k_plain(base + s * sb, F::plane);
+      const uint64_t bd0 = desc_k32(base + s * sb + F::a_bytes);
+      for (int r = 0; r < RB; ++r)
         for (int q = 0; q < 9; ++q) {
           // output row r, tap (dy, dx) = (q / 3 - 1, q % 3 - 1): input row r + dy + 1 of the stage, from voxel dx + 1
           const int arow = r + q / 3, ax = q % 3;
-          const uint64_t ad = desc_k_plain(base + s * sb + (uint32_t)(arow * (int)kHaloRows + ax) * 16u, kRowPlane);
-          const uint64_t bd = desc_k32(base + s * sb + kRowsA + q * bb);
+          const uint64_t ad = ad0 + (uint64_t)(arow * (int)kHaloRows + ax);
+          const uint64_t bd = bd0 + (uint64_t)(q * (bb >> 4));
           asm volatile(
               "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(r * cs)),
@@ -342,7 +357,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_rows(Geom v, int Cin, int Cou
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const int xx = x0 + 32 * warp + lane;
   const float nanv = __int_as_float(0x7fc00000);
-  for (int r = 0; r < kRB; ++r) {
+  for (int r = 0; r < RB; ++r) {
     const int yy = y0 + r;
     const bool store = xx < v.X && yy < v.Y;
     const long long vox = (((long long)n * v.T + t) * v.Y + yy) * v.X + xx;
