@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--conv", action="store_true",
                     help="3x3x3 convolution layers of the warm-start network at 128x128x32 (batch 4): tcgen05 "
                          "against the mma.sync kernels, TFLOP/s against the measured bf16 peak")
+    ap.add_argument("--profile-case", choices=["rgb", "conv"], default=None,
+                    help="small fixed cases for ncu captures: 'rgb' runs a 300-iteration solve of the 256x256x3x32 "
+                         "pair and two profiled iterations; 'conv' runs two 32->32 and two 64->64 convolutions")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the kernel profile, time-to-tolerance and end-to-end legs (for profiler runs)")
     return ap.parse_args()
@@ -672,8 +675,40 @@ def hue_pipeline_bench(n: int = 512, bins: int = 360, Ph: int = 16):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(which: str):
+    """Small fixed workloads for ncu captures (launch counts stable enough for `-s`/`-c`)."""
+    import torch
+    import paper_1501_04840_gb300 as ot
+    from paper_1501_04840_gb300 import _build, nn, synth
+    _build.build()
+    torch.cuda.set_device(0)
+    if which == "rgb":
+        f0, f1 = synth.rgb_pair(N1, N2, BLOBS, 0)
+        d0, d1 = torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda()
+        plan = ot.Plan(ot.rgb_grid(N1, N2, P))
+        plan.solve(d0, d1, 300, check_every=300)
+        torch.cuda.synchronize()
+        print(json.dumps(plan.profile(2)), flush=True)
+        return
+    vol = (4, 32, 128, 128)
+    g = torch.Generator().manual_seed(0)
+    for cin, cout in ((32, 32), (64, 64)):
+        x = torch.randn(*vol, cin, generator=g).to(torch.bfloat16).cuda()
+        w = (0.1 * torch.randn(cout, 27, cin, generator=g)).to(torch.bfloat16).cuda()
+        b = torch.zeros(cout, device="cuda")
+        y = torch.empty(*vol, cout, dtype=torch.bfloat16, device="cuda")
+        for _ in range(2):
+            nn.conv3d(vol, nn.whole(x), w, b, nn.whole(y), relu=True)
+        torch.cuda.synchronize()
+        nn.check()
+    print(json.dumps({"conv": "ok"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.hue_pipeline:
         hue_pipeline_bench()
         return

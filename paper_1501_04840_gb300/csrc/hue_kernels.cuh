@@ -223,47 +223,71 @@ __global__ void __launch_bounds__(256) k_hue_rhs(Geo<T> g, const v4<T>* __restri
 
 static __global__ void __launch_bounds__(256) k_gemm_nt(int M, int N, int K, const float* __restrict__ A,
                                                  const float* __restrict__ Bm, float* __restrict__ C) {
-  __shared__ __align__(16) float As[16][68];
-  __shared__ __align__(16) float Bs[16][68];
+  // K in steps of 32 through two shared-memory buffers: the global loads of the next step are in flight
+  // (in registers) while the products of this one run, with one barrier per step
+  constexpr int BK = 32, LD = 68;
+  __shared__ __align__(16) float As[2][BK][LD];
+  __shared__ __align__(16) float Bs[2][BK][LD];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  // loads: element q of this thread is row (tid >> 3) + 32 (q >> 2), k (tid & 7) + 8 (q & 3) of the step; a
+  // warp reads 32-byte runs of four rows, and its transposed stores hit 32 different banks
+  const int lk = threadIdx.x & 7, lr = threadIdx.x >> 3;
+  float ra[8], rb[8];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = lr + 32 * (q >> 2), k = k0 + lk + 8 * (q & 3);
+      ra[q] = (k < K && m0 + r < M) ? A[(size_t)(m0 + r) * K + k] : 0.f;
+      rb[q] = (k < K && n0 + r < N) ? Bm[(size_t)(n0 + r) * K + k] : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      As[buf][lk + 8 * (q & 3)][lr + 32 * (q >> 2)] = ra[q];
+      Bs[buf][lk + 8 * (q & 3)][lr + 32 * (q >> 2)] = rb[q];
+    }
+  };
   float acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) fetch(k0 + BK);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = threadIdx.x + 256 * q;   // row idx / 16 of the tile, k idx % 16
-      const int r = idx >> 4, kk = idx & 15;
-      const bool kin = k0 + kk < K;
-      As[kk][r] = (m0 + r < M && kin) ? A[(size_t)(m0 + r) * K + k0 + kk] : 0.f;
-      Bs[kk][r] = (n0 + r < N && kin) ? Bm[(size_t)(n0 + r) * K + k0 + kk] : 0.f;
-    }
-    __syncthreads();
-    // the 16 terms of this K step are summed on their own and then added to the total, which keeps the
-    // rounding error of a sum over K terms near that of 16 + K / 16 additions
-    float part[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    for (int h = 0; h < 2; ++h) {
+      // each run of 16 terms is summed on its own and then added to the total, which keeps the rounding
+      // error of a sum over K terms near that of 16 + K / 16 additions
+      float part[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
+        for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(&As[buf][16 * h + kk][4 * ty]);
+        const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][16 * h + kk][4 * tx]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
+    if (more) stash(buf ^ 1);   // buffer buf ^ 1 was last read before the previous barrier
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -343,6 +367,108 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int M, int N, int K, const floa
         else v = v / lam;
       }
       Cz[(size_t)m * N + nn] = v;
+    }
+  }
+}
+
+// The time transforms of the hue rows with the divide between them, in one launch for P <= 64: block
+// (column block, problem z) takes X = hat[z][0:P][n0:n0+64] into shared memory, forms Y = (Mf X) / lambda
+// there (the forward DCT along t and the eigen-divide of k_gemm_tn<true>) and writes Mi Y back to the same
+// place (k_gemm_tn<false>).  Mf [k][t] and Mi [t][k] are held transposed, so that the four rows of a thread
+// are one 16-byte read; the sums run in the same groups of 16 terms as k_gemm_tn's.
+constexpr int kHueTdivMaxP = 64, kHueTdivLD = 68;
+constexpr size_t kHueTdivSmem = sizeof(float) * 3 * 64 * kHueTdivLD;
+
+static __global__ void __launch_bounds__(256) k_hue_tdiv(int P, int N, const float* __restrict__ Mf,
+                                                  const float* __restrict__ Mi, float* __restrict__ hat,
+                                                  long long bs, HueTables tb) {
+  extern __shared__ __align__(16) float tsm[];
+  constexpr int LD = kHueTdivLD;
+  float* MfT = tsm;              // [t][k]
+  float* MiT = tsm + 64 * LD;    // [k][t]
+  float* X = tsm + 128 * LD;     // [t][n], then Y [k][n]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int n0 = blockIdx.x * 64;
+  float* hz = hat + (size_t)blockIdx.y * bs;
+  {
+    // all 48 loads of this thread in flight at once, then the shared-memory stores
+    float vm[16], vi[16], vx[16];
+    const int c = threadIdx.x & 63;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int r = (threadIdx.x >> 6) + 4 * q;   // row r, column c of the P x P matrices (zero outside)
+      const bool in = r < P && c < P;
+      vm[q] = in ? Mf[(size_t)r * P + c] : 0.f;
+      vi[q] = in ? Mi[(size_t)r * P + c] : 0.f;
+      vx[q] = (r < P && n0 + c < N) ? hz[(size_t)r * N + n0 + c] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int r = (threadIdx.x >> 6) + 4 * q;
+      MfT[c * LD + r] = vm[q];
+      MiT[c * LD + r] = vi[q];
+      X[r * LD + c] = vx[q];
+    }
+  }
+  __syncthreads();
+  // products of the 4 x 4 outputs of this thread, in runs of 16 terms over the padded 64
+  auto product = [&](const float* AT, float (&acc)[4][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < P; k0 += 16) {
+      float part[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(&AT[(k0 + kk) * LD + 4 * ty]);
+        const float4 b = *reinterpret_cast<const float4*>(&X[(k0 + kk) * LD + 4 * tx]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
+    }
+  };
+  float acc[4][4];
+  product(MfT, acc);
+  __syncthreads();   // every thread is done with X: it now takes Y
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = 4 * ty + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nn = n0 + 4 * tx + j;
+      float v = 0.f;
+      if (m < P && nn < N) {
+        v = acc[i][j];
+        const float lam = ((const float*)tb.lam)[nn] + ((const float*)tb.lamt)[m];
+        if (!(lam > 0.f)) v = 0.f;
+        else if ((double)lam < tb.lam_fp64) v = (float)((double)v / (tb.lamd[nn] + tb.lamtd[m]));
+        else v = v / lam;
+      }
+      X[m * LD + 4 * tx + j] = v;
+    }
+  }
+  __syncthreads();
+  product(MiT, acc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int t = 4 * ty + i;
+    if (t >= P) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nn = n0 + 4 * tx + j;
+      if (nn < N) hz[(size_t)t * N + nn] = acc[i][j];
     }
   }
 }

@@ -777,6 +777,8 @@ struct Plan final : PlanBase {
       CUDA_OK(cudaFuncSetAttribute((const void*)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     } else {
       if (hue_gemm) {
+        CUDA_OK(cudaFuncSetAttribute((const void*)k_hue_tdiv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kHueTdivSmem));
         hwf = (const T*)(base + o_wf);
         hwi = (const T*)(base + o_wi);
         hmf = (const T*)(base + o_mf);
@@ -859,8 +861,13 @@ struct Plan final : PlanBase {
       if constexpr (std::is_same<T, float>::value) {
         if (hue_gemm) {   // the time transforms of all slot columns: hat -> phi (with the divide) -> hat
           const dim3 gt((n1 + 63) / 64, (P + 63) / 64, B);
-          k_gemm_tn<true><<<gt, 256, 0, st>>>(P, n1, P, (const float*)hmf, hat, phi, (long long)P * n1, ht);
-          k_gemm_tn<false><<<gt, 256, 0, st>>>(P, n1, P, (const float*)hmi, phi, hat, (long long)P * n1, ht);
+          if (P <= kHueTdivMaxP) {
+            k_hue_tdiv<<<dim3((n1 + 63) / 64, B), 256, kHueTdivSmem, st>>>(P, n1, (const float*)hmf,
+                                                                           (const float*)hmi, hat, (long long)P * n1, ht);
+          } else {
+            k_gemm_tn<true><<<gt, 256, 0, st>>>(P, n1, P, (const float*)hmf, hat, phi, (long long)P * n1, ht);
+            k_gemm_tn<false><<<gt, 256, 0, st>>>(P, n1, P, (const float*)hmi, phi, hat, (long long)P * n1, ht);
+          }
           tdone = true;
         }
       }
