@@ -221,37 +221,37 @@ __global__ void __launch_bounds__(256) k_hue_rhs(Geo<T> g, const v4<T>* __restri
   }
 }
 
-static __global__ void __launch_bounds__(256) k_gemm_nt(int M, int N, int K, const float* __restrict__ A,
+static __global__ void __launch_bounds__(128) k_gemm_nt(int M, int N, int K, const float* __restrict__ A,
                                                  const float* __restrict__ Bm, float* __restrict__ C) {
-  // K in steps of 32 through two shared-memory buffers: the global loads of the next step are in flight
-  // (in registers) while the products of this one run, with one barrier per step
+  // 128 threads, 8 x 4 outputs each; K in steps of 32 through two shared-memory buffers: the global loads of
+  // the next step are in flight (in registers) while the products of this one run, one barrier per step
   constexpr int BK = 32, LD = 68;
   __shared__ __align__(16) float As[2][BK][LD];
   __shared__ __align__(16) float Bs[2][BK][LD];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // columns 4 tx .. 4 tx + 3, rows 8 ty .. 8 ty + 7
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  // loads: element q of this thread is row (tid >> 3) + 32 (q >> 2), k (tid & 7) + 8 (q & 3) of the step; a
+  // loads: element q of this thread is row (tid >> 3) + 16 (q >> 2), k (tid & 7) + 8 (q & 3) of the step; a
   // warp reads 32-byte runs of four rows, and its transposed stores hit 32 different banks
   const int lk = threadIdx.x & 7, lr = threadIdx.x >> 3;
-  float ra[8], rb[8];
+  float ra[16], rb[16];
   auto fetch = [&](int k0) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int r = lr + 32 * (q >> 2), k = k0 + lk + 8 * (q & 3);
+    for (int q = 0; q < 16; ++q) {
+      const int r = lr + 16 * (q >> 2), k = k0 + lk + 8 * (q & 3);
       ra[q] = (k < K && m0 + r < M) ? A[(size_t)(m0 + r) * K + k] : 0.f;
       rb[q] = (k < K && n0 + r < N) ? Bm[(size_t)(n0 + r) * K + k] : 0.f;
     }
   };
   auto stash = [&](int buf) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      As[buf][lk + 8 * (q & 3)][lr + 32 * (q >> 2)] = ra[q];
-      Bs[buf][lk + 8 * (q & 3)][lr + 32 * (q >> 2)] = rb[q];
+    for (int q = 0; q < 16; ++q) {
+      As[buf][lk + 8 * (q & 3)][lr + 16 * (q >> 2)] = ra[q];
+      Bs[buf][lk + 8 * (q & 3)][lr + 16 * (q >> 2)] = rb[q];
     }
   };
-  float acc[4][4];
+  float acc[8][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
   fetch(0);
@@ -265,23 +265,24 @@ static __global__ void __launch_bounds__(256) k_gemm_nt(int M, int N, int K, con
     for (int h = 0; h < 2; ++h) {
       // each run of 16 terms is summed on its own and then added to the total, which keeps the rounding
       // error of a sum over K terms near that of 16 + K / 16 additions
-      float part[4][4];
+      float part[8][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
-        const float4 a = *reinterpret_cast<const float4*>(&As[buf][16 * h + kk][4 * ty]);
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][16 * h + kk][8 * ty]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][16 * h + kk][8 * ty + 4]);
         const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][16 * h + kk][4 * tx]);
-        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
     }
@@ -290,8 +291,8 @@ static __global__ void __launch_bounds__(256) k_gemm_nt(int M, int N, int K, con
     buf ^= 1;
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + 4 * ty + i;
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + 8 * ty + i;
     if (m >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {

@@ -852,7 +852,7 @@ struct Plan final : PlanBase {
       if constexpr (std::is_same<T, float>::value) {
         if (hue_gemm) {   // r into phi (overwritten by the inverse below), then R W^T into hat
           k_hue_rhs<T><<<grid1d((long long)B * N), 256, 0, st>>>(g, asrc, f0n, f1n, phi);
-          k_gemm_nt<<<gg, 256, 0, st>>>(B * P, n1, n1, phi, hwf, hat);
+          k_gemm_nt<<<gg, 128, 0, st>>>(B * P, n1, n1, phi, hwf, hat);
         }
       }
       if (!hue_gemm) k_hue_fwd<T><<<dim3(P, B), 256, smH, st>>>(g, asrc, f0n, f1n, hat, ht);
@@ -874,7 +874,7 @@ struct Plan final : PlanBase {
       if (!tdone) kh<<<dim3((n1 + 256 / pmax - 1) / (256 / pmax), B), 256, smHt, st>>>(g, hat, ht);
       if (evs) cudaEventRecord(evs[2], st);
       if constexpr (std::is_same<T, float>::value) {
-        if (hue_gemm) k_gemm_nt<<<gg, 256, 0, st>>>(B * P, n1, n1, hat, hwi, phi);
+        if (hue_gemm) k_gemm_nt<<<gg, 128, 0, st>>>(B * P, n1, n1, hat, hwi, phi);
       }
       if (!hue_gemm) k_hue_inv<T><<<dim3(P, B), 256, smH, st>>>(g, hat, phi, ht);
       if (evs) cudaEventRecord(evs[3], st);
