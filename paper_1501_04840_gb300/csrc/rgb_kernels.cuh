@@ -406,6 +406,28 @@ __host__ __device__ __forceinline__ size_t xt_layout(XtSmem<T>* s, char* sm, int
   return off;
 }
 
+// Writes the (t, x) tile [P][n1] of one (y, c) row to dst (cell layout: planes S apart).  FP32 rows whose
+// length is a multiple of 4 go out as 16-byte vectors (a plane's n1 / 4 vectors per pass of the block, 256 / (n1 / 4)
+// planes at once), which takes a quarter of the store instructions of one cell per thread.
+template <typename T>
+__device__ __forceinline__ void store_tile_rows(const T* tile, T* __restrict__ dst, size_t S, int P, int n1) {
+  if constexpr (std::is_same<T, float>::value) {
+    const int nv = n1 >> 2;
+    if ((n1 & 3) == 0 && nv <= (int)blockDim.x && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      const int per = blockDim.x / nv, xv = threadIdx.x % nv, tq = threadIdx.x / nv;
+      if (tq < per) {
+#pragma unroll 8
+        for (int t = tq; t < P; t += per)
+          *reinterpret_cast<float4*>(dst + (size_t)t * S + 4 * xv) =
+              *reinterpret_cast<const float4*>(tile + t * n1 + 4 * xv);
+      }
+      return;
+    }
+  }
+  for (int t = 0; t < P; ++t)
+    for (int x = threadIdx.x; x < n1; x += blockDim.x) dst[(size_t)t * S + x] = tile[t * n1 + x];
+}
+
 // N1 == 0 selects the dense x transform.
 template <typename T, int N1, int N2, int PMAX>
 __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, const v4<T>* __restrict__ ap,
@@ -480,8 +502,7 @@ __global__ void __launch_bounds__(256, DYNOT_XT_MINB) k_rhs_fwd_xt(Geo<T> g, con
   }
   __syncthreads();
   pdl_trigger();
-  for (int t = 0; t < P; ++t)
-    for (int x = threadIdx.x; x < n1; x += blockDim.x) rhat[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
+  store_tile_rows<T>(s.tile, rhat + cidx(g, b, 0, 0, y, c), (size_t)g.S, P, n1);
 }
 
 // ---------------------------------------------------------------------------
@@ -650,8 +671,7 @@ __global__ void __launch_bounds__(256, DYNOT_XTC_MINB) k_inv_xt(Geo<T> g, const 
     else dct_dense_rows<T, false>(rows, P, n1, true, (T*)s.scr, 2 * scr_elems, s.cos4);
   }
   pdl_trigger();
-  for (int t = 0; t < P; ++t)
-    for (int x = threadIdx.x; x < n1; x += blockDim.x) phi[cidx(g, b, t, x, y, c)] = s.tile[t * n1 + x];
+  store_tile_rows<T>(s.tile, phi + cidx(g, b, 0, 0, y, c), (size_t)g.S, P, n1);
 }
 
 // ---------------------------------------------------------------------------
