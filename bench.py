@@ -72,7 +72,8 @@ def parse():
                     help="section 5's hue image morph on a synthetic 512x512 flower pair (360 bins, 16 steps)")
     ap.add_argument("--conv", action="store_true",
                     help="3x3x3 convolution layers of the warm-start network at 128x128x32 (batch 4): tcgen05 "
-                         "against the mma.sync kernels, TFLOP/s against the measured bf16 peak")
+                         "(persistent up to 16 output channels; 'rows': one tile per CTA) against the mma.sync "
+                         "kernels, TFLOP/s against the measured bf16 peak")
     ap.add_argument("--profile-case", choices=["rgb", "conv"], default=None,
                     help="small fixed cases for ncu captures: 'rgb' runs a 300-iteration solve of the 256x256x3x32 "
                          "pair and two profiled iterations; 'conv' runs two 32->32 and two 64->64 convolutions")
@@ -580,7 +581,9 @@ def conv_bench(reps: int = 20):
         y = torch.empty(*vol, cout, dtype=torch.bfloat16, device="cuda")
         flops = 2.0 * vox * 27 * cin * cout
         row = {}
-        for impl in ("tcgen05", "mma"):
+        for impl in ("tcgen05", "rows", "mma"):
+            if impl == "rows" and cout > 16:
+                continue   # the persistent form is taken up to 16 output channels only
             os.environ["DYNOT_CONV"] = impl
             for _ in range(3):
                 nn.conv3d(vol, nn.whole(x), w, b, nn.whole(y), relu=True)
@@ -692,7 +695,7 @@ def profile_case(which: str):
         return
     vol = (4, 32, 128, 128)
     g = torch.Generator().manual_seed(0)
-    for cin, cout in ((32, 32), (64, 64)):
+    for cin, cout in ((16, 16), (32, 32), (64, 64)):
         x = torch.randn(*vol, cin, generator=g).to(torch.bfloat16).cuda()
         w = (0.1 * torch.randn(cout, 27, cin, generator=g)).to(torch.bfloat16).cuda()
         b = torch.zeros(cout, device="cuda")

@@ -727,7 +727,11 @@ static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const 
     CUtensorMap tmR, tmW;
     const cuuint64_t dim[5] = {(cuuint64_t)xs, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)T, (cuuint64_t)N};
     const cuuint64_t str[4] = {2ull * xs, 2ull * xs * X, 2ull * xs * X * Y, 2ull * xs * X * Y * T};
-    const int rb = Cout <= 32 ? 8 : tc::kRB;
+    // Cout <= 16: the persistent form (8 rows per tile), unless DYNOT_CONV=rows asks for the one-tile-per-CTA
+    // form (with 32 output channels the persistent form, 4 rows per tile to fit two double accumulators in
+    // tensor memory, measured slower than 8-row blocks)
+    const bool persist = Cout <= 16 && !(sel && std::strcmp(sel, "rows") == 0);
+    const int rb = persist ? 8 : (Cout <= 32 ? 8 : tc::kRB);
     const cuuint32_t box[5] = {8, tc::kHaloRows, (cuuint32_t)(rb + 2), 1, 1};
     const cuuint32_t one[5] = {1, 1, 1, 1, 1};
     const cuuint64_t wdim[3] = {(cuuint64_t)Cin, 27, (cuuint64_t)Cout};
@@ -740,6 +744,24 @@ static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const 
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
+    if (persist) {
+      const size_t smem = rb == 8 ? tc::rows_p_smem_bytes<8>(Cout) : tc::rows_p_smem_bytes<4>(Cout);
+      auto kern = rb == 8 ? tc::k_conv3d_tc_rows_p<8> : tc::k_conv3d_tc_rows_p<4>;
+      int dev = 0, nsm = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        const long long ntiles = (long long)g.nxb * ((Y + rb - 1) / rb) * N * T;
+        if (ntiles >= (1LL << 31)) return false;
+        const int grid = (int)std::min<long long>(ntiles, 2LL * nsm);   // two CTAs per SM (tensor memory, shared memory)
+        kern<<<grid, 192, smem, st>>>(g, Cin, Cout, xo, (int)ntiles, bias, y, ys, yo, relu, out_f32, tmR, tmW);
+        e = cudaGetLastError();
+      }
+      *status = e == cudaSuccess ? OT_OK : seterr(OT_ECUDA, "conv3d (tcgen05 persistent rows): %s", cudaGetErrorString(e));
+      return true;
+    }
     const size_t smem = rb == 8 ? tc::rows_smem_bytes<8>(Cout) : tc::rows_smem_bytes<tc::kRB>(Cout);
     auto kern = rb == 8 ? tc::k_conv3d_tc_rows<8> : tc::k_conv3d_tc_rows<tc::kRB>;
     cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -407,5 +407,192 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_rows(Geom v, int Cin, int Cou
   if (!ok) atomicExch(&g_tc_err, 1);
 }
 
+// Persistent form of the row blocks for narrow outputs (the host takes it for Cout <= 16).  With 16 output
+// channels a CTA of the row form above runs only 3 pipeline stages, so its tensor-memory allocation, pipeline
+// fill and epilogue dominate.  Here 2 CTAs per SM stay resident and walk the tiles (RB output rows of 128 voxels) with a stride
+// of the grid: warp 0 issues the bulk tensor copies and warp 1 the MMAs, both continuously across tiles through
+// the two-stage ring, and warps 2-5 run the epilogue of a tile from one of two accumulators in tensor memory
+// while the MMAs of the next tile fill the other.  Barriers: full / empty per stage (copies landed / MMAs done
+// reading), and per accumulator acc_full (its last MMA done, by tcgen05.commit) and acc_empty (its four epilogue
+// warps done reading).  Every wait has a time limit; a wait that runs out marks the thread's results as NaN,
+// stops its waits and sets g_tc_err.
+constexpr int kPStages = 2;
+template <int RB>
+inline size_t rows_p_smem_bytes(int cout) { return (size_t)kPStages * rows_stage_bytes<RB>(cout) + 128 + 1024; }
+
+template <int RB>
+__global__ void __launch_bounds__(192) k_conv3d_tc_rows_p(Geom v, int Cin, int Cout, int xo, int ntiles,
+                                                          const float* __restrict__ bias, void* __restrict__ y,
+                                                          int ys, int yo, int relu, int out_f32,
+                                                          const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmW) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  using F = RowsForm<RB>;
+  const uint32_t sb = rows_stage_bytes<RB>(Cout), bb = b_bytes(Cout);
+  const uint32_t base = saddr(sm);
+  const uint32_t bars = base + kPStages * sb;
+  auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return bars + 8u * (uint32_t)(kPStages + s); };
+  auto acc_full = [&](int a) { return bars + 8u * (uint32_t)(2 * kPStages + a); };
+  auto acc_empty = [&](int a) { return bars + 8u * (uint32_t)(2 * kPStages + 2 + a); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kPStages * sb + 8 * (2 * kPStages + 4));
+  const int cs = rows_col_stride(Cout);
+  const uint32_t acols = (uint32_t)(RB * cs);   // columns of one accumulator
+  const int ncols = tmem_cols(2 * RB * cs);
+  const int chunks = Cin / 16, nk = 3 * chunks;
+  const int nyb = (v.Y + RB - 1) / RB;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPStages; ++s) {
+      bar_init(full(s), 1);
+      bar_init(empty(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      bar_init(acc_full(a), 1);
+      bar_init(acc_empty(a), 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  auto tile_pos = [&](int tile, int& x0, int& y0, int& t, int& n) {
+    x0 = (tile % v.nxb) * 128;
+    const int rest = tile / v.nxb;
+    y0 = (rest % nyb) * RB;
+    const int nt = rest / nyb;
+    t = nt % v.T;
+    n = nt / v.T;
+  };
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;   // k-steps issued so far (the ring position)
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int x0, y0, t, n;
+        tile_pos(tile, x0, y0, t, n);
+        for (int i = 0; i < nk; ++i, ++g) {
+          const int s = g % kPStages;
+          if (g >= kPStages && ok) ok = bar_wait(empty(s), ((g / kPStages) & 1) ^ 1);
+          const int dt = i / chunks - 1, cc = i % chunks;
+          bar_expect_tx(full(s), 2u * F::in * kHaloRows * 16u + 9u * 32u * (uint32_t)Cout);
+          for (int h = 0; h < 2; ++h)
+            tma_5d(base + s * sb + h * F::plane, &tmX, xo + 16 * cc + 8 * h, x0 - 1, y0 - 1, t + dt, n, full(s));
+          for (int q = 0; q < 9; ++q)
+            tma_3d(base + s * sb + F::a_bytes + q * bb, &tmW, 16 * cc, 9 * (dt + 1) + q, 0, full(s));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kM, Cout);
+      int g = 0, j = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+        const int ab = j & 1;
+        if (j >= 2 && ok) ok = bar_wait(acc_empty(ab), ((j >> 1) & 1) ^ 1);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)ab * acols;
+        for (int i = 0; i < nk; ++i, ++g) {
+          const int s = g % kPStages;
+          if (ok) ok = bar_wait(full(s), (g / kPStages) & 1);
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint64_t ad0 = desc_k_plain(base + s * sb, F::plane);
+          const uint64_t bd0 = desc_k32(base + s * sb + F::a_bytes);
+          for (int r = 0; r < RB; ++r)
+            for (int q = 0; q < 9; ++q) {
+              const int arow = r + q / 3, ax = q % 3;
+              const uint64_t ad = ad0 + (uint64_t)(arow * (int)kHaloRows + ax);
+              const uint64_t bd = bd0 + (uint64_t)(q * (bb >> 4));
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc + (uint32_t)(r * cs)),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(i > 0 || q > 0 ? 1 : 0)
+                  : "memory");
+            }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(s))
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(acc_full(ab))
+                     : "memory");
+      }
+    }
+  } else {
+    // epilogue: warp w reads the lanes 32 (w % 4) .. 32 (w % 4) + 31 of the accumulator
+    const int quad = warp & 3;
+    const float nanv = __int_as_float(0x7fc00000);
+    int j = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+      const int ab = j & 1;
+      int x0, y0, t, n;
+      tile_pos(tile, x0, y0, t, n);
+      if (ok) ok = bar_wait(acc_full(ab), (j >> 1) & 1);
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int xx = x0 + 32 * quad + lane;
+      for (int r = 0; r < RB; ++r) {
+        const int yy = y0 + r;
+        const bool store = xx < v.X && yy < v.Y;
+        const long long vox = (((long long)n * v.T + t) * v.Y + yy) * v.X + xx;
+        for (int c0 = 0; c0 < Cout; c0 += 16) {
+          uint32_t rr[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];\n"
+              : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+                "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+                "=r"(rr[15])
+              : "r"(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)ab * acols + (uint32_t)(r * cs + c0)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          if (!store) continue;
+          float u[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            u[q] = __uint_as_float(rr[q]) + (bias ? bias[c0 + q] : 0.f);
+            if (relu) u[q] = fmaxf(u[q], 0.f);
+            if (!ok) u[q] = nanv;
+          }
+          const long long o = vox * ys + yo + c0;
+          if (out_f32) {
+            float4* yp = reinterpret_cast<float4*>((float*)y + o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) yp[q] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
+          } else {
+            uint4* yp = reinterpret_cast<uint4*>((__nv_bfloat16*)y + o);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              uint32_t pk[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat16 lo = __float2bfloat16(u[8 * q + 2 * e]), hi = __float2bfloat16(u[8 * q + 2 * e + 1]);
+                pk[e] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+              }
+              yp[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+          }
+        }
+      }
+      // this warp's lanes of accumulator ab are read: hand it back to the MMA warp
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acc_empty(ab)) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+  if (!ok) atomicExch(&g_tc_err, 1);
+}
+
 }  // namespace tc
 }  // namespace dynot

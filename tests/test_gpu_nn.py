@@ -85,6 +85,30 @@ def test_conv3d_tcgen05_tiles(K, cin, cout, vol, out_f32, monkeypatch):
         outs.append(got)
 
 
+@pytest.mark.parametrize("cin,cout,vol", [(16, 16, (4, 32, 40, 128)), (48, 16, (2, 32, 75, 128)),
+                                          (16, 16, (2, 32, 45, 256))])
+def test_conv3d_persistent_rows_equal_row_blocks(K, cin, cout, vol, monkeypatch):
+    """Up to 16 output channels on rows of 128 voxels the convolution runs persistent CTAs (two per SM) that
+    walk the tiles with a two-stage copy ring and two accumulators in tensor memory, so that a tile's epilogue
+    overlaps the next tile's MMAs.  Its MMAs are those of the one-tile-per-CTA row blocks (DYNOT_CONV=rows) in
+    the same order: the outputs are equal bit for bit.  The volumes have 640 to 768 tiles, so every CTA
+    reuses both accumulators several times, with a partial last row block."""
+    import torch
+    x = _bf(vol + (cin,), 31).cuda()
+    w = _bf((cout, 27, cin), 32, 0.2).cuda()
+    b = torch.randn(cout, generator=torch.Generator().manual_seed(33)).cuda()
+    outs = []
+    for kind in ("tcgen05", "rows"):
+        monkeypatch.setenv("DYNOT_CONV", kind)
+        y = torch.full(vol + (cout,), float("nan"), dtype=torch.bfloat16, device="cuda")
+        K.conv3d(vol, K.whole(x), w, b, K.whole(y), relu=True)
+        torch.cuda.synchronize()
+        K.check()
+        outs.append(y)
+    assert not torch.isnan(outs[0].float()).any()
+    assert torch.equal(outs[0], outs[1])
+
+
 def test_conv3d_slices_relu_bf16(K):
     """Input and output are channel slices of wider buffers; other channels stay untouched."""
     import torch
