@@ -74,9 +74,10 @@ def parse():
                     help="3x3x3 convolution layers of the warm-start network at 128x128x32 (batch 4): tcgen05 "
                          "(persistent up to 16 output channels; 'rows': one tile per CTA) against the mma.sync "
                          "kernels, TFLOP/s against the measured bf16 peak")
-    ap.add_argument("--profile-case", choices=["rgb", "conv"], default=None,
+    ap.add_argument("--profile-case", choices=["rgb", "conv", "hue"], default=None,
                     help="small fixed cases for ncu captures: 'rgb' runs a 300-iteration solve of the 256x256x3x32 "
-                         "pair and two profiled iterations; 'conv' runs two 32->32 and two 64->64 convolutions")
+                         "pair and two profiled iterations; 'conv' runs two 16->16, two 32->32 and two 64->64 "
+                         "convolutions; 'hue' runs 20 iterations of a plan of 64 hue pairs (360 bins, P = 64)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the kernel profile, time-to-tolerance and end-to-end legs (for profiler runs)")
     return ap.parse_args()
@@ -692,6 +693,14 @@ def profile_case(which: str):
         plan.solve(d0, d1, 300, check_every=300)
         torch.cuda.synchronize()
         print(json.dumps(plan.profile(2)), flush=True)
+        return
+    if which == "hue":
+        a = np.stack([synth.hue_pair(360, s)[0] for s in range(64)])
+        b = np.stack([synth.hue_pair(360, s)[1] for s in range(64)])
+        plan = ot.Plan(ot.hue_grid(360, 64), batch=64)
+        st = plan.solve(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), 20, check_every=20)
+        torch.cuda.synchronize()
+        print(json.dumps({"hue_iterations": st.iterations}), flush=True)
         return
     vol = (4, 32, 128, 128)
     g = torch.Generator().manual_seed(0)
