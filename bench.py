@@ -72,8 +72,8 @@ def parse():
                     help="section 5's hue image morph on a synthetic 512x512 flower pair (360 bins, 16 steps)")
     ap.add_argument("--conv", action="store_true",
                     help="3x3x3 convolution layers of the warm-start network at 128x128x32 (batch 4): tcgen05 "
-                         "(persistent up to 16 output channels; 'rows': one tile per CTA) against the mma.sync "
-                         "kernels, TFLOP/s against the measured bf16 peak")
+                         "(16 and 32 output channels: stacked dy taps; 'persist': one MMA per tap; 'rows': one tile "
+                         "per CTA) against the mma.sync kernels, TFLOP/s against the measured bf16 peak")
     ap.add_argument("--profile-case", choices=["rgb", "conv", "hue"], default=None,
                     help="small fixed cases for ncu captures: 'rgb' runs a 300-iteration solve of the 256x256x3x32 "
                          "pair and two profiled iterations; 'conv' runs two 16->16, two 32->32 and two 64->64 "
@@ -582,9 +582,9 @@ def conv_bench(reps: int = 20):
         y = torch.empty(*vol, cout, dtype=torch.bfloat16, device="cuda")
         flops = 2.0 * vox * 27 * cin * cout
         row = {}
-        for impl in ("tcgen05", "rows", "mma"):
-            if impl == "rows" and cout > 16:
-                continue   # the persistent form is taken up to 16 output channels only
+        for impl in ("tcgen05", "persist", "rows", "mma"):
+            if (impl == "rows" and cout > 32) or (impl == "persist" and cout > 16):
+                continue   # the stacked and persistent forms exist for narrow outputs only
             os.environ["DYNOT_CONV"] = impl
             for _ in range(3):
                 nn.conv3d(vol, nn.whole(x), w, b, nn.whole(y), relu=True)

@@ -727,11 +727,12 @@ static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const 
     CUtensorMap tmR, tmW;
     const cuuint64_t dim[5] = {(cuuint64_t)xs, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)T, (cuuint64_t)N};
     const cuuint64_t str[4] = {2ull * xs, 2ull * xs * X, 2ull * xs * X * Y, 2ull * xs * X * Y * T};
-    // Cout <= 16: the persistent form (8 rows per tile), unless DYNOT_CONV=rows asks for the one-tile-per-CTA
-    // form (with 32 output channels the persistent form, 4 rows per tile to fit two double accumulators in
-    // tensor memory, measured slower than 8-row blocks)
-    const bool persist = Cout <= 16 && !(sel && std::strcmp(sel, "rows") == 0);
-    const int rb = persist ? 8 : (Cout <= 32 ? 8 : tc::kRB);
+    const bool one_tile = sel && std::strcmp(sel, "rows") == 0, unstacked = sel && std::strcmp(sel, "persist") == 0;
+    // Cout 16 and 32: stacked y taps (N = 3 Cout), persistent, 8 and 4 rows per tile (DYNOT_CONV=persist keeps the
+    // persistent form with one MMA per tap, DYNOT_CONV=rows one tile per CTA)
+    const bool stacked = (Cout == 16 || Cout == 32) && !one_tile && !unstacked;
+    const bool persist = Cout <= 16 && !one_tile && !stacked;
+    const int rb = stacked ? (Cout == 16 ? 8 : 4) : persist ? 8 : (Cout <= 32 ? 8 : tc::kRB);
     const cuuint32_t box[5] = {8, tc::kHaloRows, (cuuint32_t)(rb + 2), 1, 1};
     const cuuint32_t one[5] = {1, 1, 1, 1, 1};
     const cuuint64_t wdim[3] = {(cuuint64_t)Cin, 27, (cuuint64_t)Cout};
@@ -744,6 +745,24 @@ static bool conv3d_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const 
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
+    if (stacked) {
+      const size_t smem = rb == 8 ? tc::rows_s_smem_bytes<8>(Cout) : tc::rows_s_smem_bytes<4>(Cout);
+      auto kern = rb == 8 ? tc::k_conv3d_tc_rows_s<8> : tc::k_conv3d_tc_rows_s<4>;
+      int dev = 0, nsm = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        const long long ntiles = (long long)g.nxb * ((Y + rb - 1) / rb) * N * T;
+        if (ntiles >= (1LL << 31)) return false;
+        const int grid = (int)std::min<long long>(ntiles, nsm);   // one CTA per SM (all 512 tensor-memory columns)
+        kern<<<grid, 192, smem, st>>>(g, Cin, Cout, xo, (int)ntiles, bias, y, ys, yo, relu, out_f32, tmR, tmW);
+        e = cudaGetLastError();
+      }
+      *status = e == cudaSuccess ? OT_OK : seterr(OT_ECUDA, "conv3d (tcgen05 stacked rows): %s", cudaGetErrorString(e));
+      return true;
+    }
     if (persist) {
       const size_t smem = rb == 8 ? tc::rows_p_smem_bytes<8>(Cout) : tc::rows_p_smem_bytes<4>(Cout);
       auto kern = rb == 8 ? tc::k_conv3d_tc_rows_p<8> : tc::k_conv3d_tc_rows_p<4>;

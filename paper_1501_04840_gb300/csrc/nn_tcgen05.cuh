@@ -594,5 +594,210 @@ __global__ void __launch_bounds__(192) k_conv3d_tc_rows_p(Geom v, int Cin, int C
   if (!ok) atomicExch(&g_tc_err, 1);
 }
 
+// Stacked y taps (persistent, narrow outputs: Cout = 16 with RB = 8 rows per tile, Cout = 32 with RB = 4).
+// An input row a of the stage feeds the output rows a, a - 1, a - 2 through its taps dy = -1, 0, 1, so one MMA per
+// (input row, dx) with N = 3 Cout -- the weights of the three dy taps of that dx side by side -- does the work of
+// three MMAs of N = Cout and reads the 128 x 16 input block once instead of three times.  The accumulator holds
+// the rows r = -2 .. RB + 1 at columns (RB + 1 - r) Cout, decreasing with r, so that the three Cout-column
+// segments of the MMA of input row a land on rows a, a - 1, a - 2 (rows outside 0 .. RB - 1 collect terms that
+// are never read).  In the first stage of a tile the dx = 0 taps go out as three MMAs of N = Cout each, in the
+// order that makes each row's first write the one that clears it (row a by its own input row, k = 0).  Weight
+// slices are stored dx-major (slot 3 (dx + 1) + dy + 1), Cout rows of 32 bytes each, so the three dy slices of a
+// dx are one operand of 3 Cout rows.  One CTA per SM (two accumulators of (RB + 4) Cout columns fill the 512
+// tensor-memory columns), four pipeline stages; the warp roles and barriers are those of k_conv3d_tc_rows_p.
+constexpr int kSStages = 4;
+template <int RB>
+__host__ __device__ constexpr uint32_t rows_s_stage_bytes(int cout) {
+  return (RowsForm<RB>::a_bytes + 9u * 32u * (uint32_t)cout + 1023u) & ~1023u;
+}
+template <int RB>
+inline size_t rows_s_smem_bytes(int cout) { return (size_t)kSStages * rows_s_stage_bytes<RB>(cout) + 128 + 1024; }
+
+template <int RB>
+__global__ void __launch_bounds__(192) k_conv3d_tc_rows_s(Geom v, int Cin, int Cout, int xo, int ntiles,
+                                                          const float* __restrict__ bias, void* __restrict__ y,
+                                                          int ys, int yo, int relu, int out_f32,
+                                                          const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmW) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  using F = RowsForm<RB>;
+  const uint32_t sb = rows_s_stage_bytes<RB>(Cout), bb = 32u * (uint32_t)Cout;
+  const uint32_t base = saddr(sm);
+  const uint32_t bars = base + kSStages * sb;
+  auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return bars + 8u * (uint32_t)(kSStages + s); };
+  auto acc_full = [&](int a) { return bars + 8u * (uint32_t)(2 * kSStages + a); };
+  auto acc_empty = [&](int a) { return bars + 8u * (uint32_t)(2 * kSStages + 2 + a); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSStages * sb + 8 * (2 * kSStages + 4));
+  const uint32_t acols = (uint32_t)((RB + 4) * Cout);   // columns of one accumulator
+  const int ncols = 512;
+  const int chunks = Cin / 16, nk = 3 * chunks;
+  const int nyb = (v.Y + RB - 1) / RB;
+  auto col = [&](int r) { return (uint32_t)((RB + 1 - r) * Cout); };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSStages; ++s) {
+      bar_init(full(s), 1);
+      bar_init(empty(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      bar_init(acc_full(a), 1);
+      bar_init(acc_empty(a), 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  auto tile_pos = [&](int tile, int& x0, int& y0, int& t, int& n) {
+    x0 = (tile % v.nxb) * 128;
+    const int rest = tile / v.nxb;
+    y0 = (rest % nyb) * RB;
+    const int nt = rest / nyb;
+    t = nt % v.T;
+    n = nt / v.T;
+  };
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int x0, y0, t, n;
+        tile_pos(tile, x0, y0, t, n);
+        for (int i = 0; i < nk; ++i, ++g) {
+          const int s = g % kSStages;
+          if (g >= kSStages && ok) ok = bar_wait(empty(s), ((g / kSStages) & 1) ^ 1);
+          const int dt = i / chunks - 1, cc = i % chunks;
+          bar_expect_tx(full(s), 2u * F::in * kHaloRows * 16u + 9u * 32u * (uint32_t)Cout);
+          for (int h = 0; h < 2; ++h)
+            tma_5d(base + s * sb + h * F::plane, &tmX, xo + 16 * cc + 8 * h, x0 - 1, y0 - 1, t + dt, n, full(s));
+          // weight slot 3 (dx + 1) + (dy + 1) takes tap 9 (dt + 1) + 3 (dy + 1) + (dx + 1)
+          for (int dxi = 0; dxi < 3; ++dxi)
+            for (int k = 0; k < 3; ++k)
+              tma_3d(base + s * sb + F::a_bytes + (uint32_t)(3 * dxi + k) * bb, &tmW, 16 * cc, 9 * (dt + 1) + 3 * k + dxi,
+                     0, full(s));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id3 = idesc_bf16(kM, 3 * Cout), id1 = idesc_bf16(kM, Cout);
+      int g = 0, j = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+        const int ab = j & 1;
+        if (j >= 2 && ok) ok = bar_wait(acc_empty(ab), ((j >> 1) & 1) ^ 1);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)ab * acols;
+        for (int i = 0; i < nk; ++i, ++g) {
+          const int s = g % kSStages;
+          if (ok) ok = bar_wait(full(s), (g / kSStages) & 1);
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint64_t ad0 = desc_k_plain(base + s * sb, F::plane);
+          const uint64_t bd0 = desc_k32(base + s * sb + F::a_bytes);
+          for (int dxi = 0; dxi < 3; ++dxi)
+            for (int a = 0; a < RB + 2; ++a) {
+              const uint64_t ad = ad0 + (uint64_t)(a * (int)kHaloRows + dxi);
+              if (i == 0 && dxi == 0) {
+                // first writes of the tile: one MMA per dy tap; k = 0 (row a) clears its row
+                for (int k = 0; k < 3; ++k) {
+                  const uint64_t bd = bd0 + (uint64_t)(k * (bb >> 4));
+                  asm volatile(
+                      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc + col(a - k)),
+                      "l"(ad), "l"(bd), "r"(id1), "r"(k > 0 ? 1 : 0)
+                      : "memory");
+                }
+              } else {
+                const uint64_t bd = bd0 + (uint64_t)(3 * dxi * (bb >> 4));
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc + col(a)),
+                    "l"(ad), "l"(bd), "r"(id3), "r"(1)
+                    : "memory");
+              }
+            }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(s))
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(acc_full(ab))
+                     : "memory");
+      }
+    }
+  } else {
+    const int quad = warp & 3;
+    const float nanv = __int_as_float(0x7fc00000);
+    int j = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+      const int ab = j & 1;
+      int x0, y0, t, n;
+      tile_pos(tile, x0, y0, t, n);
+      if (ok) ok = bar_wait(acc_full(ab), (j >> 1) & 1);
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int xx = x0 + 32 * quad + lane;
+      for (int r = 0; r < RB; ++r) {
+        const int yy = y0 + r;
+        const bool store = xx < v.X && yy < v.Y;
+        const long long vox = (((long long)n * v.T + t) * v.Y + yy) * v.X + xx;
+        for (int c0 = 0; c0 < Cout; c0 += 16) {
+          uint32_t rr[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];\n"
+              : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+                "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+                "=r"(rr[15])
+              : "r"(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)ab * acols + col(r) + (uint32_t)c0));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          if (!store) continue;
+          float u[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            u[q] = __uint_as_float(rr[q]) + (bias ? bias[c0 + q] : 0.f);
+            if (relu) u[q] = fmaxf(u[q], 0.f);
+            if (!ok) u[q] = nanv;
+          }
+          const long long o = vox * ys + yo + c0;
+          if (out_f32) {
+            float4* yp = reinterpret_cast<float4*>((float*)y + o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) yp[q] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
+          } else {
+            uint4* yp = reinterpret_cast<uint4*>((__nv_bfloat16*)y + o);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              uint32_t pk[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat16 lo = __float2bfloat16(u[8 * q + 2 * e]), hi = __float2bfloat16(u[8 * q + 2 * e + 1]);
+                pk[e] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+              }
+              yp[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acc_empty(ab)) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+  if (!ok) atomicExch(&g_tc_err, 1);
+}
+
 }  // namespace tc
 }  // namespace dynot

@@ -58,7 +58,7 @@ def test_conv3d_forward_fp32(K, cin, cout, vol):
 @pytest.mark.parametrize("cin,cout,vol,out_f32", [(16, 16, (1, 3, 8, 16), True), (32, 64, (2, 2, 5, 32), True),
                                                   (64, 48, (1, 2, 3, 128), False), (16, 32, (1, 4, 9, 64), False),
                                                   (48, 16, (2, 3, 4, 8), True), (16, 16, (2, 2, 3, 256), True),
-                                                  (32, 64, (1, 2, 9, 128), False)])
+                                                  (32, 64, (1, 2, 9, 128), False), (32, 32, (1, 2, 5, 128), True)])
 def test_conv3d_tcgen05_tiles(K, cin, cout, vol, out_f32, monkeypatch):
     """Shapes the tcgen05 convolution takes (cout % 16 == 0, X dividing 128 or a multiple of it): tiles of
     128 voxels over one or several rows, partial tiles at the y edge, rows of 128 voxels (X = 128, 256) in
@@ -88,7 +88,7 @@ def test_conv3d_tcgen05_tiles(K, cin, cout, vol, out_f32, monkeypatch):
 @pytest.mark.parametrize("cin,cout,vol", [(16, 16, (4, 32, 40, 128)), (48, 16, (2, 32, 75, 128)),
                                           (16, 16, (2, 32, 45, 256))])
 def test_conv3d_persistent_rows_equal_row_blocks(K, cin, cout, vol, monkeypatch):
-    """Up to 16 output channels on rows of 128 voxels the convolution runs persistent CTAs (two per SM) that
+    """The persistent form with one MMA per tap (DYNOT_CONV=persist) runs CTAs (two per SM) that
     walk the tiles with a two-stage copy ring and two accumulators in tensor memory, so that a tile's epilogue
     overlaps the next tile's MMAs.  Its MMAs are those of the one-tile-per-CTA row blocks (DYNOT_CONV=rows) in
     the same order: the outputs are equal bit for bit.  The volumes have 640 to 768 tiles, so every CTA
@@ -98,7 +98,7 @@ def test_conv3d_persistent_rows_equal_row_blocks(K, cin, cout, vol, monkeypatch)
     w = _bf((cout, 27, cin), 32, 0.2).cuda()
     b = torch.randn(cout, generator=torch.Generator().manual_seed(33)).cuda()
     outs = []
-    for kind in ("tcgen05", "rows"):
+    for kind in ("persist", "rows"):
         monkeypatch.setenv("DYNOT_CONV", kind)
         y = torch.full(vol + (cout,), float("nan"), dtype=torch.bfloat16, device="cuda")
         K.conv3d(vol, K.whole(x), w, b, K.whole(y), relu=True)
@@ -107,6 +107,34 @@ def test_conv3d_persistent_rows_equal_row_blocks(K, cin, cout, vol, monkeypatch)
         outs.append(y)
     assert not torch.isnan(outs[0].float()).any()
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("cin,cout,vol", [(16, 16, (4, 32, 40, 128)), (48, 16, (2, 32, 75, 128)),
+                                          (16, 32, (2, 32, 42, 128)), (32, 32, (1, 32, 37, 256))])
+def test_conv3d_stacked_taps_match_row_blocks(K, cin, cout, vol, monkeypatch):
+    """With 16 and 32 output channels on rows of 128 voxels the convolution issues one MMA per input row and dx
+    for the three dy taps together (N = 3 Cout), with persistent CTAs (one per SM) walking 640 to 704 tiles, so that every CTA
+    reuses both accumulators; the first stage of a tile clears each row by its own tap.  fp32 outputs against
+    the one-tile-per-CTA row blocks (DYNOT_CONV=rows), which sum the same products in another order: within
+    2e-5 of the sum of absolute terms (each is within 1e-5 of the exact convolution)."""
+    import torch
+    x = _bf(vol + (cin,), 41).cuda()
+    w = _bf((cout, 27, cin), 42, 0.2).cuda()
+    b = torch.randn(cout, generator=torch.Generator().manual_seed(43)).cuda()
+    outs = []
+    for kind in ("tcgen05", "rows"):
+        monkeypatch.setenv("DYNOT_CONV", kind)
+        y = torch.full(vol + (cout,), float("nan"), dtype=torch.float32, device="cuda")
+        K.conv3d(vol, K.whole(x), w, b, K.whole(y), relu=False, out_f32=True)
+        torch.cuda.synchronize()
+        K.check()
+        outs.append(y)
+    monkeypatch.setenv("DYNOT_CONV", "rows")
+    bound = torch.empty(vol + (cout,), dtype=torch.float32, device="cuda")
+    K.conv3d(vol, K.whole(x.abs()), w.abs(), b.abs(), K.whole(bound), relu=False, out_f32=True)
+    torch.cuda.synchronize()
+    assert not torch.isnan(outs[0]).any()
+    assert bool(((outs[0] - outs[1]).abs() <= 2e-5 * bound + 1e-30).all())
 
 
 def test_conv3d_slices_relu_bf16(K):
