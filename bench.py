@@ -572,7 +572,7 @@ def conv_bench(reps: int = 20):
         peak, kind = 1900.0, "fallback"
     vol = (4, 32, 128, 128)
     vox = vol[0] * vol[1] * vol[2] * vol[3]
-    out = {"metric": "3x3x3 convolution forward, TFLOP/s", "unit": "TFLOP/s", "peak_bf16_tflops": peak,
+    out = {"metric": "3x3x3 convolution forward and weight gradient, TFLOP/s", "unit": "TFLOP/s", "peak_bf16_tflops": peak,
            "peak_kind": kind, "volume": list(vol), "layers": {}}
     g = torch.Generator().manual_seed(0)
     for cin, cout in ((16, 16), (32, 32), (48, 48), (64, 64)):
@@ -599,8 +599,54 @@ def conv_bench(reps: int = 20):
             ms = e0.elapsed_time(e1) / reps
             tf = flops / (ms / 1e3) / 1e12
             row[impl] = {"ms": ms, "tflops": tf, "frac": tf / peak}
+        # weight gradient of the same layer (dy = y), tcgen05 against mma.sync
+        dw = torch.zeros(cout * 27 * cin, dtype=torch.float32, device="cuda")
+        wg = {}
+        for impl in ("tcgen05", "mma"):
+            os.environ["DYNOT_CONV"] = impl
+            for _ in range(3):
+                nn.conv3d_wgrad(vol, nn.whole(x), nn.whole(y), dw, None)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                nn.conv3d_wgrad(vol, nn.whole(x), nn.whole(y), dw, None)
+            e1.record()
+            torch.cuda.synchronize()
+            nn.check()
+            ms = e0.elapsed_time(e1) / reps
+            tf = flops / (ms / 1e3) / 1e12
+            wg[impl] = {"ms": ms, "tflops": tf, "frac": tf / peak}
+        row["weight_gradient"] = wg
         os.environ.pop("DYNOT_CONV", None)
         out["layers"]["%d->%d" % (cin, cout)] = row
+    # weight gradients of the U-Net's layer shapes, level by level (batch 4, P = 32), tcgen05 against mma.sync
+    out["unet_weight_gradients"] = {}
+    for side, shapes in ((128, ((16, 16), (48, 16), (16, 32))), (64, ((16, 32), (32, 32), (80, 32))),
+                         (32, ((32, 48), (48, 48), (112, 48))), (16, ((48, 64), (64, 64)))):
+        lv = (4, 32, side, side)
+        lvox = 4 * 32 * side * side
+        for cin, cout in shapes:
+            x = torch.randn(*lv, cin, generator=g).to(torch.bfloat16).cuda()
+            dyt = torch.randn(*lv, cout, generator=g).to(torch.bfloat16).cuda()
+            dw = torch.zeros(cout * 27 * cin, dtype=torch.float32, device="cuda")
+            rec = {}
+            for impl in ("tcgen05", "mma"):
+                os.environ["DYNOT_CONV"] = impl
+                for _ in range(3):
+                    nn.conv3d_wgrad(lv, nn.whole(x), nn.whole(dyt), dw, None)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    nn.conv3d_wgrad(lv, nn.whole(x), nn.whole(dyt), dw, None)
+                e1.record()
+                torch.cuda.synchronize()
+                nn.check()
+                ms = e0.elapsed_time(e1) / reps
+                rec[impl] = {"ms": ms, "tflops": 2.0 * lvox * 27 * cin * cout / (ms / 1e3) / 1e12}
+            os.environ.pop("DYNOT_CONV", None)
+            out["unet_weight_gradients"]["%d: %d->%d" % (side, cin, cout)] = rec
     print(json.dumps(out), flush=True)
 
 

@@ -294,7 +294,10 @@ void ot_batch_destroy(ot_batch_t b);
  * ot_nn_check: waits for `stream` and returns OT_ETIMEOUT (once) if a bounded device wait of
  *   the tcgen05 convolution ran out since the last check (that launch wrote NaN), else OT_OK.
  * ot_nn_conv3d_wgrad: dw (fp32 [cout][27][cin]) += sum_v dy[v] x[v + tap]; db (fp32,
- *   may be NULL) += sum_v dy[v]; cin, cout % 16 == 0.  The data gradient is
+ *   may be NULL) += sum_v dy[v]; cin, cout % 16 == 0.  Tensor cores: tcgen05 (both operands
+ *   staged by bulk tensor copies, fp32 sums in tensor memory, per-CTA partials added in a fixed
+ *   order) where 32 <= cin <= 128, 32 <= cout <= 64, X is 16, 32, 64 or 128 and the slices
+ *   start on 16 bytes; mma.sync otherwise.  The data gradient is
  *   ot_nn_conv3d with ot_nn_rotate_weights(w) (wr[ci][tap][co] = w[co][26-tap][ci]).
  * ot_nn_relu_grad: g *= (y > 0).  ot_nn_pool / ot_nn_upsample: 2x2 average pooling
  *   and nearest upsampling over (y, x) (Yc, Xc = coarse sizes), forward or backward.

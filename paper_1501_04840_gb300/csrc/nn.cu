@@ -420,6 +420,18 @@ __global__ void k_wgrad_reduce(int Cin, int nblk, const float* __restrict__ part
   }
 }
 
+// dw[co][tap][ci] += sum over the chunks of the tcgen05 weight gradient's partials [chunk][tap][co][ci]
+__global__ void k_wgrad_reduce_tc(int Cin, int Cout, int nchunks, const float* __restrict__ part,
+                                  float* __restrict__ dw) {
+  const int tap = blockIdx.x, co = blockIdx.y;
+  for (int ci = threadIdx.x; ci < Cin; ci += blockDim.x) {
+    const float* p = part + ((size_t)tap * Cout + co) * Cin + ci;
+    float s = 0.f;
+    for (int k = 0; k < nchunks; ++k) s += p[(size_t)k * 27 * Cout * Cin];
+    dw[((size_t)co * 27 + tap) * Cin + ci] += s;
+  }
+}
+
 // db[c] += sum_v dy[v][c]
 __global__ void k_bias_grad(long long M, int C, const bf16* __restrict__ dy, int dys, int dyo, float* __restrict__ db) {
   const int c = blockIdx.y;
@@ -875,6 +887,79 @@ ot_status ot_nn_check(void* stream) {
   return OT_OK;
 }
 
+// The weight gradient on tcgen05 (rows of X = 16, 32, 64 or 128 voxels, Cin and Cout multiples of 16, Cout <= 64,
+// Cin <= 128: four stages of 210 KB at most):
+// per-CTA partial sums of 27 x Cout x Cin, reduced in a fixed order.  false: not this form (DYNOT_CONV=mma, or the
+// shapes and alignments do not allow it); then *status is untouched.
+static bool wgrad_tcgen05(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo, const void* dy,
+                          int dys, int dyo, float* dw, cudaStream_t st, ot_status* status) {
+  const char* sel = std::getenv("DYNOT_CONV");
+  if (sel && std::strcmp(sel, "mma") == 0) return false;
+  // with 16 input or output channels the M = 64 padding or the N = 16 operand leaves the tensor cores idle, and
+  // the mma.sync kernels are faster (bench.py --conv, U-Net shapes); DYNOT_CONV=tcgen05 takes this form anyway
+  const bool forced = sel && std::strcmp(sel, "tcgen05") == 0;
+  if (!forced && (Cin < 32 || Cout < 32)) return false;
+  if ((X != 16 && X != 32 && X != 64 && X != 128) || Cin % 16 || Cout % 16 || Cout > 64 || Cin > 128 || xs % 8 ||
+      xo % 8 || dys % 8 || dyo % 8 || ((uintptr_t)x & 15) || ((uintptr_t)dy & 15) || (long long)N * T * Y >= (1LL << 31))
+    return false;
+  const int R = 128 / X;   // rows of one stage
+  auto enc = nn_tensor_map_encoder();
+  if (!enc) return false;
+  CUtensorMap tmX, tmD;
+  const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+  {
+    const cuuint64_t dim[5] = {(cuuint64_t)xs, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)T, (cuuint64_t)N};
+    const cuuint64_t str[4] = {2ull * xs, 2ull * xs * X, 2ull * xs * X * Y, 2ull * xs * X * Y * T};
+    const cuuint32_t box[5] = {8, (cuuint32_t)(X + 2), (cuuint32_t)R, 1, 1};
+    if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dim, str, box, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  {
+    const cuuint64_t dim[5] = {(cuuint64_t)dys, (cuuint64_t)X, (cuuint64_t)Y, (cuuint64_t)T, (cuuint64_t)N};
+    const cuuint64_t str[4] = {2ull * dys, 2ull * dys * X, 2ull * dys * X * Y, 2ull * dys * X * Y * T};
+    const cuuint32_t box[5] = {8, (cuuint32_t)X, (cuuint32_t)R, 1, 1};
+    if (enc(&tmD, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(dy), dim, str, box, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = tc::wg_smem_bytes(Cin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)tc::k_conv3d_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (e != cudaSuccess) {
+    *status = seterr(OT_ECUDA, "conv3d_wgrad (tcgen05): %s", cudaGetErrorString(e));
+    return true;
+  }
+  // CTAs per SM that shared and tensor memory allow, nine (dt, dy) pairs, chunks of voxel rows to fill the SMs
+  const int per_sm = (2 * smem + 2048 <= 228 * 1024 && 3 * Cin <= 256) ? 2 : 1;
+  const int rows = N * T * ((Y + R - 1) / R);
+  int nchunks = std::max(1, std::min(rows, per_sm * nsm / 9));
+  const int rpc = (rows + nchunks - 1) / nchunks;
+  nchunks = (rows + rpc - 1) / rpc;   // every chunk holds at least one row
+  tc::Geom g{N, T, Y, X, X, R, 1};
+  float* part = nullptr;
+  const size_t bytes = sizeof(float) * (size_t)nchunks * 27 * Cout * Cin;
+  e = cudaMallocAsync((void**)&part, bytes, st);
+  if (e == cudaSuccess) {
+    tc::k_conv3d_tc_wgrad<<<dim3((unsigned)nchunks, 9), 128, smem, st>>>(g, Cin, Cout, xo, dyo, rows, rpc, part, tmX, tmD);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      k_wgrad_reduce_tc<<<dim3(27, (unsigned)Cout), 128, 0, st>>>(Cin, Cout, nchunks, part, dw);
+      e = cudaGetLastError();
+    }
+    const cudaError_t e2 = cudaFreeAsync(part, st);
+    if (e == cudaSuccess) e = e2;
+  }
+  *status = e == cudaSuccess ? OT_OK : seterr(OT_ECUDA, "conv3d_wgrad (tcgen05): %s", cudaGetErrorString(e));
+  return true;
+}
+
 ot_status ot_nn_conv3d_wgrad(int N, int T, int Y, int X, int Cin, int Cout, const void* x, int xs, int xo,
                              const void* dy, int dys, int dyo, float* dw, float* db, void* stream) {
   if (Cin % 16 || Cout % 16) return seterr(OT_EINVAL, "conv3d_wgrad: channel counts must be multiples of 16");
@@ -883,6 +968,17 @@ ot_status ot_nn_conv3d_wgrad(int N, int T, int Y, int X, int Cin, int Cout, cons
   const Vol v{N, T, Y, X};
   const long long M = (long long)N * T * Y * X;
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    ot_status s2 = OT_OK;
+    if (wgrad_tcgen05(N, T, Y, X, Cin, Cout, x, xs, xo, dy, dys, dyo, dw, st, &s2)) {
+      if (s2 != OT_OK) return s2;
+      if (db) {
+        k_bias_grad<<<dim3(64, Cout), 256, 0, st>>>(M, Cout, (const bf16*)dy, dys, dyo, db);
+        NN_LAUNCH_CHECK();
+      }
+      return OT_OK;
+    }
+  }
   if (xs % 8 == 0 && xo % 8 == 0 && dys % 8 == 0 && dyo % 8 == 0 && ((uintptr_t)x & 15) == 0 &&
       ((uintptr_t)dy & 15) == 0) {
     // shared-memory tiled form: per-block partials, then a fixed-order reduction into dw

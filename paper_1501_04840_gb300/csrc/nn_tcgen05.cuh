@@ -799,5 +799,146 @@ __global__ void __launch_bounds__(192) k_conv3d_tc_rows_s(Geom v, int Cin, int C
   if (!ok) atomicExch(&g_tc_err, 1);
 }
 
+// Weight gradient on the tensor cores: dw[co][tap][ci] = sum over voxels v of dy[v][co] x[v + tap][ci], for rows
+// of X voxels along x (X = 16, 32, 64 or 128).  Per tap this is a GEMM with M = output channels (padded to 64),
+// N = input channels and K = voxels, both operands MN-major (channels are the contiguous dimension of the
+// activations).  A pipeline stage holds R = 128 / X consecutive rows (y) of one (n, t): dy as 8-channel planes of
+// 128 voxels of 16 bytes (the planes past Cout stay zero), x as 8-channel planes of the R input rows of one
+// (dt, dy) shift with their x halo (X + 2 voxels each), which the three dx taps read through descriptors one voxel
+// apart.  A CTA takes one (dt, dy) pair and a chunk of row groups; per stage it issues 3 x 8 MMAs (M = 64,
+// N = Cin, K = 16 voxels of one row) into three accumulators (dx = -1, 0, 1) of Cin columns, and at the end
+// writes its 3 x Cout x Cin sums to `part`, which a second kernel adds in a fixed order.  The descriptors of MN-major operands without
+// swizzle carry the K-group stride (8 voxels, 128 bytes) in bits 16-29 and the 8-channel plane stride in bits
+// 32-45; an M = 64 accumulator keeps row r in lane 32 (r / 16) + r % 16.  Waits are time-limited (g_tc_err).
+constexpr int kWStages = 4;
+constexpr uint32_t kWPlaneA = 128 * 16, kWPlaneB = 2304;   // 128 voxels; R (X + 2) <= 144 voxels, of 16 bytes
+__host__ __device__ constexpr uint32_t wg_stage_bytes(int cin) {
+  return (8u * kWPlaneA + (uint32_t)(cin / 8) * kWPlaneB + 1023u) & ~1023u;
+}
+inline size_t wg_smem_bytes(int cin) { return (size_t)kWStages * wg_stage_bytes(cin) + 128 + 1024; }
+__device__ __forceinline__ uint64_t desc_mn_plain(uint32_t addr, uint32_t plane) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128u >> 4) << 16;                       // K groups of 8 voxels
+  d |= (uint64_t)((plane >> 4) & 0x3FFFu) << 32;          // 8-channel planes
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// rows: the N * T * ceil(Y / R) row groups (n, t, y0), chunked over blockIdx.x; blockIdx.y = 3 (dt + 1) + (dy + 1)
+__global__ void __launch_bounds__(128) k_conv3d_tc_wgrad(Geom v, int Cin, int Cout, int xo, int dyo, int rows,
+                                                         int rows_per_chunk, float* __restrict__ part,
+                                                         const __grid_constant__ CUtensorMap tmX,
+                                                         const __grid_constant__ CUtensorMap tmD) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t sb = wg_stage_bytes(Cin);
+  const uint32_t base = saddr(sm);
+  const uint32_t bars = base + kWStages * sb;
+  auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return bars + 8u * (uint32_t)(kWStages + s); };
+  const uint32_t done = bars + 8u * (2 * kWStages);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kWStages * sb + 8 * (2 * kWStages + 1));
+  const int ncols = tmem_cols(3 * Cin) >= 3 * Cin ? tmem_cols(3 * Cin) : 512;
+  const int dt = (int)blockIdx.y / 3 - 1, dy = (int)blockIdx.y % 3 - 1;
+  const int r0 = blockIdx.x * rows_per_chunk, r1 = min(rows, r0 + rows_per_chunk);
+  const int nrow = max(0, r1 - r0);
+  // the A planes past Cout are never copied: zero them in every stage
+  for (uint32_t i = threadIdx.x * 16u; i < (uint32_t)kWStages * sb; i += 128u * 16u) {
+    if ((i % sb) < 8u * kWPlaneA) *reinterpret_cast<uint4*>(sm + i) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWStages; ++s) {
+      bar_init(full(s), 1);
+      bar_init(empty(s), 1);
+    }
+    bar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  const int pa = Cout / 8, pb = Cin / 8;
+  const int X = v.X, R = 128 / X, nyg = (v.Y + R - 1) / R;
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < nrow; ++i) {
+      const int s = i % kWStages;
+      if (i >= kWStages && ok) ok = bar_wait(empty(s), ((i / kWStages) & 1) ^ 1);
+      const int row = r0 + i;
+      const int y = (row % nyg) * R, t = (row / nyg) % v.T, n = row / (nyg * v.T);
+      bar_expect_tx(full(s), (uint32_t)pa * kWPlaneA + (uint32_t)pb * (uint32_t)(R * (X + 2)) * 16u);
+      for (int h = 0; h < pa; ++h) tma_5d(base + s * sb + h * kWPlaneA, &tmD, dyo + 8 * h, 0, y, t, n, full(s));
+      for (int h = 0; h < pb; ++h)
+        tma_5d(base + s * sb + 8 * kWPlaneA + h * kWPlaneB, &tmX, xo + 8 * h, -1, y + dy, t + dt, n, full(s));
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(Cin >> 3) << 17) |
+                           ((uint32_t)(64 >> 4) << 24);
+    for (int i = 0; i < nrow; ++i) {
+      const int s = i % kWStages;
+      if (ok) ok = bar_wait(full(s), (i / kWStages) & 1);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint64_t ad0 = desc_mn_plain(base + s * sb, kWPlaneA);
+      const uint64_t bd0 = desc_mn_plain(base + s * sb + 8 * kWPlaneA, kWPlaneB);
+      for (int dxi = 0; dxi < 3; ++dxi)
+        for (int k0 = 0; k0 < 8; ++k0) {
+          // voxels 16 k0 .. 16 k0 + 15 of the stage: row r = 16 k0 / X, from voxel xk of it
+          const int r = (16 * k0) / X, xk = 16 * k0 - r * X;
+          const uint64_t ad = ad0 + (uint64_t)(16 * k0);                          // dy rows are contiguous
+          const uint64_t bd = bd0 + (uint64_t)(r * (X + 2) + xk + dxi);           // input row r, voxel x + dx + 1
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(dxi * Cin)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(i > 0 || k0 > 0 ? 1 : 0)
+              : "memory");
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(s))
+                   : "memory");
+    }
+    if (nrow > 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(done)
+                   : "memory");
+  }
+  __syncwarp();
+  if (nrow > 0 && ok) ok = bar_wait(done, 0);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  // output channel co = 16 warp + lane sits in lane 32 warp + lane (lanes 0-15 of each quarter)
+  const int co = 16 * warp + lane;
+  const float nanv = __int_as_float(0x7fc00000);
+  for (int dxi = 0; dxi < 3; ++dxi)
+    for (int c0 = 0; c0 < Cin; c0 += 16) {
+      uint32_t rr[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];\n"
+          : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+            "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+          : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(dxi * Cin + c0)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (lane >= 16 || co >= Cout) continue;
+      const int tap = 9 * (dt + 1) + 3 * (dy + 1) + dxi;
+      float* q = part + (((size_t)blockIdx.x * 27 + tap) * Cout + co) * Cin + c0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) q[j] = (nrow == 0) ? 0.f : (ok ? __uint_as_float(rr[j]) : nanv);
+    }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+  if (!ok) atomicExch(&g_tc_err, 1);
+}
+
 }  // namespace tc
 }  // namespace dynot

@@ -193,6 +193,33 @@ def test_conv3d_weight_gradient(K, cin, cout, vol):
     assert np.all(np.abs(db.cpu().double().numpy() - dbr) <= 1e-5 * 2 * np.abs(_np(dy)).sum(axis=(0, 1, 2, 3)))
 
 
+@pytest.mark.parametrize("cin,cout,vol", [(16, 16, (2, 3, 7, 128)), (112, 48, (1, 4, 5, 128)),
+                                          (48, 64, (1, 3, 6, 128)), (32, 32, (2, 2, 33, 128)),
+                                          (32, 32, (2, 3, 9, 64)), (48, 48, (1, 4, 7, 32)), (64, 64, (2, 2, 6, 16)),
+                                          (112, 48, (1, 3, 5, 32))])
+def test_conv3d_weight_gradient_tcgen05(K, cin, cout, vol, monkeypatch):
+    """Rows of 16 to 128 voxels take the tcgen05 weight gradient (dy as the M = 64 operand, the shifted input rows
+    as N = Cin, both MN-major; 128 / X rows per stage; three dx accumulators per (dt, dy) pair; partial sums per
+    chunk of row groups added in a fixed order): against the oracle, accumulated twice (+=), the input a channel
+    slice of a wider tensor, row groups ragged at the y edge, from one CTA per SM (Cin = 112: 336 tensor-memory
+    columns) to two; the mma.sync kernels (DYNOT_CONV=mma) agree."""
+    import torch
+    xb = _bf(vol + (cin + 16,), 51)
+    dy = _bf(vol + (cout,), 52)
+    x = _np(xb)[..., 16:]
+    ref = 2 * unet.conv3d_wgrad(x, _np(dy))
+    bound = 2 * unet.conv3d_wgrad(np.abs(x), np.abs(_np(dy)))
+    for kind in ("tcgen05", "mma"):
+        monkeypatch.setenv("DYNOT_CONV", kind)
+        dw = torch.zeros(cout * 27 * cin, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            K.conv3d_wgrad(vol, K.Slice(xb.cuda(), 16, cin), K.whole(dy.cuda()), dw, None)
+        torch.cuda.synchronize()
+        K.check()
+        got = dw.cpu().double().numpy().reshape(cout, 27, cin)
+        assert np.all(np.abs(got - ref) <= 1e-5 * bound + 1e-30), kind
+
+
 def test_pool_upsample_relu_add(K):
     import torch
     vc = (2, 3, 4, 5)                  # coarse volume; fine is (2, 3, 8, 10)
