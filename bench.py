@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--profile-case", choices=["rgb", "conv", "hue"], default=None,
                     help="small fixed cases for ncu captures: 'rgb' runs a 300-iteration solve of the 256x256x3x32 "
                          "pair and two profiled iterations; 'conv' runs two 16->16, two 32->32 and two 64->64 "
-                         "convolutions; 'hue' runs 20 iterations of a plan of 64 hue pairs (360 bins, P = 64)")
+                         "convolutions and two 64->64 weight gradients; 'hue' runs 20 iterations of a plan of 64 hue pairs (360 bins, P = 64)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the kernel profile, time-to-tolerance and end-to-end legs (for profiler runs)")
     return ap.parse_args()
@@ -759,6 +759,12 @@ def profile_case(which: str):
             nn.conv3d(vol, nn.whole(x), w, b, nn.whole(y), relu=True)
         torch.cuda.synchronize()
         nn.check()
+    # two weight gradients of the 64 -> 64 layer (dy = y)
+    dw = torch.zeros(64 * 27 * 64, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        nn.conv3d_wgrad(vol, nn.whole(x), nn.whole(y), dw, None)
+    torch.cuda.synchronize()
+    nn.check()
     print(json.dumps({"conv": "ok"}), flush=True)
 
 

@@ -59,6 +59,34 @@ __device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity) {
     else if ((i & 63) == 0 && now_ns() - start > kWaitNs) return false;
   }
 }
+// The same for a wait that spans a whole K loop: it runs out only after kWaitNs without progress, i.e. without a
+// change of *prog (a stage counter the MMA thread advances), so a long loop is not taken for a stuck one.
+__device__ __forceinline__ bool bar_wait_progress(uint32_t b, uint32_t parity, const volatile uint32_t* prog) {
+  unsigned long long start = 0;
+  uint32_t seen = 0;
+#pragma unroll 1
+  for (int i = 0;; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (i == 0) {
+      start = now_ns();
+      seen = *prog;
+    } else if ((i & 63) == 0) {
+      const uint32_t cur = *prog;
+      if (cur != seen) {
+        seen = cur;
+        start = now_ns();
+      } else if (now_ns() - start > kWaitNs) {
+        return false;
+      }
+    }
+  }
+}
 __device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* m, int c0, int c1, int c2, int c3, int c4,
                                        uint32_t b) {
   asm volatile(
@@ -809,7 +837,8 @@ __global__ void __launch_bounds__(192) k_conv3d_tc_rows_s(Geom v, int Cin, int C
 // N = Cin, K = 16 voxels of one row) into three accumulators (dx = -1, 0, 1) of Cin columns, and at the end
 // writes its 3 x Cout x Cin sums to `part`, which a second kernel adds in a fixed order.  The descriptors of MN-major operands without
 // swizzle carry the K-group stride (8 voxels, 128 bytes) in bits 16-29 and the 8-channel plane stride in bits
-// 32-45; an M = 64 accumulator keeps row r in lane 32 (r / 16) + r % 16.  Waits are time-limited (g_tc_err).
+// 32-45; an M = 64 accumulator keeps row r in lane 32 (r / 16) + r % 16.  Waits are time-limited (g_tc_err); the
+// wait for the end of the whole K loop runs out only after the MMA thread has made no progress for the limit.
 constexpr int kWStages = 4;
 constexpr uint32_t kWPlaneA = 128 * 16, kWPlaneB = 2304;   // 128 voxels; R (X + 2) <= 144 voxels, of 16 bytes
 __host__ __device__ constexpr uint32_t wg_stage_bytes(int cin) {
@@ -839,6 +868,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_wgrad(Geom v, int Cin, int Co
   auto empty = [&](int s) { return bars + 8u * (uint32_t)(kWStages + s); };
   const uint32_t done = bars + 8u * (2 * kWStages);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kWStages * sb + 8 * (2 * kWStages + 1));
+  volatile uint32_t* prog = reinterpret_cast<volatile uint32_t*>(sm + kWStages * sb + 8 * (2 * kWStages + 2));
   const int ncols = tmem_cols(3 * Cin) >= 3 * Cin ? tmem_cols(3 * Cin) : 512;
   const int dt = (int)blockIdx.y / 3 - 1, dy = (int)blockIdx.y % 3 - 1;
   const int r0 = blockIdx.x * rows_per_chunk, r1 = min(rows, r0 + rows_per_chunk);
@@ -854,6 +884,7 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_wgrad(Geom v, int Cin, int Co
       bar_init(empty(s), 1);
     }
     bar_init(done, 1);
+    *prog = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -903,13 +934,14 @@ __global__ void __launch_bounds__(128) k_conv3d_tc_wgrad(Geom v, int Cin, int Co
         }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(s))
                    : "memory");
+      *prog = (uint32_t)(i + 1);   // progress for the threads that wait for the whole loop
     }
     if (nrow > 0)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(done)
                    : "memory");
   }
   __syncwarp();
-  if (nrow > 0 && ok) ok = bar_wait(done, 0);
+  if (nrow > 0 && ok) ok = bar_wait_progress(done, 0, prog);
   __syncwarp();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   // output channel co = 16 warp + lane sits in lane 32 warp + lane (lanes 0-15 of each quarter)
