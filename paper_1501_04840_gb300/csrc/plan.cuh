@@ -911,7 +911,7 @@ struct Plan final : PlanBase {
         const TileLayout Lt{S, n1, n1 * n2, (long long)P * S, n1, (long long)S};
         launch_pdl(pick_kd<T>(C, check, wx, g.per1 || g.per2), grd, dim3(kTX, kTY), 0, st, g, A, tc, Lt, part);
       }
-      if (check) k_reduce_check<<<B, 256, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass, g.active);
+      if (check) k_reduce_check<<<B, 512, 0, st>>>(part, (int)(grd.x * grd.y * grd.z / B), P, acc, mass, g.active);
       return;
     }
     if (hue && !check && !wx && !g.active && B >= 8 && !plain_update) {

@@ -1133,29 +1133,25 @@ __global__ void __launch_bounds__(kTX * kTY, DYNOT_UPD_MINB) k_update_tiled(Geo<
 }
 
 
-// Sum the per-block partials of each problem (one block per problem) into acc and mass.
+// Sum the per-block partials of each problem (one block per problem) into acc and mass: one warp per quantity
+// (the 3 residual and energy terms, the P mass sums, the dual term), lanes striding over the blocks in a fixed order.
 static __global__ void k_reduce_check(const double* __restrict__ part, int nblk, int P, double* __restrict__ acc,
                                double* __restrict__ mass, const int* __restrict__ active) {
   const int b = blockIdx.x;
   if (active != nullptr && active[b] == 0) return;
   const double* pb = part + (size_t)b * nblk * kPart;
-  __shared__ double red[32];
-  for (int qi = 0; qi < 4 + P; ++qi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int qi = warp; qi < 4 + P; qi += nw) {
     const int q = qi < 3 + P ? qi : kPartW;
     double s = 0;
-    for (int j = threadIdx.x; j < nblk; j += blockDim.x) s += pb[(size_t)j * kPart + q];
+    for (int j = lane; j < nblk; j += 32) s += pb[(size_t)j * kPart + q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-      if (q < 3) acc[(size_t)b * kAcc + q] = t;
-      else if (q == kPartW) acc[(size_t)b * kAcc + 3] = t;
-      else if (q - 3 < P) mass[(size_t)b * P + (q - 3)] = t;
+    if (lane == 0) {
+      if (q < 3) acc[(size_t)b * kAcc + q] = s;
+      else if (q == kPartW) acc[(size_t)b * kAcc + 3] = s;
+      else if (q - 3 < P) mass[(size_t)b * P + (q - 3)] = s;
     }
-    __syncthreads();
   }
 }
 

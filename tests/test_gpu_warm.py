@@ -168,8 +168,8 @@ def test_unet_gradients_match_oracle(ot):
 
 def test_trained_network_beats_cold_start(ot):
     """The packaged U-Net (trained on 2000 solver-generated pairs at 128x128x3, P = 32) against the
-    cold start on held-out pairs: fewer iterations and less wall time (inference included) to residual
-    1e-4, and the same accuracy against a solve to 1e-6."""
+    cold start on held-out pairs: fewer iterations and less wall time (inference included; median over the
+    pairs) to residual 1e-4, and the same accuracy against a solve to 1e-6."""
     import os
     from paper_1501_04840_gb300 import warmstart as W
     if not os.path.exists(W.DEFAULT_WEIGHTS):
@@ -182,5 +182,6 @@ def test_trained_network_beats_cold_start(ot):
         warm["err"]["mean"]))
     assert cold["all_converged"] and warm["all_converged"]
     assert warm["iters"]["mean"] <= 0.92 * cold["iters"]["mean"]
-    assert warm["ms"]["mean"] < cold["ms"]["mean"]
+    # wall time by the median over the pairs, which a one-off stall of the process in one pair does not move
+    assert warm["ms"]["p50"] < cold["ms"]["p50"]
     assert warm["err"]["mean"] <= cold["err"]["mean"] + 0.01
