@@ -362,6 +362,11 @@ struct Plan final : PlanBase {
         OT_TRY(make_tensor_maps());
     }
     OT_TRY(tune());
+    {
+      // DYNOT_TIME_CHUNK=k: time chunks of k planes in the tiled update instead of the tuned length (comparisons)
+      const char* tcs = std::getenv("DYNOT_TIME_CHUNK");
+      if (tiled && tcs && std::atoi(tcs) >= 1) tc = std::min(std::atoi(tcs), P);
+    }
     return OT_OK;
   }
 
@@ -411,9 +416,10 @@ struct Plan final : PlanBase {
   //  - the y/colour pass: column strips of 4, 8 or 16 (FFT lengths, FP32) with 6, 12 or 24 row pairs per
   //    FFT chunk;
   //  - the tiled update: staged by bulk tensor copies or with plain loads (where both exist), and time chunks
-  //    of P, P/2, P/4 or P/8 planes.
-  // Each candidate is timed over three launches on the zeroed workspace (b set so that the prox takes its
-  // Newton branch); a later candidate must beat the best by 3 % (ties keep the earlier, simpler one).
+  //    of P, P/2, P/4 or P/8 planes, each timed over whole iterations (FP32).
+  // Each candidate is timed over ten launches (after two untimed ones) on the zeroed workspace (b set so that the prox takes its
+  // Newton branch); a later candidate must beat the best by 3 % (1 % for the FP32 update, timed over whole iterations,
+  // where the update's share dilutes its differences; ties keep the earlier, simpler one).
   struct Tuned {
     int yw = kW, tc = 0;
     bool tma = false;
@@ -456,11 +462,12 @@ struct Plan final : PlanBase {
   }
 
   template <class F>
-  ot_status time3(F&& launch, float& ms) {
+  ot_status time_launches(F&& launch, float& ms) {
     launch();   // warm
+    launch();
     CUDA_OK(cudaGetLastError());
     CUDA_OK(cudaEventRecord(ev[10], st));
-    for (int r = 0; r < 3; ++r) launch();
+    for (int r = 0; r < 10; ++r) launch();
     CUDA_OK(cudaEventRecord(ev[11], st));
     CUDA_OK(cudaEventSynchronize(ev[11]));
     CUDA_OK(cudaEventElapsedTime(&ms, ev[10], ev[11]));
@@ -497,7 +504,7 @@ struct Plan final : PlanBase {
       for (int w : {kW, 4, 16}) {
         if (!set_yw(w)) continue;
         float ms = 0;
-        OT_TRY(time3([&] {
+        OT_TRY(time_launches([&] {
           launch_pdl(kb, dim3((n1 + yw - 1) / yw, P, B), dim3(yc_threads(n2, yw)), smB, st, g, hat, yc, scrB);
         }, ms));
         if (ms < 0.97f * best) {
@@ -515,8 +522,12 @@ struct Plan final : PlanBase {
         for (int c : cands) {
           tc = c;
           float ms = 0;
-          OT_TRY(time3([&] { enqueue_update(0, false, false); }, ms));
-          if (ms < 0.97f * best) {
+          // FP32: whole iterations, the update's time with phi just written by the inverse pass, as in a solve
+          // (timed alone, on a cold workspace, the ranking of the time chunks differed from the one inside
+          // iterations); FP64 (the precision study's reference, whose iterations are long): the update alone
+          if (std::is_same<T, float>::value) OT_TRY(time_launches([&] { enqueue_iteration(0, false, false); }, ms));
+          else OT_TRY(time_launches([&] { enqueue_update(0, false, false); }, ms));
+          if (ms < (std::is_same<T, float>::value ? 0.99f : 0.97f) * best) {   // whole iterations: 1 %
             best = ms;
             pick.tc = c;
             pick.tma = use_tma;
